@@ -1,0 +1,320 @@
+"""Benchmark of the GB300 dual-tree Gauss transform.
+
+One step = one full dual-tree sum of the workload: build the kd-tree and
+raw moments of the points (Q = R), then dfgt_sum over every bandwidth of
+the workload at eps.  The metric is effective query-reference pairs per
+second, |Q| |R| n_h / time, next to the GPU brute force on the same data.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dfgt|reference]
+
+Under torchrun every rank runs an independent replica on its own GPU
+(its own seeded draw of the same workload; weak scaling, no collective on
+the data path); rank 0 prints one JSON line with the max time over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1102_2878_gb300 import datagen  # noqa: E402
+
+METRIC = "effective query-ref pairs/s (|Q|·|R|/time) at ε=1e-2, DFGT vs GPU brute force"
+UNIT = "pairs/s"
+DEFAULT_WORKLOAD = "kde3d_n2e5_sweep10"
+SM_COUNT, SFU_EX2_PER_CLK_PER_SM = 152, 16
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_oracle_rate(x, hs, target_s, seed=0):
+    """Time the FP64 oracle's exact sums on a bounded query sample (all
+    references, all bandwidths); returns (pairs/s, sample description, cores)."""
+    import oracle
+
+    oracle.build()
+    x64 = x.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    probe = rng.choice(len(x), size=8, replace=False)
+    t0 = time.perf_counter()
+    for h in hs:
+        oracle.naive_kde(x64[probe], x64, h)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    per_query = dt / len(probe)
+    nq = int(max(16, min(len(x), target_s / per_query)))
+    sample = rng.choice(len(x), size=nq, replace=False)
+    t0 = time.perf_counter()
+    for h in hs:
+        oracle.naive_kde(x64[sample], x64, h)
+    dt = time.perf_counter() - t0
+    pairs = nq * len(x) * len(hs)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return pairs / dt, f"{nq} of {len(x)} queries x all {len(x)} references x {len(hs)} bandwidths, {dt:.1f} s", cores
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    x, hs, eps = datagen.workload(args.workload)
+    vals = []
+    desc, cores = "", 0
+    per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        v, desc, cores = cpu_oracle_rate(x, hs, per_step, seed=i)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    pairs_step = len(x) * len(x) * len(hs)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * pairs_step / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "D": x.shape[1], "N": len(x), "nh": len(hs),
+                       "eps": eps, "q_eq_r": True},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc + " per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_dfgt(args, rank, world, local):
+    import torch
+
+    import paper_1102_2878_gb300 as dfgt
+
+    torch.cuda.set_device(local)
+    dfgt.build()
+    x, hs, eps = datagen.workload(args.workload)
+    if rank > 0:  # an independent replica: same recipe, another seed
+        rng = np.random.default_rng(1000 + rank)
+        x = np.ascontiguousarray(x[rng.permutation(len(x))] +
+                                 rng.normal(0, 1e-4, size=x.shape).astype(np.float32))
+        x = np.clip(x, 0, 1).astype(np.float32)
+    N, D, nh = x.shape[0], x.shape[1], len(hs)
+    ctx = dfgt.Context(local)
+    pts = torch.from_numpy(x).to(f"cuda:{local}")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
+    torch.cuda.synchronize()
+
+    def step():
+        tree = dfgt.Tree(ctx, pts)
+        G, st = dfgt.kde_sum(ctx, tree, tree, hs, eps)
+        tree.close()
+        return G, st
+
+    for _ in range(args.warmup):
+        G, st = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launch_count()
+    times, stats = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(ctx.stream):
+            flush.fill_(1.0)  # evict L2 (129 MB) between timed steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        G, st = step()
+        e1.record(ctx.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        stats.append(st)
+    launches = ctx.launch_count() - launches0
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = statistics.mean(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    pairs_step = N * N * nh
+    value = world * pairs_step / (ms / 1e3)
+
+    # GPU brute force on the same data (the comparison named by the metric)
+    Gb = dfgt.kde_sum_bruteforce(ctx, pts, pts, hs)
+    bf_ms = []
+    for _ in range(max(2, min(args.steps, 3))):
+        with torch.cuda.stream(ctx.stream):
+            flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        dfgt.kde_sum_bruteforce(ctx, pts, pts, hs, out=Gb)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        bf_ms.append(e0.elapsed_time(e1))
+    bf = statistics.mean(bf_ms)
+    rel = ((G - Gb).abs() / Gb).max().item()
+
+    # end to end through the host-buffer C-ABI call (copies inside the timed region)
+    xh = torch.from_numpy(x).pin_memory().numpy()
+    Gh = torch.empty((nh, N), dtype=torch.float64).pin_memory().numpy()
+    dfgt.kde_host(ctx, xh, None, hs, eps, out=Gh)
+    e2e_t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        dfgt.kde_host(ctx, xh, None, hs, eps, out=Gh)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t)
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (the exact leaf-pair sums): one ex2 per
+    # pair interaction plus ~2D+2 FP32 ops, ALU-bound on the SFU ex2 rate
+    inter = statistics.mean(s["base_interactions"] for s in stats)
+    base_ms = statistics.mean(s["ms_base"] for s in stats)
+    peaks = measured_peaks()
+    sm_clk = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = SM_COUNT * SFU_EX2_PER_CLK_PER_SM * sm_clk * 1e6
+    achieved = inter / (base_ms / 1e3) if base_ms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_base (DFGTBase leaf-pair sums)", "achieved": achieved,
+            "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": f"152 SMs x 16 ex2/clk x {sm_clk:.0f} MHz (unit counts)"}
+    cpu_rate, cpu_desc, cores = (None, None, None)
+    if not args.no_cpu_baseline:
+        cpu_rate, cpu_desc, cores = cpu_oracle_rate(x, hs, args.cpu_seconds)
+    mean = lambda k: statistics.mean(s[k] for s in stats)  # noqa: E731
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "D": D, "N": N, "nh": nh,
+                   "h": [float(v) for v in hs], "eps": eps, "q_eq_r": True,
+                   "step": "kd-tree build + moments + dual-tree sum over all bandwidths",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "bruteforce": {"value": world * pairs_step / (bf / 1e3), "unit": UNIT, "ms_per_step": bf},
+        "speedup_vs_bruteforce": bf / ms,
+        "max_rel_err_vs_bruteforce": rel,
+        "breakdown_ms": {"traverse": mean("ms_traverse"), "base": mean("ms_base"),
+                         "farfield": mean("ms_farfield"), "local": mean("ms_local"),
+                         "f2l": mean("ms_f2l"), "post": mean("ms_post")},
+        "work": {"pairs_visited": mean("pairs_visited"), "prune": mean("n_prune"),
+                 "farfield": mean("n_farfield"), "local": mean("n_local"), "f2l": mean("n_f2l"),
+                 "base_pairs": mean("n_base"), "base_interactions": inter, "rounds": mean("rounds")},
+        "roofline": roof,
+        "cpu_baseline": None if cpu_rate is None else
+        {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cpu_desc},
+        "e2e": {"value": pairs_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
+                "d2h_bytes_per_step": int(Gh.nbytes)},
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dfgt", "reference"], default="dfgt")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_dfgt(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * dfgt.h -- C ABI of the GB300 dual-tree fast Gauss transform library.
+ *
+ * The library computes Gaussian kernel sums (Eq. 5 of Lee, Gray & Moore,
+ * "Dual-Tree Fast Gauss Transforms")
+ *
+ *     G(q_i) = sum_j exp(-||q_i - r_j||^2 / (2 h^2))
+ *
+ * for every query q_i, either exactly (brute force) or with a per-query
+ * relative error bound |G~(q_i) - G(q_i)| <= eps * G(q_i) (Definition 1.2)
+ * by the dual-tree traversal of Section 3.6.  All compute runs in CUDA
+ * kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - Points are row-major float32 arrays [n][d], 1 <= d <= 32.
+ *   - "_dev" pointers are device memory on the context's device and are
+ *     owned by the caller; "_host" pointers are host memory owned by the
+ *     caller.  The library never frees or keeps caller memory.
+ *   - Trees and contexts are opaque and owned by the library; free them
+ *     with dfgt_tree_destroy / dfgt_destroy.
+ *   - Every call is enqueued on the context's stream and returns only
+ *     after that work has finished and its status word has been read back.
+ *     No call aborts, traps or throws; failures come back as a status and
+ *     a message from dfgt_last_error.
+ *   - Invalid arguments return DFGT_EINVAL before anything is launched.
+ *   - One context serves one host thread at a time.
+ */
+#ifndef DFGT_H
+#define DFGT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DFGT_OK = 0,
+  DFGT_EINVAL = 1,        /* an argument is out of range; nothing was launched */
+  DFGT_ENOMEM = 2,        /* a device or pinned-host allocation failed */
+  DFGT_ECUDA = 3,         /* a CUDA runtime call failed (message in dfgt_last_error) */
+  DFGT_ECAPACITY = 4,     /* a device work list overflowed its hard size limit */
+  DFGT_ETIMEOUT = 5,      /* a bounded loop (tree levels, traversal rounds) ran out */
+  DFGT_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} dfgt_status;
+
+typedef struct dfgt_ctx dfgt_ctx;   /* device, stream, cached workspace */
+typedef struct dfgt_tree dfgt_tree; /* permuted points, kd-tree nodes, raw moments */
+
+/* Build and traversal options.  Zero-initialised means "defaults". */
+typedef struct {
+  int leaf_size;   /* leaf threshold of Algorithm 2 (BuildKdTree); 0 -> 32; max 256 */
+  int p_max;       /* per-dimension expansion order limit; 0 -> the paper's table
+                      (Section 3.6: 6 for D=2, 4 for D=3, 2 for D=4,5, 1 for D>=6;
+                      8 for D=1); a smaller positive value lowers it */
+  double eps_fp;   /* part of eps reserved for float32 rounding in exact sums;
+                      0 -> 2e-5; must be < eps */
+} dfgt_opts;
+
+/* Work counters of one dfgt_sum call, summed over its bandwidths. */
+typedef struct {
+  long long pairs_visited;      /* node pairs classified */
+  long long n_prune;            /* pairs summarised by the distance-bound prune */
+  long long n_farfield;         /* pairs summarised by far-field evaluation (F) */
+  long long n_local;            /* pairs summarised by direct local accumulation (D) */
+  long long n_f2l;              /* pairs summarised by far-to-local translation (T) */
+  long long n_base;             /* leaf pairs summed exactly (DFGTBase) */
+  long long base_interactions;  /* sum over base pairs of |Q_leaf| * |R_leaf| */
+  long long kernel_launches;    /* kernels this call launched */
+  int rounds;                   /* level-synchronous traversal rounds */
+  int overflow_retries;         /* times a work list was regrown and the call redone */
+  double ms_traverse;           /* device time of the traversal rounds */
+  double ms_actions;            /* device time of the F/D/T/base kernels */
+  double ms_post;               /* device time of the downward pass and finalisation */
+  double ms_base;               /* device time of the base-case kernel (DFGTBase) */
+  double ms_farfield;           /* device time of the far-field evaluation kernel */
+  double ms_local;              /* device time of the direct local accumulation kernel */
+  double ms_f2l;                /* device time of the far-to-local translation kernel */
+} dfgt_stats;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to run on (not owned), or NULL to create a private
+ * non-blocking stream. */
+dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream);
+
+/* Set the initial capacity of the traversal's work lists (node pairs per
+ * frontier, items per action list).  A call whose lists outgrow them
+ * regrows them and redoes its traversal (dfgt_stats.overflow_retries);
+ * larger values trade memory for fewer retries.  Both must be >= 1. */
+dfgt_status dfgt_set_capacity(dfgt_ctx* ctx, int64_t frontier_pairs, int64_t list_items);
+
+/* Free a context and its cached workspace.  NULL is ignored. */
+void dfgt_destroy(dfgt_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched since it was created
+ * (tree builds, sums, brute force); -1 for a NULL context. */
+long long dfgt_launch_count(const dfgt_ctx* ctx);
+
+/* Message of the last failure on this context ("" if none).  The string
+ * belongs to the context and lives until the next call on it. */
+const char* dfgt_last_error(const dfgt_ctx* ctx);
+
+/* Build the mid-point kd-tree of Algorithm 2 (BuildKdTree, Section 2.1)
+ * over n points (points_dev: float32 [n][d], device, caller-owned, not
+ * modified) and the raw far-field moments of every node
+ * (Eq. far_field_moments; leaves directly, internal nodes by the
+ * far-to-far translation of Lemma 3.5).  The tree keeps its own permuted
+ * copy of the points.  n >= 1, 1 <= d <= 32, finite coordinates. */
+dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
+                       const dfgt_opts* opts, dfgt_tree** out);
+
+/* Free a tree.  NULL is ignored. */
+void dfgt_tree_destroy(dfgt_tree* tree);
+
+/* Approximate G(q_i) for every query of `qtree` against every reference
+ * of `rtree` (qtree may equal rtree: the cross-validation setting of the
+ * introduction) for each of the nh bandwidths h_host[0..nh), with the
+ * relative error bound eps of Definition 1.2 (Theorem 3.3), by the
+ * dual-tree traversal of Section 3.6 (DFGTMain).
+ *   h_host : nh finite values > 0 (host); 1 <= nh <= 1024
+ *   eps    : 0 < eps < 1
+ *   G_dev  : float64 [nh][nq] (device, caller-owned), written in the
+ *            caller's original query order; unnormalised sums of Eq. 5
+ *   stats  : optional work counters (host), may be NULL
+ * The guarantee holds for every query whose exact sum is above ~1e-30
+ * (float32 range of the exact leaf sums). */
+dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree,
+                     const double* h_host, int nh, double eps, double* G_dev,
+                     dfgt_stats* stats);
+
+/* Exact G(q_i) by the all-pairs sum of Algorithm 1 (NaiveKDE, without its
+ * normalisation) for nh bandwidths; float32 distances and exponentials,
+ * compensated accumulation.
+ *   q_dev  : float32 [nq][d] device;  r_dev : float32 [nr][d] device
+ *   h_host : nh values > 0 (host), 1 <= nh <= 1024
+ *   G_dev  : float64 [nh][nq] device, caller-owned */
+dfgt_status dfgt_sum_bruteforce(dfgt_ctx* ctx, const float* q_dev, int64_t nq,
+                                const float* r_dev, int64_t nr, int d, const double* h_host,
+                                int nh, double* G_dev);
+
+/* End-to-end convenience call on HOST buffers: copies the points to the
+ * device, builds the tree(s), runs dfgt_sum and copies G back.  When
+ * q_host == r_host and nq == nr one tree serves both sides.
+ *   q_host, r_host : float32 [n][d] host (pinned memory is fastest)
+ *   G_host         : float64 [nh][nq] host, caller-owned */
+dfgt_status dfgt_kde_host(dfgt_ctx* ctx, const float* q_host, int64_t nq, const float* r_host,
+                          int64_t nr, int d, const double* h_host, int nh, double eps,
+                          const dfgt_opts* opts, double* G_host, dfgt_stats* stats);
+
+/* ---- introspection (used by the tests; not on the hot path) ---- */
+
+typedef struct {
+  int64_t n_points;
+  int d;
+  int n_nodes;     /* nodes are numbered level by level (breadth-first) */
+  int n_leaves;
+  int depth;       /* number of levels */
+  int leaf_size;
+  int p_max;       /* storage radix of the coefficient tables */
+  int n_coeff;     /* p_max^d coefficients per node */
+} dfgt_tree_info;
+
+dfgt_status dfgt_tree_get_info(const dfgt_tree* tree, dfgt_tree_info* out);
+
+/* Copy the tree to caller-owned HOST buffers; any pointer may be NULL.
+ *   perm    int32  [n]          original index of the point at each position
+ *   lo, hi  float32[n_nodes][d] tight bounding box of each node (Algorithm 2)
+ *   begin, count int32 [n_nodes] the node's points are positions [begin, begin+count)
+ *   left    int32  [n_nodes]    first child (the second is left+1), -1 for a leaf
+ *   moments float64[n_nodes][n_coeff] raw moments m_alpha = sum_r (r-c)^alpha/alpha!
+ *           about the box center c, multi-index alpha at position
+ *           sum_d alpha[d] p_max^(d_count-1-d) (last dimension least significant);
+ *           the h-scaled moments of Eq. far_field_moments are m_alpha (2h^2)^(-|alpha|/2). */
+dfgt_status dfgt_tree_export(const dfgt_tree* tree, int32_t* perm, float* lo, float* hi,
+                             int32_t* begin, int32_t* count, int32_t* left, double* moments);
+
+/* Actions of Summarize / DFGTBase applied to explicit node pairs. */
+enum {
+  DFGT_ACT_PRUNE = 0,    /* |R|(K(d^l)+K(d^u))/2 to every query of Q */
+  DFGT_ACT_FARFIELD = 1, /* EvaluateFarFieldExpansion of R at the queries of Q, order p */
+  DFGT_ACT_LOCAL = 2,    /* AccumulateDirectLocalMoment of R into Q, order p */
+  DFGT_ACT_F2L = 3,      /* TransFarToLocal of R's moments into Q, order p */
+  DFGT_ACT_BASE = 4      /* DFGTBase: exact sum (both nodes must be leaves) */
+};
+
+/* Apply the listed actions for one bandwidth h and write, for every query
+ * of qtree, the sum of their contributions after the downward pass
+ * (TransLocalToLocal + EvaluateLocalExpansion, DFGTPost) into G_dev
+ * (float64 [nq], caller order).  qnode/rnode/action/order are host arrays
+ * of length n (order in 1..p_max, ignored for prune and base).  This runs
+ * the same kernels as dfgt_sum on a caller-chosen pair list; it exists so
+ * each operator can be checked against a reference. */
+dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree,
+                             const int32_t* qnode_host, const int32_t* rnode_host,
+                             const int32_t* action_host, const int32_t* order_host, int n,
+                             double h, double* G_dev);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DFGT_H */

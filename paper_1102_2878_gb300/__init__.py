@@ -1,0 +1,204 @@
+"""GB300-native dual-tree fast Gauss transform (Lee, Gray & Moore).
+
+Python face of ``libdfgt.so``.  PyTorch provides device memory and the
+stream; every step of the computation runs in the library's CUDA kernels.
+
+    ctx = Context()                       # device 0, a private CUDA stream
+    tree = Tree(ctx, points)              # points: float32 CUDA tensor [n, d]
+    G, stats = kde_sum(ctx, tree, tree, [0.01, 0.1], eps=1e-2)   # [nh, n] float64
+    Gx = kde_sum_bruteforce(ctx, points, points, [0.01, 0.1])    # exact sums
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+
+__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_bruteforce", "kde_host",
+           "apply_pairs", "build"]
+
+
+class DFGTError(RuntimeError):
+    def __init__(self, status, message):
+        self.status = _lib.STATUS.get(status, str(status))
+        super().__init__(f"{self.status}: {message}")
+
+
+def build(force: bool = False) -> str:
+    from .build_ext import build as _b
+
+    return _b(force=force)
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+class Context:
+    """A device, a CUDA stream (a torch stream the library runs on) and the
+    library's cached workspace.  Calls wait for the caller's current torch
+    stream before they start, and return after their own work finished."""
+
+    def __init__(self, device: int = 0):
+        torch = _torch()
+        self.lib = _lib.load()
+        self.device = device
+        self.stream = torch.cuda.Stream(device=device)
+        h = C.c_void_p()
+        st = self.lib.dfgt_create(C.byref(h), device, C.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise DFGTError(st, "dfgt_create failed")
+        self.h = h
+
+    def check(self, st, what):
+        if st != 0:
+            msg = self.lib.dfgt_last_error(self.h)
+            raise DFGTError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_capacity(self, frontier_pairs: int, list_items: int):
+        """Initial work-list capacities (pairs per frontier, items per list)."""
+        self.check(self.lib.dfgt_set_capacity(self.h, int(frontier_pairs), int(list_items)),
+                   "dfgt_set_capacity")
+
+    def launch_count(self) -> int:
+        """Kernels this context launched so far."""
+        return int(self.lib.dfgt_launch_count(self.h))
+
+    def order_after_torch(self):
+        torch = _torch()
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.dfgt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _opts(leaf_size=0, p_max=0, eps_fp=0.0):
+    return _lib.Opts(int(leaf_size), int(p_max), float(eps_fp))
+
+
+class Tree:
+    """The mid-point kd-tree of Algorithm 2 over float32 points [n, d] on
+    the context's device, with the raw far-field moments of every node."""
+
+    def __init__(self, ctx: Context, points, leaf_size: int = 0, p_max: int = 0, eps_fp: float = 0.0):
+        torch = _torch()
+        if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
+                and points.dim() == 2):
+            raise TypeError("points must be a float32 CUDA tensor [n, d]")
+        self.ctx = ctx
+        self.points = points.contiguous()
+        self.n, self.d = self.points.shape
+        opts = _opts(leaf_size, p_max, eps_fp)
+        h = C.c_void_p()
+        ctx.order_after_torch()
+        st = ctx.lib.dfgt_build(ctx.h, C.c_void_p(self.points.data_ptr()), self.n, self.d,
+                                C.byref(opts), C.byref(h))
+        ctx.check(st, "dfgt_build")
+        self.h = h
+
+    def info(self) -> dict:
+        inf = _lib.TreeInfo()
+        self.ctx.check(self.ctx.lib.dfgt_tree_get_info(self.h, C.byref(inf)), "dfgt_tree_get_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def export(self) -> dict:
+        inf = self.info()
+        nn, d, P = inf["n_nodes"], inf["d"], inf["n_coeff"]
+        out = {"perm": np.empty(self.n, np.int32), "lo": np.empty((nn, d), np.float32),
+               "hi": np.empty((nn, d), np.float32), "begin": np.empty(nn, np.int32),
+               "count": np.empty(nn, np.int32), "left": np.empty(nn, np.int32),
+               "moments": np.empty((nn, P), np.float64)}
+        ptr = [C.c_void_p(out[k].ctypes.data) for k in ("perm", "lo", "hi", "begin", "count", "left", "moments")]
+        self.ctx.check(self.ctx.lib.dfgt_tree_export(self.h, *ptr), "dfgt_tree_export")
+        out["info"] = inf
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.dfgt_tree_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _hs(hs):
+    a = np.ascontiguousarray(np.atleast_1d(np.asarray(hs, dtype=np.float64)))
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def kde_sum(ctx: Context, qtree: Tree, rtree: Tree, hs, eps: float, out=None):
+    """G~ [nh, nq] float64 (CUDA) within relative error eps of Eq. 5, and work stats."""
+    torch = _torch()
+    ha, hp = _hs(hs)
+    if out is None:
+        out = torch.empty((len(ha), qtree.n), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    stats = _lib.Stats()
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_sum(ctx.h, qtree.h, rtree.h, hp, len(ha), float(eps), C.c_void_p(out.data_ptr()),
+                          C.byref(stats))
+    ctx.check(st, "dfgt_sum")
+    return out, stats.as_dict()
+
+
+def kde_sum_bruteforce(ctx: Context, q, r, hs, out=None):
+    """Exact G [nh, nq] float64 (CUDA) by the all-pairs sum."""
+    torch = _torch()
+    ha, hp = _hs(hs)
+    q = q.contiguous()
+    r = r.contiguous()
+    if out is None:
+        out = torch.empty((len(ha), q.shape[0]), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_sum_bruteforce(ctx.h, C.c_void_p(q.data_ptr()), q.shape[0], C.c_void_p(r.data_ptr()),
+                                     r.shape[0], q.shape[1], hp, len(ha), C.c_void_p(out.data_ptr()))
+    ctx.check(st, "dfgt_sum_bruteforce")
+    return out
+
+
+def kde_host(ctx: Context, q: np.ndarray, r: np.ndarray | None, hs, eps: float, leaf_size=0, p_max=0,
+             eps_fp=0.0, out: np.ndarray | None = None):
+    """End to end on host arrays: G~ [nh, nq] float64 (numpy).  Pass r=None
+    (or r is q) for the cross-validation setting Q = R (one tree)."""
+    q = np.ascontiguousarray(q, dtype=np.float32)
+    same = r is None or r is q
+    r = q if same else np.ascontiguousarray(r, dtype=np.float32)
+    ha, hp = _hs(hs)
+    if out is None:
+        out = np.empty((len(ha), q.shape[0]), dtype=np.float64)
+    opts = _opts(leaf_size, p_max, eps_fp)
+    stats = _lib.Stats()
+    st = ctx.lib.dfgt_kde_host(ctx.h, C.c_void_p(q.ctypes.data), q.shape[0], C.c_void_p(r.ctypes.data),
+                               r.shape[0], q.shape[1], hp, len(ha), float(eps), C.byref(opts),
+                               C.c_void_p(out.ctypes.data), C.byref(stats))
+    ctx.check(st, "dfgt_kde_host")
+    return out, stats.as_dict()
+
+
+def apply_pairs(ctx: Context, qtree: Tree, rtree: Tree, qnode, rnode, action, order, h: float, out=None):
+    """Contributions of explicit (Q, R, action, order) items for one bandwidth."""
+    torch = _torch()
+    arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in (qnode, rnode, action, order)]
+    n = len(arrs[0])
+    if out is None:
+        out = torch.empty(qtree.n, dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_apply_pairs(ctx.h, qtree.h, rtree.h, *[C.c_void_p(a.ctypes.data) for a in arrs], n,
+                                  float(h), C.c_void_p(out.data_ptr()))
+    ctx.check(st, "dfgt_apply_pairs")
+    return out

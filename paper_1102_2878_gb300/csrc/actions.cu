@@ -1,0 +1,664 @@
+// actions.cu -- the summaries and exact sums the traversal decided on
+// (Summarize and DFGTBase of Section 3.6) and the post-processing pass
+// (DFGTPost: local-to-local translation down the query tree, local
+// expansion read-out, final sum).
+//
+// One warp handles one listed node pair.  Multi-index tables use the
+// paper's linear layout (radix p_max, last dimension least significant)
+// and are unrolled at compile time per dimension D = 1..5; D >= 6 has
+// p_max = 1 and uses the order-0 kernels at the end of the file.  Sums of
+// the exact and far-field parts go to a float64 per-query accumulator;
+// local moments are float64 per (bandwidth, query node).
+#include "internal.hpp"
+
+namespace dfgt {
+namespace {
+
+constexpr int kT = 256;
+constexpr int kWarpsPerBlock = kT / 32;
+
+template <int D, int PM>
+__device__ __forceinline__ constexpr int digit_c(int idx, int k) {
+  int v = idx;
+  for (int j = D - 1; j > k; --j) v /= PM;
+  return v % PM;
+}
+
+template <int D, int PM>
+__device__ __forceinline__ int abs_c(int idx) {
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) s += digit_c<D, PM>(idx, k);
+  return s;
+}
+
+template <int D, int PM>
+__device__ __forceinline__ bool below_c(int idx, int p) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < D; ++k) ok = ok && (digit_c<D, PM>(idx, k) < p);
+  return ok;
+}
+
+template <int D, int PM>
+__device__ __forceinline__ double multifact_c(int idx) {
+  double f = 1.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) f *= fact_d(digit_c<D, PM>(idx, k));
+  return f;
+}
+
+// Hermite functions h_0..h_{NT-1}(t) (h_n = e^{-t^2} H_n(t)) by the
+// recurrence h_{n+1} = 2t h_n - 2n h_{n-1} (ComputePartialDerivatives).
+template <int NT>
+__device__ __forceinline__ void hermite_f32(float t, float* H) {
+  H[0] = ex2_approx(-t * t * (float)kLog2e);
+  if (NT > 1) H[1] = 2.f * t * H[0];
+#pragma unroll
+  for (int n = 1; n + 1 < NT; ++n) H[n + 1] = 2.f * t * H[n] - 2.f * (float)n * H[n - 1];
+}
+
+template <int NT>
+__device__ __forceinline__ void hermite_f64(double t, double* H) {
+  H[0] = exp(-t * t);
+  if (NT > 1) H[1] = 2.0 * t * H[0];
+#pragma unroll
+  for (int n = 1; n + 1 < NT; ++n) H[n + 1] = 2.0 * t * H[n] - 2.0 * (double)n * H[n - 1];
+}
+
+__device__ __forceinline__ double center(const TreeView& T, int node, int k) {
+  return 0.5 * ((double)T.lo[(size_t)node * T.d + k] + (double)T.hi[(size_t)node * T.d + k]);
+}
+
+template <int D>
+__device__ __forceinline__ void load_point(const float* __restrict__ p, float* v) {
+  if constexpr (D == 1) {
+    v[0] = __ldg(p);
+  } else if constexpr (D == 2) {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = a.x; v[1] = a.y;
+  } else if constexpr (D <= 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z;
+    if constexpr (D == 4) v[3] = a.w;
+  } else {
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = __ldg(p + k);
+  }
+}
+
+// ------------------------------------------------------------------ base
+// DFGTBase: exact sum over a leaf pair.  Lane per query, references read
+// as broadcast loads, float32 exp2 on the SFU.
+template <int D>
+__global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const Pair* __restrict__ list,
+                                             int n, const double* __restrict__ hv,
+                                             double* __restrict__ gacc) {
+  constexpr int DD = D > 0 ? D : kMaxD;
+  const int d = D > 0 ? D : Q.d;
+  const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const Pair pr = list[w];
+  const double h = hv[pr.h];
+  const float c2 = (float)(-kLog2e / (2.0 * h * h));
+  const int qb = Q.beg[pr.q], qn = Q.cnt[pr.q], rb = R.beg[pr.r], rn = R.cnt[pr.r];
+  for (int qi = lane; qi < qn; qi += 32) {
+    float qv[DD];
+    if constexpr (D > 0) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
+    else
+      for (int k = 0; k < d; ++k) qv[k] = Q.pts[(size_t)(qb + qi) * Q.dp + k];
+    float s = 0.f;
+#pragma unroll 4
+    for (int j = 0; j < rn; ++j) {
+      float rv[DD];
+      if constexpr (D > 0) load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
+      float d2 = 0.f;
+      if constexpr (D > 0) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) { const float t = qv[k] - rv[k]; d2 = fmaf(t, t, d2); }
+      } else {
+        for (int k = 0; k < d; ++k) { const float t = qv[k] - R.pts[(size_t)(rb + j) * R.dp + k]; d2 = fmaf(t, t, d2); }
+      }
+      s += ex2_approx(d2 * c2);
+    }
+    atomicAdd(&gacc[(size_t)pr.h * Q.n + qb + qi], (double)s);
+  }
+}
+
+// Scaled far-field moments M_alpha = m_alpha (2h^2)^(-|alpha|/2) for alpha < p
+// (zero elsewhere) into shared memory, float32.
+template <int D, int PM, int P>
+__device__ __forceinline__ void stage_moments(const double* __restrict__ m, double s, int p,
+                                              float* Ms, int lane) {
+  for (int idx = lane; idx < P; idx += 32) {
+    int a[D];
+    int ab = 0;
+    bool ok = true;
+    {
+      int v = idx;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k) { a[k] = v % PM; v /= PM; ab += a[k]; ok = ok && a[k] < p; }
+    }
+    Ms[idx] = ok ? (float)(m[idx] * pow_int(s, ab)) : 0.f;
+  }
+}
+
+// ------------------------------------------------------------- far field
+// EvaluateFarFieldExpansion: sum_{alpha<p} M_alpha h_alpha((q - R.c)/sqrt(2h^2)).
+template <int D>
+__global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
+                                                 const Action* __restrict__ list, int n,
+                                                 const double* __restrict__ hv,
+                                                 double* __restrict__ gacc) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  __shared__ float sM[kWarpsPerBlock][P];
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarpsPerBlock + wib;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const Action a = list[w];
+  const double h = hv[a.h];
+  const double s = 1.0 / sqrt(2.0 * h * h);
+  float* Ms = sM[wib];
+  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, s, a.p, Ms, lane);
+  __syncwarp();
+  float cR[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) cR[k] = (float)center(R, a.r, k);
+  const float sf = (float)s;
+  const int qb = Q.beg[a.q], qn = Q.cnt[a.q];
+  for (int qi = lane; qi < qn; qi += 32) {
+    float qv[D];
+    load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
+    float H[D][PM];
+#pragma unroll
+    for (int k = 0; k < D; ++k) hermite_f32<PM>((qv[k] - cR[k]) * sf, H[k]);
+    float acc = 0.f;
+#pragma unroll
+    for (int idx = 0; idx < P; ++idx) {
+      float t = Ms[idx];
+#pragma unroll
+      for (int k = 0; k < D; ++k) t *= H[k][digit_c<D, PM>(idx, k)];
+      acc += t;
+    }
+    atomicAdd(&gacc[(size_t)a.h * Q.n + qb + qi], (double)acc);
+  }
+}
+
+// ------------------------------------------------------------ direct local
+// AccumulateDirectLocalMoment:
+// L_beta(Q) += ((-1)^{|beta|}/beta!) sum_{r in R} h_beta((Q.c - r)/sqrt(2h^2)).
+// Each lane tabulates the 1-D Hermite functions of one reference point in
+// shared memory; each lane then owns coefficient positions and sums over
+// the 32 tabulated points.  Runs of 32 are summed in float32 and added in
+// float64.
+template <int D>
+__global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const Action* __restrict__ list,
+                                              int n, const double* __restrict__ hv,
+                                              double* __restrict__ L, int* __restrict__ pused) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  constexpr int S = (P + 31) / 32;
+  __shared__ float sH[kWarpsPerBlock][32][D][PM];
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarpsPerBlock + wib;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const Action a = list[w];
+  const double h = hv[a.h];
+  const float sf = (float)(1.0 / sqrt(2.0 * h * h));
+  float cQ[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) cQ[k] = (float)center(Q, a.q, k);
+  const int rb = R.beg[a.r], rn = R.cnt[a.r];
+  double acc[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) acc[s] = 0.0;
+  for (int j0 = 0; j0 < rn; j0 += 32) {
+    const int j = j0 + lane;
+    if (j < rn) {
+      float rv[D];
+      load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
+#pragma unroll
+      for (int k = 0; k < D; ++k) hermite_f32<PM>((cQ[k] - rv[k]) * sf, sH[wib][lane][k]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < D; ++k)
+#pragma unroll
+        for (int e = 0; e < PM; ++e) sH[wib][lane][k][e] = 0.f;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const int idx = lane + 32 * s;
+      if (idx < P) {
+        int al[D];
+        {
+          int v = idx;
+#pragma unroll
+          for (int k = D - 1; k >= 0; --k) { al[k] = v % PM; v /= PM; }
+        }
+        float part = 0.f;
+        for (int jj = 0; jj < 32; ++jj) {
+          float t = sH[wib][jj][0][al[0]];
+#pragma unroll
+          for (int k = 1; k < D; ++k) t *= sH[wib][jj][k][al[k]];
+          part += t;
+        }
+        acc[s] += (double)part;
+      }
+    }
+    __syncwarp();
+  }
+  const size_t hq = (size_t)a.h * Q.nn + a.q;
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int idx = lane + 32 * s;
+    if (idx < P) {
+      int ab = 0;
+      bool ok = true;
+      double f = 1.0;
+      int v = idx;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k) { const int e = v % PM; v /= PM; ab += e; ok = ok && e < a.p; f *= fact_d(e); }
+      if (ok) atomicAdd(&L[hq * P + idx], ((ab & 1) ? -acc[s] : acc[s]) / f);
+    }
+  }
+  if (lane == 0) atomicMax(&pused[hq], a.p);
+}
+
+// --------------------------------------------------------- far to local
+// TransFarToLocal (Lemma 3.3, Eq. farfield_to_local_formula):
+// L_beta(Q) += ((-1)^{|beta|}/beta!) sum_{alpha<p} M_alpha h_{alpha+beta}((Q.c - R.c)/sqrt(2h^2)).
+// The 1-D Hermite table up to order 2p_max-2 is computed in float64.
+template <int D>
+__global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action* __restrict__ list,
+                                            int n, const double* __restrict__ hv,
+                                            double* __restrict__ L, int* __restrict__ pused) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  constexpr int NH = 2 * PM - 1;
+  constexpr int S = (P + 31) / 32;
+  __shared__ float sM[kWarpsPerBlock][P];
+  __shared__ float sH[kWarpsPerBlock][D][NH];
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarpsPerBlock + wib;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const Action a = list[w];
+  const double h = hv[a.h];
+  const double s = 1.0 / sqrt(2.0 * h * h);
+  if (lane < D) {
+    double H[NH];
+    hermite_f64<NH>((center(Q, a.q, lane) - center(R, a.r, lane)) * s, H);
+#pragma unroll
+    for (int e = 0; e < NH; ++e) sH[wib][lane][e] = (float)H[e];
+  }
+  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, s, a.p, sM[wib], lane);
+  __syncwarp();
+  const size_t hq = (size_t)a.h * Q.nn + a.q;
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    const int idx = lane + 32 * sl;
+    if (idx >= P) break;
+    int be[D];
+    int ab = 0;
+    bool ok = true;
+    double f = 1.0;
+    {
+      int v = idx;
+#pragma unroll
+      for (int k = D - 1; k >= 0; --k) { be[k] = v % PM; v /= PM; ab += be[k]; ok = ok && be[k] < a.p; f *= fact_d(be[k]); }
+    }
+    if (!ok) continue;
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+      float t = sM[wib][j];
+#pragma unroll
+      for (int k = 0; k < D; ++k) t *= sH[wib][k][digit_c<D, PM>(j, k) + be[k]];
+      acc += t;
+    }
+    atomicAdd(&L[hq * P + idx], ((ab & 1) ? -(double)acc : (double)acc) / f);
+  }
+  if (lane == 0) atomicMax(&pused[hq], a.p);
+}
+
+// ------------------------------------------------------------- prune
+// Distance-bound prune applied to listed pairs (the traversal applies it
+// inline): L_0(Q) += |R| (K(d^l) + K(d^u)) / 2.
+__global__ void k_prune_apply(TreeView Q, TreeView R, const Pair* __restrict__ list, int n,
+                              const double* __restrict__ hv, double* __restrict__ L,
+                              int* __restrict__ pused) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Pair pr = list[i];
+  const int d = Q.d;
+  double dl2 = 0.0, du2 = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double ql = Q.lo[(size_t)pr.q * d + k], qu = Q.hi[(size_t)pr.q * d + k];
+    const double rl = R.lo[(size_t)pr.r * d + k], ru = R.hi[(size_t)pr.r * d + k];
+    const double gap = fmax(0.0, fmax(rl - qu, ql - ru));
+    const double far = fmax(ru - ql, qu - rl);
+    dl2 += gap * gap;
+    du2 += far * far;
+  }
+  const double h = hv[pr.h];
+  const double inv = 1.0 / (2.0 * h * h);
+  const size_t hq = (size_t)pr.h * Q.nn + pr.q;
+  atomicAdd(&L[hq * Q.P], 0.5 * (double)R.cnt[pr.r] * (exp(-dl2 * inv) + exp(-du2 * inv)));
+  atomicMax(&pused[hq], 1);
+}
+
+// ------------------------------------------------------- local to local
+// TransLocalToLocal (Lemma 3.6, Eq. local_to_local_translation) from every
+// node of one level to both children, order p = highest order used at the
+// node: L_alpha(c') += sum_{alpha<=beta<p} beta!/(alpha!(beta-alpha)!) L_beta(c) ((c'-c)/sqrt(2h^2))^{beta-alpha}.
+// One warp per (node, bandwidth); a child has a single parent, so its
+// coefficients are updated without atomics.
+template <int D>
+__global__ void __launch_bounds__(kT) k_l2l(TreeView Q, double* __restrict__ L,
+                                            int* __restrict__ pused, const double* __restrict__ hv,
+                                            int nh, int a, int e) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  constexpr int S = (P + 31) / 32;
+  const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nl = e - a;
+  if (w >= nl * nh) return;
+  const int node = a + w % nl, hidx = w / nl;
+  const int cl = Q.left[node];
+  if (cl < 0) return;
+  const size_t hq = (size_t)hidx * Q.nn + node;
+  const int p = pused[hq];
+  if (p == 0) return;
+  const double* Lp = L + hq * P;
+  const double h = hv[hidx];
+  const double s = 1.0 / sqrt(2.0 * h * h);
+  for (int ch = 0; ch < 2; ++ch) {
+    const int c = cl + ch;
+    const size_t hc = (size_t)hidx * Q.nn + c;
+    double X[D][PM];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double x = (center(Q, c, k) - center(Q, node, k)) * s;
+      double v = 1.0;
+#pragma unroll
+      for (int q = 0; q < PM; ++q) { X[k][q] = v; v *= x; }
+    }
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+      const int idx = lane + 32 * sl;
+      if (idx >= P) break;
+      int al[D];
+      bool ok = true;
+      {
+        int v = idx;
+#pragma unroll
+        for (int k = D - 1; k >= 0; --k) { al[k] = v % PM; v /= PM; ok = ok && al[k] < p; }
+      }
+      if (!ok) continue;
+      double acc = 0.0;
+#pragma unroll
+      for (int j = 0; j < P; ++j) {
+        double t = Lp[j];
+        bool use = true;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const int bk = digit_c<D, PM>(j, k);
+          use = use && bk >= al[k] && bk < p;
+          if (bk >= al[k]) t *= X[k][bk - al[k]] * (fact_d(bk) / (fact_d(al[k]) * fact_d(bk - al[k])));
+        }
+        if (use) acc += t;
+      }
+      L[hc * P + idx] += acc;
+    }
+    if (lane == 0 && pused[hc] < p) pused[hc] = p;
+  }
+}
+
+// ------------------------------------------------------------ finalise
+// Leaf read-out (EvaluateLocalExpansion) and the final sum of DFGTPost:
+// G~(q) = exact + far-field parts + sum_{beta<p} L_beta ((q - Q.c)/sqrt(2h^2))^beta,
+// written to the caller's query order.  The constant term is added in
+// float64, the rest of the polynomial is evaluated in float32.
+template <int D>
+__global__ void __launch_bounds__(kT) k_finalize(TreeView Q, const double* __restrict__ gacc,
+                                                 const double* __restrict__ L,
+                                                 const int* __restrict__ pused,
+                                                 const double* __restrict__ hv, int nh,
+                                                 double* __restrict__ G) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  const long t = (long)blockIdx.x * kT + threadIdx.x;
+  if (t >= (long)nh * Q.n) return;
+  const int hidx = (int)(t / Q.n), i = (int)(t % Q.n);
+  const int leaf = Q.leaf_of[i];
+  const size_t hq = (size_t)hidx * Q.nn + leaf;
+  double val = gacc[t];
+  const int p = pused[hq];
+  if (p > 0) {
+    const double* Lq = L + hq * P;
+    val += Lq[0];
+    if (p > 1) {
+      const double h = hv[hidx];
+      const float sf = (float)(1.0 / sqrt(2.0 * h * h));
+      float qv[D];
+      load_point<D>(Q.pts + (size_t)i * Q.dp, qv);
+      float X[D][PM];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float x = (qv[k] - (float)center(Q, leaf, k)) * sf;
+        float v = 1.f;
+#pragma unroll
+        for (int q = 0; q < PM; ++q) { X[k][q] = v; v *= x; }
+      }
+      float acc = 0.f;
+#pragma unroll
+      for (int idx = 1; idx < P; ++idx) {
+        if (!below_c<D, PM>(idx, p)) continue;
+        float term = (float)Lq[idx];
+#pragma unroll
+        for (int k = 0; k < D; ++k) term *= X[k][digit_c<D, PM>(idx, k)];
+        acc += term;
+      }
+      val += (double)acc;
+    }
+  }
+  G[(size_t)hidx * Q.n + Q.perm[i]] = val;
+}
+
+// ------------------------------------------------- order 0 (D >= 6)
+// With p_max = 1 every expansion keeps only its alpha = 0 term:
+// F: |R| e^{-||q-R.c||^2/2h^2};  D: L_0 += sum_r e^{-||Q.c-r||^2/2h^2};
+// T: L_0 += |R| e^{-||Q.c-R.c||^2/2h^2}.
+__global__ void __launch_bounds__(kT) k_farfield_g(TreeView Q, TreeView R, const Action* __restrict__ list,
+                                                   int n, const double* __restrict__ hv,
+                                                   double* __restrict__ gacc) {
+  const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const Action a = list[w];
+  const double h = hv[a.h];
+  const float c2 = (float)(-kLog2e / (2.0 * h * h));
+  const float m0 = (float)R.mom[a.r];
+  const int qb = Q.beg[a.q], qn = Q.cnt[a.q];
+  for (int qi = lane; qi < qn; qi += 32) {
+    float d2 = 0.f;
+    for (int k = 0; k < Q.d; ++k) {
+      const float t = Q.pts[(size_t)(qb + qi) * Q.dp + k] - (float)center(R, a.r, k);
+      d2 = fmaf(t, t, d2);
+    }
+    atomicAdd(&gacc[(size_t)a.h * Q.n + qb + qi], (double)(m0 * ex2_approx(d2 * c2)));
+  }
+}
+
+__global__ void __launch_bounds__(kT) k_local_g(TreeView Q, TreeView R, const Action* __restrict__ list,
+                                                int n, const double* __restrict__ hv,
+                                                double* __restrict__ L, int* __restrict__ pused) {
+  const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const Action a = list[w];
+  const double h = hv[a.h];
+  const float c2 = (float)(-kLog2e / (2.0 * h * h));
+  const int rb = R.beg[a.r], rn = R.cnt[a.r];
+  float part = 0.f;
+  for (int j = lane; j < rn; j += 32) {
+    float d2 = 0.f;
+    for (int k = 0; k < Q.d; ++k) {
+      const float t = (float)center(Q, a.q, k) - R.pts[(size_t)(rb + j) * R.dp + k];
+      d2 = fmaf(t, t, d2);
+    }
+    part += ex2_approx(d2 * c2);
+  }
+  double v = part;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const size_t hq = (size_t)a.h * Q.nn + a.q;
+  if (lane == 0) {
+    atomicAdd(&L[hq], v);
+    atomicMax(&pused[hq], 1);
+  }
+}
+
+__global__ void k_f2l_g(TreeView Q, TreeView R, const Action* __restrict__ list, int n,
+                        const double* __restrict__ hv, double* __restrict__ L,
+                        int* __restrict__ pused) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Action a = list[i];
+  const double h = hv[a.h];
+  double d2 = 0.0;
+  for (int k = 0; k < Q.d; ++k) {
+    const double t = center(Q, a.q, k) - center(R, a.r, k);
+    d2 += t * t;
+  }
+  const size_t hq = (size_t)a.h * Q.nn + a.q;
+  atomicAdd(&L[hq], R.mom[a.r] * exp(-d2 / (2.0 * h * h)));
+  atomicMax(&pused[hq], 1);
+}
+
+__global__ void k_l2l_g(TreeView Q, double* __restrict__ L, int* __restrict__ pused, int nh, int a,
+                        int e) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nl = e - a;
+  if (t >= nl * nh) return;
+  const int node = a + t % nl, hidx = t / nl;
+  const int cl = Q.left[node];
+  if (cl < 0) return;
+  const size_t hq = (size_t)hidx * Q.nn + node;
+  if (pused[hq] == 0) return;
+  for (int ch = 0; ch < 2; ++ch) {
+    const size_t hc = (size_t)hidx * Q.nn + cl + ch;
+    L[hc] += L[hq];
+    if (pused[hc] < 1) pused[hc] = 1;
+  }
+}
+
+__global__ void k_finalize_g(TreeView Q, const double* __restrict__ gacc, const double* __restrict__ L,
+                             const int* __restrict__ pused, int nh, double* __restrict__ G) {
+  const long t = (long)blockIdx.x * kT + threadIdx.x;
+  if (t >= (long)nh * Q.n) return;
+  const int hidx = (int)(t / Q.n), i = (int)(t % Q.n);
+  const size_t hq = (size_t)hidx * Q.nn + Q.leaf_of[i];
+  double val = gacc[t];
+  if (pused[hq] > 0) val += L[hq];
+  G[(size_t)hidx * Q.n + Q.perm[i]] = val;
+}
+
+inline int warp_grid(long items) { return (int)((items * 32 + kT - 1) / kT); }
+
+}  // namespace
+
+#define DISPATCH_D(d, ...)                             \
+  switch (d) {                                         \
+    case 1: { constexpr int DD = 1; __VA_ARGS__; } break; \
+    case 2: { constexpr int DD = 2; __VA_ARGS__; } break; \
+    case 3: { constexpr int DD = 3; __VA_ARGS__; } break; \
+    case 4: { constexpr int DD = 4; __VA_ARGS__; } break; \
+    case 5: { constexpr int DD = 5; __VA_ARGS__; } break; \
+    default: break;                                    \
+  }
+
+cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                        const Pair* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int g = warp_grid(n);
+  if (Q.d <= 5) {
+    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc));
+  } else {
+    k_base<0><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                            const Action* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int g = warp_grid(n);
+  if (Q.d <= 5) {
+    DISPATCH_D(Q.d, k_farfield<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc));
+  } else {
+    k_farfield_g<<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                         const Action* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int g = warp_grid(n);
+  if (Q.d <= 5) {
+    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused));
+  } else {
+    k_local_g<<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                       const Action* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (Q.d <= 5) {
+    const int g = warp_grid(n);
+    DISPATCH_D(Q.d, k_f2l<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused));
+  } else {
+    k_f2l_g<<<(n + kT - 1) / kT, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prune_apply(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                               const Pair* list, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_prune_apply<<<(n + kT - 1) / kT, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_l2l_level(const TreeView& Q, const TravBuffers& b, int a, int e, cudaStream_t s) {
+  const long items = (long)(e - a) * b.nh;
+  if (items <= 0) return cudaSuccess;
+  if (Q.d <= 5) {
+    const int g = warp_grid(items);
+    DISPATCH_D(Q.d, k_l2l<DD><<<g, kT, 0, s>>>(Q, b.L, b.pused, b.h, b.nh, a, e));
+  } else {
+    k_l2l_g<<<(int)((items + kT - 1) / kT), kT, 0, s>>>(Q, b.L, b.pused, b.nh, a, e);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const TreeView& Q, const TravBuffers& b, double* G, cudaStream_t s) {
+  const long items = (long)b.nh * Q.n;
+  const int g = (int)((items + kT - 1) / kT);
+  if (Q.d <= 5) {
+    DISPATCH_D(Q.d, k_finalize<DD><<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.h, b.nh, G));
+  } else {
+    k_finalize_g<<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.nh, G);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace dfgt

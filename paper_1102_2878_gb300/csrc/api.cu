@@ -1,0 +1,428 @@
+// api.cu -- the extern "C" entry points declared in include/dfgt.h and the
+// host orchestration of one dual-tree sum (DFGTMain of Section 3.6):
+// initialise the per-node state (DFGTInitQ), run traversal rounds until the
+// frontier is empty, run the listed summaries and base cases, translate the
+// local moments down the query tree and finalise (DFGTPost).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <limits>
+
+#include "internal.hpp"
+
+using namespace dfgt;
+
+namespace {
+
+dfgt_status fail(dfgt_ctx* ctx, dfgt_status st, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return st;
+}
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t _e = (x);                                                              \
+    if (_e != cudaSuccess)                                                             \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? DFGT_ENOMEM : DFGT_ECUDA,     \
+                  std::string(#x) + ": " + cudaGetErrorString(_e));                    \
+  } while (0)
+
+constexpr size_t kHardCap = size_t(1) << 28;  // entries per work list
+
+bool bad_h(const double* h, int nh) {
+  if (!h || nh < 1 || nh > 1024) return true;
+  for (int i = 0; i < nh; ++i)
+    if (!(h[i] > 0.0) || !std::isfinite(h[i])) return true;
+  return false;
+}
+
+// Shared tail of dfgt_sum and dfgt_apply_pairs: the action kernels over
+// the lists, the local-to-local pass down the query tree, finalisation.
+dfgt_status actions_and_post(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
+                             const TravBuffers& b, int n_far, int n_loc, int n_f2l, int n_base,
+                             double* G_dev, dfgt_stats* st) {
+  cudaStream_t s = ctx->stream;
+  const TreeView Q = qt->view(), R = rt->view();
+  CK(cudaEventRecord(ctx->ev[1], s));
+  CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), n_base, s));
+  CK(cudaEventRecord(ctx->ev[4], s));
+  CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), n_far, s));
+  CK(cudaEventRecord(ctx->ev[5], s));
+  CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), n_loc, s));
+  CK(cudaEventRecord(ctx->ev[6], s));
+  CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), n_f2l, s));
+  ctx->launches += (n_base > 0) + (n_far > 0) + (n_loc > 0) + (n_f2l > 0);
+  CK(cudaEventRecord(ctx->ev[2], s));
+  for (int lev = 0; lev + 1 < qt->depth; ++lev) {
+    CK(launch_l2l_level(Q, b, qt->lvl_off[lev], qt->lvl_off[lev + 1], s));
+    ++ctx->launches;
+  }
+  CK(launch_finalize(Q, b, G_dev, s));
+  ++ctx->launches;
+  CK(cudaEventRecord(ctx->ev[3], s));
+  CK(cudaStreamSynchronize(s));
+  if (st) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    st->ms_actions = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
+    st->ms_post = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[4]);
+    st->ms_base = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
+    st->ms_farfield = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[5], ctx->ev[6]);
+    st->ms_local = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[2]);
+    st->ms_f2l = ms;
+  }
+  return DFGT_OK;
+}
+
+// Zeroed per-call state; returns the traversal buffers.
+dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
+                        const double* h_host, int nh, double eps_eff, TravBuffers* b) {
+  cudaStream_t s = ctx->stream;
+  const size_t nodes = (size_t)nh * qt->nn;
+  CK(ctx->hvals.ensure(nh * sizeof(double)));
+  CK(ctx->node_state.ensure(4 * nodes * sizeof(u64)));
+  CK(ctx->lmom.ensure(nodes * qt->P * sizeof(double)));
+  CK(ctx->pused.ensure(nodes * sizeof(int)));
+  CK(ctx->gacc.ensure((size_t)nh * qt->n * sizeof(double)));
+  CK(ctx->counters.ensure(sizeof(RoundCounters)));
+  CK(cudaMemcpyAsync(ctx->hvals.p, h_host, nh * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(ctx->node_state.p, 0, 4 * nodes * sizeof(u64), s));
+  CK(cudaMemsetAsync(ctx->lmom.p, 0, nodes * qt->P * sizeof(double), s));
+  CK(cudaMemsetAsync(ctx->pused.p, 0, nodes * sizeof(int), s));
+  CK(cudaMemsetAsync(ctx->gacc.p, 0, (size_t)nh * qt->n * sizeof(double), s));
+  CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(RoundCounters), s));
+  u64* ns = ctx->node_state.as<u64>();
+  b->inherited = ns;
+  b->decided = ns + nodes;
+  b->incr = ns + 2 * nodes;
+  b->lbsum = ns + 3 * nodes;
+  b->L = ctx->lmom.as<double>();
+  b->pused = ctx->pused.as<int>();
+  b->gacc = ctx->gacc.as<double>();
+  b->h = ctx->hvals.as<double>();
+  b->nh = nh;
+  b->eps_eff = eps_eff;
+  b->fix_scale = std::ldexp(1.0, 62) / (double)rt->n;
+  b->p_limit = std::min(qt->p_limit, rt->p_limit);
+  return DFGT_OK;
+}
+
+dfgt_status ensure_lists(dfgt_ctx* ctx) {
+  CK(ctx->frontier[0].ensure(ctx->cap_frontier * sizeof(Pair)));
+  CK(ctx->frontier[1].ensure(ctx->cap_frontier * sizeof(Pair)));
+  CK(ctx->list_far.ensure(ctx->cap_lists * sizeof(Action)));
+  CK(ctx->list_loc.ensure(ctx->cap_lists * sizeof(Action)));
+  CK(ctx->list_f2l.ensure(ctx->cap_lists * sizeof(Action)));
+  CK(ctx->list_base.ensure(ctx->cap_lists * sizeof(Pair)));
+  return DFGT_OK;
+}
+
+dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const double* h_host,
+                    int nh, double eps, double* G_dev, dfgt_stats* st) {
+  cudaStream_t s = ctx->stream;
+  const long long launches0 = ctx->launches;
+  const TreeView Q = qt->view(), R = rt->view();
+  const double eps_eff = eps - std::max(qt->eps_fp, rt->eps_fp);
+  const int max_rounds = qt->depth + rt->depth + 8;
+  int retries = 0;
+  for (;;) {
+    TravBuffers b;
+    dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, &b);
+    if (rc != DFGT_OK) return rc;
+    rc = ensure_lists(ctx);
+    if (rc != DFGT_OK) return rc;
+    RoundCounters* dctr = ctx->counters.as<RoundCounters>();
+    RoundCounters* hc = ctx->h_counters;
+    CK(cudaEventRecord(ctx->ev[0], s));
+    CK(launch_init_frontier(ctx->frontier[0].as<Pair>(), nh, s));
+    ++ctx->launches;
+    int cur = 0, nF = nh, rounds = 0;
+    long long visited = 0;
+    bool overflow = false;
+    while (nF > 0) {
+      if (rounds >= max_rounds) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: traversal did not finish");
+      CK(launch_fold(b, qt->nn, s));
+      CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
+      CK(cudaMemsetAsync(&dctr->n_next, 0, sizeof(int), s));
+      CK(launch_classify(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, ctx->frontier[cur ^ 1].as<Pair>(),
+                         (int)ctx->cap_frontier, ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(),
+                         ctx->list_f2l.as<Action>(), ctx->list_base.as<Pair>(), (int)ctx->cap_lists,
+                         dctr, s));
+      ctx->launches += 3;
+      CK(cudaMemcpyAsync(hc, dctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      visited += nF;
+      ++rounds;
+      if (hc->status & kStOverflow) { overflow = true; break; }
+      nF = hc->n_next;
+      cur ^= 1;
+    }
+    if (overflow) {
+      if (++retries > 8) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work lists overflowed repeatedly");
+      const size_t need_f = (size_t)std::max(hc->n_next, 0);
+      const size_t need_l = (size_t)std::max(std::max(hc->n_far, hc->n_loc), std::max(hc->n_f2l, hc->n_base));
+      if (need_f > ctx->cap_frontier) ctx->cap_frontier = std::max(2 * ctx->cap_frontier, need_f + need_f / 2);
+      if (need_l >= ctx->cap_lists) ctx->cap_lists = std::max(2 * ctx->cap_lists, need_l + need_l / 2);
+      if (ctx->cap_frontier > kHardCap || ctx->cap_lists > kHardCap)
+        return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work lists exceed the hard size limit");
+      continue;
+    }
+    const RoundCounters fin = *hc;
+    dfgt_status r2 = actions_and_post(ctx, qt, rt, b, fin.n_far, fin.n_loc, fin.n_f2l, fin.n_base, G_dev, st);
+    if (r2 != DFGT_OK) return r2;
+    if (st) {
+      st->pairs_visited = visited;
+      st->n_prune = (long long)fin.n_prune;
+      st->n_farfield = fin.n_far;
+      st->n_local = fin.n_loc;
+      st->n_f2l = fin.n_f2l;
+      st->n_base = fin.n_base;
+      st->base_interactions = (long long)fin.base_inter;
+      st->rounds = rounds;
+      st->overflow_retries = retries;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+      st->ms_traverse = ms;
+      st->kernel_launches = ctx->launches - launches0;
+    }
+    return DFGT_OK;
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream) {
+  if (!out) return DFGT_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return DFGT_ECUDA;
+  if (device < 0 || device >= ndev) return DFGT_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return DFGT_ECUDA;
+  dfgt_ctx* ctx = new dfgt_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    ctx->own_stream = true;
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, sizeof(RoundCounters));
+  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  if (e != cudaSuccess) {
+    dfgt_destroy(ctx);
+    return e == cudaErrorMemoryAllocation ? DFGT_ENOMEM : DFGT_ECUDA;
+  }
+  *out = ctx;
+  return DFGT_OK;
+}
+
+dfgt_status dfgt_set_capacity(dfgt_ctx* ctx, int64_t frontier_pairs, int64_t list_items) {
+  if (!ctx) return DFGT_EINVAL;
+  if (frontier_pairs < 1 || list_items < 1 || (size_t)frontier_pairs > kHardCap ||
+      (size_t)list_items > kHardCap)
+    return fail(ctx, DFGT_EINVAL, "dfgt_set_capacity: need 1 <= capacity <= 2^28");
+  ctx->cap_frontier = (size_t)frontier_pairs;
+  ctx->cap_lists = (size_t)list_items;
+  return DFGT_OK;
+}
+
+void dfgt_destroy(dfgt_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1],
+                    &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
+                    &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g};
+  for (DevBuf* b : bufs) b->release();
+  if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+  for (int i = 0; i < 8; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+long long dfgt_launch_count(const dfgt_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+const char* dfgt_last_error(const dfgt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
+                       const dfgt_opts* opts, dfgt_tree** out) {
+  if (!ctx || !out) return DFGT_EINVAL;
+  *out = nullptr;
+  if (!points_dev || n < 1 || n > (int64_t)std::numeric_limits<int>::max() / 4 || d < 1 || d > kMaxD)
+    return fail(ctx, DFGT_EINVAL, "dfgt_build: need points, 1 <= n < 2^29, 1 <= d <= 32");
+  if (opts && (opts->leaf_size < 0 || opts->leaf_size > kMaxLeaf || opts->p_max < 0 || opts->eps_fp < 0))
+    return fail(ctx, DFGT_EINVAL, "dfgt_build: options out of range");
+  CK(cudaSetDevice(ctx->device));
+  dfgt_tree* t = new dfgt_tree();
+  t->device = ctx->device;
+  ctx->err.clear();
+  dfgt_status rc = build_tree(ctx, points_dev, n, d, opts, t);
+  if (rc != DFGT_OK) {
+    delete t;
+    return rc;
+  }
+  *out = t;
+  return DFGT_OK;
+}
+
+void dfgt_tree_destroy(dfgt_tree* tree) {
+  if (!tree) return;
+  cudaSetDevice(tree->device);
+  free_tree(tree);
+  delete tree;
+}
+
+dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree,
+                     const double* h_host, int nh, double eps, double* G_dev, dfgt_stats* stats) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!qtree || !rtree || !G_dev || qtree->d != rtree->d)
+    return fail(ctx, DFGT_EINVAL, "dfgt_sum: need two trees of the same dimension and an output");
+  if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_sum: need 1..1024 finite bandwidths > 0");
+  if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, DFGT_EINVAL, "dfgt_sum: need 0 < eps < 1");
+  if (!(std::max(qtree->eps_fp, rtree->eps_fp) < eps))
+    return fail(ctx, DFGT_EINVAL, "dfgt_sum: eps must exceed the float allowance eps_fp");
+  if (qtree->device != ctx->device || rtree->device != ctx->device)
+    return fail(ctx, DFGT_EINVAL, "dfgt_sum: trees live on another device");
+  CK(cudaSetDevice(ctx->device));
+  ctx->err.clear();
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  return run_sum(ctx, qtree, rtree, h_host, nh, eps, G_dev, stats);
+}
+
+dfgt_status dfgt_sum_bruteforce(dfgt_ctx* ctx, const float* q_dev, int64_t nq, const float* r_dev,
+                                int64_t nr, int d, const double* h_host, int nh, double* G_dev) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!q_dev || !r_dev || !G_dev || nq < 1 || nr < 1 || nq > std::numeric_limits<int>::max() ||
+      nr > std::numeric_limits<int>::max() || d < 1 || d > kMaxD)
+    return fail(ctx, DFGT_EINVAL, "dfgt_sum_bruteforce: bad sizes or pointers");
+  if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_bruteforce: need 1..1024 finite bandwidths > 0");
+  CK(cudaSetDevice(ctx->device));
+  ctx->err.clear();
+  CK(launch_bruteforce(q_dev, (int)nq, r_dev, (int)nr, d, h_host, nh, G_dev, ctx->stream, &ctx->launches));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return DFGT_OK;
+}
+
+dfgt_status dfgt_kde_host(dfgt_ctx* ctx, const float* q_host, int64_t nq, const float* r_host,
+                          int64_t nr, int d, const double* h_host, int nh, double eps,
+                          const dfgt_opts* opts, double* G_host, dfgt_stats* stats) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!q_host || !r_host || !G_host || nq < 1 || nr < 1 || d < 1 || d > kMaxD)
+    return fail(ctx, DFGT_EINVAL, "dfgt_kde_host: bad sizes or pointers");
+  if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_kde_host: need 1..1024 finite bandwidths > 0");
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const bool same = (q_host == r_host) && (nq == nr);
+  CK(ctx->io_q.ensure((size_t)nq * d * sizeof(float)));
+  CK(cudaMemcpyAsync(ctx->io_q.p, q_host, (size_t)nq * d * sizeof(float), cudaMemcpyHostToDevice, s));
+  if (!same) {
+    CK(ctx->io_r.ensure((size_t)nr * d * sizeof(float)));
+    CK(cudaMemcpyAsync(ctx->io_r.p, r_host, (size_t)nr * d * sizeof(float), cudaMemcpyHostToDevice, s));
+  }
+  CK(ctx->io_g.ensure((size_t)nh * nq * sizeof(double)));
+  dfgt_tree *qt = nullptr, *rt = nullptr;
+  dfgt_status rc = dfgt_build(ctx, ctx->io_q.as<float>(), nq, d, opts, &qt);
+  if (rc == DFGT_OK) {
+    if (same) rt = qt;
+    else rc = dfgt_build(ctx, ctx->io_r.as<float>(), nr, d, opts, &rt);
+  }
+  if (rc == DFGT_OK) rc = dfgt_sum(ctx, qt, rt, h_host, nh, eps, ctx->io_g.as<double>(), stats);
+  if (rc == DFGT_OK) {
+    cudaError_t e = cudaMemcpyAsync(G_host, ctx->io_g.p, (size_t)nh * nq * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = fail(ctx, DFGT_ECUDA, std::string("dfgt_kde_host copy-out: ") + cudaGetErrorString(e));
+  }
+  if (rt && rt != qt) dfgt_tree_destroy(rt);
+  if (qt) dfgt_tree_destroy(qt);
+  return rc;
+}
+
+dfgt_status dfgt_tree_get_info(const dfgt_tree* t, dfgt_tree_info* out) {
+  if (!t || !out) return DFGT_EINVAL;
+  out->n_points = t->n;
+  out->d = t->d;
+  out->n_nodes = t->nn;
+  out->n_leaves = t->nleaves;
+  out->depth = t->depth;
+  out->leaf_size = t->leaf;
+  out->p_max = t->pm;
+  out->n_coeff = t->P;
+  return DFGT_OK;
+}
+
+dfgt_status dfgt_tree_export(const dfgt_tree* t, int32_t* perm, float* lo, float* hi,
+                             int32_t* begin, int32_t* count, int32_t* left, double* moments) {
+  if (!t) return DFGT_EINVAL;
+  if (cudaSetDevice(t->device) != cudaSuccess) return DFGT_ECUDA;
+  struct Item { void* dst; const void* src; size_t bytes; } items[] = {
+      {perm, t->perm, (size_t)t->n * sizeof(int)},
+      {lo, t->lo, (size_t)t->nn * t->d * sizeof(float)},
+      {hi, t->hi, (size_t)t->nn * t->d * sizeof(float)},
+      {begin, t->beg, (size_t)t->nn * sizeof(int)},
+      {count, t->cnt, (size_t)t->nn * sizeof(int)},
+      {left, t->left, (size_t)t->nn * sizeof(int)},
+      {moments, t->mom, (size_t)t->nn * t->P * sizeof(double)},
+  };
+  for (const Item& it : items)
+    if (it.dst && cudaMemcpy(it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return DFGT_ECUDA;
+  return DFGT_OK;
+}
+
+dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
+                             const int32_t* qnode, const int32_t* rnode, const int32_t* action,
+                             const int32_t* order, int n, double h, double* G_dev) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!qt || !rt || !G_dev || qt->d != rt->d || n < 0 || (n > 0 && (!qnode || !rnode || !action)))
+    return fail(ctx, DFGT_EINVAL, "dfgt_apply_pairs: bad arguments");
+  if (bad_h(&h, 1)) return fail(ctx, DFGT_EINVAL, "dfgt_apply_pairs: need a finite bandwidth > 0");
+  std::vector<Pair> prune, base;
+  std::vector<Action> far, loc, f2l;
+  for (int i = 0; i < n; ++i) {
+    const int q = qnode[i], r = rnode[i], a = action[i];
+    const int p = order ? order[i] : 1;
+    if (q < 0 || q >= qt->nn || r < 0 || r >= rt->nn)
+      return fail(ctx, DFGT_EINVAL, "dfgt_apply_pairs: node index out of range");
+    if (a == DFGT_ACT_PRUNE) prune.push_back(Pair{q, r, 0, 0});
+    else if (a == DFGT_ACT_BASE) base.push_back(Pair{q, r, 0, 0});
+    else if (a >= DFGT_ACT_FARFIELD && a <= DFGT_ACT_F2L) {
+      if (p < 1 || p > qt->pm) return fail(ctx, DFGT_EINVAL, "dfgt_apply_pairs: order out of range");
+      (a == DFGT_ACT_FARFIELD ? far : a == DFGT_ACT_LOCAL ? loc : f2l).push_back(Action{q, r, 0, p});
+    } else {
+      return fail(ctx, DFGT_EINVAL, "dfgt_apply_pairs: unknown action");
+    }
+  }
+  CK(cudaSetDevice(ctx->device));
+  ctx->err.clear();
+  cudaStream_t s = ctx->stream;
+  TravBuffers b;
+  dfgt_status rc = setup_state(ctx, qt, rt, &h, 1, 0.5, &b);
+  if (rc != DFGT_OK) return rc;
+  const size_t need = std::max<size_t>({prune.size(), base.size(), far.size(), loc.size(), f2l.size(), 1});
+  ctx->cap_lists = std::max(ctx->cap_lists, need);
+  ctx->cap_frontier = std::max(ctx->cap_frontier, need);
+  rc = ensure_lists(ctx);
+  if (rc != DFGT_OK) return rc;
+  auto up = [&](DevBuf& dst, const void* src, size_t bytes) {
+    return bytes ? cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  CK(up(ctx->frontier[0], prune.data(), prune.size() * sizeof(Pair)));
+  CK(up(ctx->list_base, base.data(), base.size() * sizeof(Pair)));
+  CK(up(ctx->list_far, far.data(), far.size() * sizeof(Action)));
+  CK(up(ctx->list_loc, loc.data(), loc.size() * sizeof(Action)));
+  CK(up(ctx->list_f2l, f2l.data(), f2l.size() * sizeof(Action)));
+  CK(launch_prune_apply(qt->view(), rt->view(), b, ctx->frontier[0].as<Pair>(), (int)prune.size(), s));
+  return actions_and_post(ctx, qt, rt, b, (int)far.size(), (int)loc.size(), (int)f2l.size(),
+                          (int)base.size(), G_dev, nullptr);
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// common.cuh -- types and device helpers shared by the DFGT CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dfgt {
+
+constexpr int kMaxD = 32;
+constexpr int kWarp = 32;
+constexpr int kMaxLeaf = 256;
+typedef unsigned long long u64;
+
+// Per-dimension expansion order limit p_max (Section 3.6, query-tree
+// initialisation): 6 for D=2, 4 for D=3, 2 for D=4,5, 1 for D>=6.  D=1 is
+// not listed in the paper; 8 is used.
+__host__ __device__ constexpr int pmax_of(int D) {
+  return D <= 1 ? 8 : D == 2 ? 6 : D == 3 ? 4 : D <= 5 ? 2 : 1;
+}
+__host__ __device__ constexpr int ipow_c(int b, int e) { return e <= 0 ? 1 : b * ipow_c(b, e - 1); }
+
+// Row stride of the permuted point copy: float2 rows for D<=2, float4-aligned otherwise.
+inline int padded_dim(int d) { return d <= 2 ? d : ((d + 3) & ~3); }
+
+// Read-only view of a tree passed to kernels by value.
+struct TreeView {
+  const float* pts;    // [n][dp] points in leaf-contiguous (permuted) order
+  const int* perm;     // [n] original index of each permuted point
+  const float* lo;     // [nn][d] tight bounding box (Algorithm 2)
+  const float* hi;     // [nn][d]
+  const int* beg;      // [nn] first point of the node
+  const int* cnt;      // [nn] number of points
+  const int* left;     // [nn] first child, -1 for a leaf (second child = left+1)
+  const int* parent;   // [nn] parent node, -1 for the root
+  const int* leaf_of;  // [n] leaf owning each permuted point
+  const double* mom;   // [nn][P] raw moments sum (r-c)^alpha/alpha! about the box center
+  int n, d, dp, nn, pm, P;
+};
+
+// ---------------------------------------------------------------- math
+// 2^x on the special-function unit (PTX ex2.approx, flush-to-zero).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+constexpr double kLog2e = 1.4426950408889634073599246810018921;
+
+__host__ __device__ inline double fact_d(int n) {
+  double f = 1.0;
+  for (int i = 2; i <= n; ++i) f *= (double)i;
+  return f;
+}
+
+__device__ __forceinline__ double pow_int(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+// Order-p truncation bound shared by far-field evaluation (Eq.
+// error_bound_far_field) and direct local accumulation (Eq.
+// error_bound_local): |R|/(1-r)^D sum_{k<D} C(D,k)(1-r^p)^k (r^p/sqrt(p!))^{D-k}.
+__device__ inline double bound_farfield(double nR, int D, double r, int p) {
+  const double rp = pow_int(r, p);
+  const double a = 1.0 - rp;
+  const double b = rp / sqrt(fact_d(p));
+  double sum = 0.0, ak = 1.0, c = 1.0;  // c = C(D,k)
+  for (int k = 0; k < D; ++k) {
+    sum += c * ak * pow_int(b, D - k);
+    ak *= a;
+    c = c * (double)(D - k) / (double)(k + 1);
+  }
+  return nR * sum / pow_int(1.0 - r, D);
+}
+
+// Eq. error_bound_far_to_local with r < 1/2:
+// |R|/(1-2r)^{2D} sum_{k<D} C(D,k) ((1-(2r)^p)^2)^k ((2r)^p(2-(2r)^p)/sqrt(p!))^{D-k}.
+__device__ inline double bound_f2l(double nR, int D, double r, int p) {
+  const double q = pow_int(2.0 * r, p);
+  const double a = (1.0 - q) * (1.0 - q);
+  const double b = q * (2.0 - q) / sqrt(fact_d(p));
+  double sum = 0.0, ak = 1.0, c = 1.0;
+  for (int k = 0; k < D; ++k) {
+    sum += c * ak * pow_int(b, D - k);
+    ak *= a;
+    c = c * (double)(D - k) / (double)(k + 1);
+  }
+  return nR * sum / pow_int(1.0 - 2.0 * r, 2 * D);
+}
+
+// Rounding allowance for an order-p expansion evaluated in float32.  Each
+// term of the truncated series is bounded (Szasz's inequality, as in the
+// proofs of the truncation lemmas) so that the sum of absolute terms is at
+// most |R| * S with S = ((1-r^p)/(1-r))^D (far field, local) or
+// ((1-(2r)^p)/(1-2r))^{2D} (far to local); float32 evaluation, the
+// float32 local-expansion read-out and the coefficient conversions add at
+// most c * u * |R| * S with u = 2^-24 and c = 2 (2 p^D + 6D + 16).
+__device__ inline double fp_allowance(double nR, int D, double r_eff, int p, int pow2) {
+  const double u = 5.9604644775390625e-08;
+  const double g = (1.0 - pow_int(r_eff, p)) / (1.0 - r_eff);
+  const double S = pow_int(g, pow2 * D);
+  const double c = 2.0 * (2.0 * pow_int((double)p, D) + 6.0 * D + 16.0);
+  return c * u * nR * S;
+}
+
+// ------------------------------------------------------------- atomics
+__device__ __forceinline__ void atomic_min_f(float* a, float v) {
+  if (v >= 0.f)
+    atomicMin(reinterpret_cast<int*>(a), __float_as_int(v));
+  else
+    atomicMax(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_f(float* a, float v) {
+  if (v >= 0.f)
+    atomicMax(reinterpret_cast<int*>(a), __float_as_int(v));
+  else
+    atomicMin(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
+}
+
+// Packed work item of the traversal: query node, reference node,
+// bandwidth index and flags (bit 0: q was just split from its parent).
+struct Pair {
+  int q, r, h, flags;
+};
+// Summary action item: node pair, bandwidth index and expansion order.
+struct Action {
+  int q, r, h, p;
+};
+
+enum : int { kFlagSplitQ = 1 };
+
+// Device status word bits (read back once per call).
+enum : int {
+  kStNonFinite = 1,   // a coordinate was NaN/Inf
+  kStOverflow = 2,    // a work list ran out of room (retry with more)
+};
+
+}  // namespace dfgt

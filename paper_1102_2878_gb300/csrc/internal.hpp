@@ -1,0 +1,150 @@
+// internal.hpp -- host-side structures of the DFGT library (not part of the ABI).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "dfgt.h"
+
+// Grow-only device buffer.  Reallocation happens only between calls (the
+// owning call has synchronised its stream), so old contents are dropped.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t want = need + need / 4 + 256;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// Counters read back after each traversal round (one pinned copy).
+struct RoundCounters {
+  int n_next;          // pairs written to the next frontier
+  int status;          // kSt* bits
+  int n_far, n_loc, n_f2l, n_base;   // cumulative list lengths
+  unsigned long long n_prune;        // cumulative prune count
+  unsigned long long base_inter;     // cumulative sum |Q||R| over base pairs
+};
+
+struct dfgt_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  long long launches = 0;
+  // cached workspace
+  DevBuf scan_tmp;
+  DevBuf counters;       // RoundCounters on the device
+  DevBuf hvals;          // bandwidths
+  DevBuf frontier[2];    // Pair
+  DevBuf list_far, list_loc, list_f2l, list_base;  // Action / Pair
+  DevBuf node_state;     // u64 inherited/decided/incr/lbsum
+  DevBuf lmom;           // double local moments [nh][nn][P]
+  DevBuf pused;          // int [nh][nn]
+  DevBuf gacc;           // double [nh][nq]
+  DevBuf io_q, io_r, io_g;  // dfgt_kde_host staging
+  size_t cap_frontier = 1 << 20;
+  size_t cap_lists = 1 << 20;
+  RoundCounters* h_counters = nullptr;  // pinned
+  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+struct dfgt_tree {
+  int device = 0;
+  int64_t n = 0;
+  int d = 0, dp = 0, leaf = 32, pm = 1, P = 1, p_limit = 1;
+  double eps_fp = 2e-5;
+  int nn = 0, nleaves = 0, depth = 0;
+  std::vector<int> lvl_off;  // nodes of level k are [lvl_off[k], lvl_off[k+1])
+  float* pts = nullptr;
+  int* perm = nullptr;
+  float* lo = nullptr;
+  float* hi = nullptr;
+  int* beg = nullptr;
+  int* cnt = nullptr;
+  int* left = nullptr;
+  int* parent = nullptr;
+  int* leaf_of = nullptr;
+  double* mom = nullptr;
+  dfgt::TreeView view() const {
+    dfgt::TreeView v;
+    v.pts = pts; v.perm = perm; v.lo = lo; v.hi = hi; v.beg = beg; v.cnt = cnt;
+    v.left = left; v.parent = parent; v.leaf_of = leaf_of; v.mom = mom;
+    v.n = (int)n; v.d = d; v.dp = dp; v.nn = nn; v.pm = pm; v.P = P;
+    return v;
+  }
+};
+
+namespace dfgt {
+
+// scan.cu: exclusive prefix sum of n int32 values into out[0..n].
+cudaError_t scan_exclusive(const int* in, int* out, int n, DevBuf& tmp, cudaStream_t s,
+                           long long* launches);
+
+// bruteforce.cu
+cudaError_t launch_bruteforce(const float* q, int nq, const float* r, int nr, int d,
+                              const double* h_host, int nh, double* G, cudaStream_t s,
+                              long long* launches);
+
+// tree.cu: build the tree (points, nodes, raw moments) on ctx's stream.
+dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n, int d,
+                       const dfgt_opts* opts, dfgt_tree* t);
+void free_tree(dfgt_tree* t);
+
+// traverse.cu / actions.cu launchers
+struct TravBuffers {
+  u64* inherited;   // [nh][nnQ]
+  u64* decided;
+  u64* incr;
+  u64* lbsum;
+  double* L;        // [nh][nnQ][P]
+  int* pused;       // [nh][nnQ]
+  double* gacc;     // [nh][nq] (permuted order)
+  const double* h;  // [nh]
+  int nh;
+  double eps_eff;   // eps minus the float allowance for exact sums
+  double fix_scale; // 2^62 / |R|
+  int p_limit;
+};
+
+cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s);
+cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
+                      int nF, cudaStream_t s);
+cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                            const Pair* F, int nF, Pair* next, int cap_next, Action* far,
+                            Action* loc, Action* f2l, Pair* base, int cap_lists,
+                            RoundCounters* counters, cudaStream_t s);
+cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s);
+
+cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                        const Pair* list, int n, cudaStream_t s);
+cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                            const Action* list, int n, cudaStream_t s);
+cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                         const Action* list, int n, cudaStream_t s);
+cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                       const Action* list, int n, cudaStream_t s);
+cudaError_t launch_prune_apply(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                               const Pair* list, int n, cudaStream_t s);
+cudaError_t launch_l2l_level(const TreeView& Q, const TravBuffers& b, int a, int e,
+                             cudaStream_t s);
+cudaError_t launch_finalize(const TreeView& Q, const TravBuffers& b, double* G_out,
+                            cudaStream_t s);
+
+}  // namespace dfgt

@@ -1,0 +1,286 @@
+// traverse.cu -- level-synchronous dual-tree traversal (the DFGT recursion of
+// Section 3.6, one round per kernel sweep over a frontier of node pairs).
+//
+// Every round classifies all frontier pairs (Q, R, h) at once:
+//   * the distance-bound prune (the finite-difference approximation of the
+//     predecessor dual-tree method, used in the proof of Theorem 3.3):
+//     every query of Q gets |R|(K(d^l)+K(d^u))/2, error at most
+//     |R|(K(d^l)-K(d^u))/2;
+//   * otherwise ChooseBestMethod with FarFieldOrder, LocalAccumulationOrder
+//     and ConvertFarFieldToLocalOrder picks far-field evaluation (F), direct
+//     local accumulation (D) or far-to-local translation (T);
+//   * otherwise a leaf-leaf pair goes to the exact base case (DFGTBase) and
+//     any other pair is split into its child pairs for the next round.
+// Both approximations are accepted only if their error is at most
+// tau = eps |R| G^l(Q) / |R_total| (CanSummarize).  Summaries are only
+// listed here; the action kernels run once over the complete lists after
+// the traversal, since no decision depends on their results.
+//
+// Lower bound G^l(Q).  In a breadth-first order the exact base-case sums
+// of the depth-first recursion are not yet known when a pair is decided,
+// so G^l(Q) is built from the bounds delta^l = |R| K(d^u) of a partition
+// of the reference set: every pair already decided for Q or an ancestor of
+// Q, plus every pair of Q pending in this round.  Each such set of pairs
+// covers every reference point exactly once (Theorem 3.2), and each
+// delta^l is at most the true contribution of its reference node to any
+// query of Q, so the sum is a valid lower bound -- all that Theorem 3.3
+// needs.  Sums are kept in 64-bit fixed point (units of |R_total| 2^-62,
+// rounded down), so they are exact, order-independent and deterministic.
+#include "internal.hpp"
+
+namespace dfgt {
+namespace {
+
+constexpr int kT = 256;
+
+__device__ __forceinline__ u64 to_fix(double x, double scale) {
+  const double v = x * scale * (1.0 - 1e-14);
+  return v > 0.0 ? __double2ull_rz(v) : 0ull;
+}
+
+// Squared distance bounds of two boxes, Eqs. (6)-(7), and their largest sides.
+template <int D>
+__device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const TreeView& R, int r,
+                                             double& dl2, double& du2, double& sideQ,
+                                             double& sideR) {
+  const int d = D > 0 ? D : Q.d;
+  dl2 = du2 = sideQ = sideR = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double ql = Q.lo[(size_t)q * d + k], qu = Q.hi[(size_t)q * d + k];
+    const double rl = R.lo[(size_t)r * d + k], ru = R.hi[(size_t)r * d + k];
+    // (x + |x|)/2 summed over the two orderings = max(rl-qu, ql-ru, 0)
+    const double gap = fmax(0.0, fmax(rl - qu, ql - ru));
+    dl2 += gap * gap;
+    const double far = fmax(ru - ql, qu - rl);
+    du2 += far * far;
+    sideQ = fmax(sideQ, qu - ql);
+    sideR = fmax(sideR, ru - rl);
+  }
+}
+
+// FarFieldOrder / LocalAccumulationOrder: least p <= plim whose truncation
+// bound plus float32 rounding allowance is <= tau; 0 = none (r >= 1).
+__device__ int order_ff(double r, double nR, int D, double tau, int plim) {
+  if (!(r < 1.0)) return 0;
+  for (int p = 1; p <= plim; ++p)
+    if (bound_farfield(nR, D, r, p) + fp_allowance(nR, D, r, p, 1) <= tau) return p;
+  return 0;
+}
+
+// ConvertFarFieldToLocalOrder; 0 = none (r >= 1/2).
+__device__ int order_t(double r, double nR, int D, double tau, int plim) {
+  if (!(r < 0.5)) return 0;
+  for (int p = 1; p <= plim; ++p)
+    if (bound_f2l(nR, D, r, p) + fp_allowance(nR, D, 2.0 * r, p, 2) <= tau) return p;
+  return 0;
+}
+
+// All 32 lanes call this; returns the first slot of this lane's n items.
+__device__ __forceinline__ int warp_alloc(int* counter, int n) {
+  const int lane = threadIdx.x & 31;
+  int incl = n;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - n;
+}
+
+__device__ __forceinline__ void warp_add_u64(unsigned long long* counter, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(counter, v);
+}
+
+__global__ void k_fold(u64* __restrict__ decided, u64* __restrict__ incr, u64* __restrict__ lbsum,
+                       int total) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  decided[i] += incr[i];
+  incr[i] = 0;
+  lbsum[i] = 0;
+}
+
+__global__ void k_init_frontier(Pair* F, int nh) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nh) F[i] = Pair{0, 0, i, 0};
+}
+
+// Pending lower bounds: inherit the decided bound of a just-split parent,
+// then add delta^l of every pending pair of the node.
+template <int D>
+__global__ void __launch_bounds__(kT) k_lb(TreeView Q, TreeView R, TravBuffers b,
+                                           const Pair* __restrict__ F, int nF) {
+  const int i = blockIdx.x * kT + threadIdx.x;
+  if (i >= nF) return;
+  const Pair pr = F[i];
+  const size_t hq = (size_t)pr.h * Q.nn + pr.q;
+  if (pr.flags & kFlagSplitQ) {
+    const size_t hp = (size_t)pr.h * Q.nn + Q.parent[pr.q];
+    b.inherited[hq] = b.inherited[hp] + b.decided[hp];  // same value from every pair of q
+  }
+  double dl2, du2, sq, sr;
+  box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
+  const double h = b.h[pr.h];
+  const double delta_l = (double)R.cnt[pr.r] * exp(-du2 / (2.0 * h * h));
+  const u64 f = to_fix(delta_l, b.fix_scale);
+  if (f) atomicAdd(&b.lbsum[hq], f);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuffers b,
+                                                 const Pair* __restrict__ F, int nF,
+                                                 Pair* __restrict__ next, int cap_next,
+                                                 Action* __restrict__ far, Action* __restrict__ loc,
+                                                 Action* __restrict__ f2l, Pair* __restrict__ base,
+                                                 int cap_lists, RoundCounters* ctr) {
+  const int d = D > 0 ? D : Q.d;
+  const int P = Q.P;
+  const int stride = gridDim.x * kT;
+  for (int i0 = blockIdx.x * kT; i0 < nF; i0 += stride) {
+    const int i = i0 + threadIdx.x;
+    // kind: -1 none, 0 prune, 1 F, 2 D, 3 T, 4 base, 5 recurse
+    int kind = -1, order = 0, nchild = 0;
+    Pair pr{0, 0, 0, 0};
+    unsigned long long inter = 0;
+    if (i < nF) {
+      pr = F[i];
+      const size_t hq = (size_t)pr.h * Q.nn + pr.q;
+      const double nQ = (double)Q.cnt[pr.q], nR = (double)R.cnt[pr.r];
+      const double h = b.h[pr.h];
+      const double inv2h2 = 1.0 / (2.0 * h * h);
+      double dl2, du2, sideQ, sideR;
+      box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
+      const double Kl = exp(-dl2 * inv2h2), Ku = exp(-du2 * inv2h2);
+      const double delta_l = nR * Ku;
+      const u64 lbf = b.inherited[hq] + b.decided[hq] + b.lbsum[hq];
+      const double Gl = (double)lbf / b.fix_scale;
+      const double tau = b.eps_eff * nR * Gl / (double)R.n;
+      if (0.5 * nR * (Kl - Ku) <= tau) {
+        kind = 0;
+        atomicAdd(&b.L[hq * P], 0.5 * nR * (Kl + Ku));
+        atomicMax(&b.pused[hq], 1);
+      } else {
+        int pF = 0, pD = 0, pT = 0;
+        if (tau > 0.0) {
+          pF = order_ff(sideR / (2.0 * h), nR, d, tau, b.p_limit);
+          pD = order_ff(sideQ / (2.0 * h), nR, d, tau, b.p_limit);
+          pT = order_t(fmax(sideQ, sideR) / (2.0 * h), nR, d, tau, b.p_limit);
+        }
+        // ChooseBestMethod with c_F = D N_Q p^D, c_D = D N_R p^D,
+        // c_T = D p^{2D}, c_E = D N_Q N_R; ties go F, D, T, E.
+        const double cF = pF ? d * nQ * pow((double)pF, (double)d) : INFINITY;
+        const double cD = pD ? d * nR * pow((double)pD, (double)d) : INFINITY;
+        const double cT = pT ? d * pow((double)pT, 2.0 * d) : INFINITY;
+        const double cE = d * nQ * nR;
+        const double m = fmin(fmin(cF, cD), fmin(cT, cE));
+        if (pF && cF == m) { kind = 1; order = pF; }
+        else if (pD && cD == m) { kind = 2; order = pD; }
+        else if (pT && cT == m) { kind = 3; order = pT; }
+        else {
+          const int ql = Q.left[pr.q], rl = R.left[pr.r];
+          if (ql < 0 && rl < 0) { kind = 4; inter = (unsigned long long)(nQ * nR); }
+          else { kind = 5; nchild = (ql >= 0 && rl >= 0) ? 4 : 2; }
+        }
+      }
+      if (kind <= 4) {
+        const u64 f = to_fix(delta_l, b.fix_scale);
+        if (f) atomicAdd(&b.incr[hq], f);
+      }
+    }
+    // warp-aggregated appends (all lanes take part)
+    {
+      const int s0 = warp_alloc(&ctr->n_next, nchild);
+      if (nchild) {
+        if (s0 + nchild <= cap_next) {
+          const int ql = Q.left[pr.q], rl = R.left[pr.r];
+          if (ql < 0) {
+            next[s0] = Pair{pr.q, rl, pr.h, 0};
+            next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
+          } else if (rl < 0) {
+            next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
+            next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
+          } else {
+            next[s0] = Pair{ql, rl, pr.h, kFlagSplitQ};
+            next[s0 + 1] = Pair{ql, rl + 1, pr.h, kFlagSplitQ};
+            next[s0 + 2] = Pair{ql + 1, rl, pr.h, kFlagSplitQ};
+            next[s0 + 3] = Pair{ql + 1, rl + 1, pr.h, kFlagSplitQ};
+          }
+        } else {
+          atomicOr(&ctr->status, kStOverflow);
+        }
+      }
+    }
+    {
+      const int s1 = warp_alloc(&ctr->n_far, kind == 1);
+      if (kind == 1) { if (s1 < cap_lists) far[s1] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
+      const int s2 = warp_alloc(&ctr->n_loc, kind == 2);
+      if (kind == 2) { if (s2 < cap_lists) loc[s2] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
+      const int s3 = warp_alloc(&ctr->n_f2l, kind == 3);
+      if (kind == 3) { if (s3 < cap_lists) f2l[s3] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
+      const int s4 = warp_alloc(&ctr->n_base, kind == 4);
+      if (kind == 4) { if (s4 < cap_lists) base[s4] = Pair{pr.q, pr.r, pr.h, 0}; else atomicOr(&ctr->status, kStOverflow); }
+    }
+    warp_add_u64(&ctr->n_prune, kind == 0 ? 1ull : 0ull);
+    warp_add_u64(&ctr->base_inter, inter);
+  }
+}
+
+template <int D>
+cudaError_t classify_d(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
+                       int nF, Pair* next, int cap_next, Action* far, Action* loc, Action* f2l,
+                       Pair* base, int cap_lists, RoundCounters* ctr, cudaStream_t s) {
+  int grid = (nF + kT - 1) / kT;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_classify<D><<<grid, kT, 0, s>>>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base,
+                                     cap_lists, ctr);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s) {
+  const int total = b.nh * nnQ;
+  k_fold<<<(total + kT - 1) / kT, kT, 0, s>>>(b.decided, b.incr, b.lbsum, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s) {
+  k_init_frontier<<<(nh + kT - 1) / kT, kT, 0, s>>>(F, nh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
+                      int nF, cudaStream_t s) {
+  const int grid = (nF + kT - 1) / kT;
+  switch (Q.d) {
+    case 1: k_lb<1><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
+    case 2: k_lb<2><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
+    case 3: k_lb<3><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
+    case 4: k_lb<4><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
+    case 5: k_lb<5><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
+    default: k_lb<0><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                            const Pair* F, int nF, Pair* next, int cap_next, Action* far,
+                            Action* loc, Action* f2l, Pair* base, int cap_lists,
+                            RoundCounters* ctr, cudaStream_t s) {
+  switch (Q.d) {
+    case 1: return classify_d<1>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 2: return classify_d<2>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 3: return classify_d<3>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 4: return classify_d<4>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 5: return classify_d<5>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    default: return classify_d<0>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+  }
+}
+
+}  // namespace dfgt

@@ -1,0 +1,527 @@
+// tree.cu -- device build of the mid-point kd-tree (Algorithm 2, BuildKdTree)
+// and of the raw far-field moments of every node (Eq. far_field_moments at
+// the leaves, the far-to-far translation of Lemma 3.5 upward).
+//
+// The build is level-synchronous: every level computes the tight bounding
+// box of each of its nodes, splits the widest dimension at the box
+// midpoint when the node holds more points than the leaf threshold, and
+// stably partitions the points of every split node (x[sd] <= sc to the
+// left) with one device-wide prefix sum.  Nodes are numbered level by
+// level, so each level is a contiguous index range and the two children of
+// a node are adjacent.  A split that would leave one side empty (all
+// points equal along the widest side, or a midpoint that rounds onto the
+// upper bound) turns the node into a leaf.
+//
+// Moments are kept unscaled, m_alpha = sum_r (r-c)^alpha / alpha!, in
+// float64 about the box center c; the bandwidth scaling (2h^2)^(-|alpha|/2)
+// of Eq. far_field_moments is applied where they are used, so one table
+// serves every bandwidth.
+#include <algorithm>
+#include <cstring>
+
+#include "internal.hpp"
+
+namespace dfgt {
+namespace {
+
+constexpr int kT = 256;
+
+__global__ void k_pad_points(const float* __restrict__ in, int n, int d, int dp,
+                             float* __restrict__ out, int* __restrict__ perm,
+                             int* __restrict__ pnode, int* __restrict__ status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool bad = false;
+  for (int k = 0; k < dp; ++k) {
+    float v = k < d ? in[(size_t)i * d + k] : 0.f;
+    if (!isfinite(v)) bad = true;
+    out[(size_t)i * dp + k] = v;
+  }
+  perm[i] = i;
+  pnode[i] = 0;
+  if (bad) atomicOr(status, kStNonFinite);
+}
+
+__global__ void k_init_nodes(int a, int e, int d, float* lo, float* hi) {
+  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= e) return;
+  for (int k = 0; k < d; ++k) {
+    lo[(size_t)j * d + k] = INFINITY;
+    hi[(size_t)j * d + k] = -INFINITY;
+  }
+}
+
+// Tight bounding boxes of the nodes of the current level (min/max over each
+// node's points).  Points are contiguous per node, so most blocks see one
+// node and reduce in shared memory before one atomic per coordinate.
+__global__ void __launch_bounds__(kT) k_bbox(const float* __restrict__ pts, int n, int d, int dp,
+                                             const int* __restrict__ pnode, float* lo, float* hi) {
+  __shared__ int s_nd;
+  __shared__ float s_min[kT / 32], s_max[kT / 32];
+  const int i = blockIdx.x * kT + threadIdx.x;
+  const int nd = i < n ? pnode[i] : -1;
+  if (threadIdx.x == 0) s_nd = nd;
+  __syncthreads();
+  const bool uniform = __syncthreads_and(nd == s_nd);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (uniform) {
+    if (nd < 0) return;
+    for (int k = 0; k < d; ++k) {
+      float v = pts[(size_t)i * dp + k];
+      float mn = v, mx = v;
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (lane == 0) { s_min[wid] = mn; s_max[wid] = mx; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 1; w < kT / 32; ++w) { mn = fminf(mn, s_min[w]); mx = fmaxf(mx, s_max[w]); }
+        atomic_min_f(&lo[(size_t)nd * d + k], mn);
+        atomic_max_f(&hi[(size_t)nd * d + k], mx);
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  // every lane of the warp is still present here (no lane has returned)
+  const unsigned peers = __match_any_sync(0xffffffffu, nd);
+  if (nd < 0) return;
+  const int leader = __ffs(peers) - 1;
+  for (int k = 0; k < d; ++k) {
+    float v = pts[(size_t)i * dp + k];
+    if (peers == 0xffffffffu) {
+      float mn = v, mx = v;
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (lane == leader) {
+        atomic_min_f(&lo[(size_t)nd * d + k], mn);
+        atomic_max_f(&hi[(size_t)nd * d + k], mx);
+      }
+    } else {
+      atomic_min_f(&lo[(size_t)nd * d + k], v);
+      atomic_max_f(&hi[(size_t)nd * d + k], v);
+    }
+  }
+}
+
+// Split decision of each node of the level: widest side sd and its box
+// midpoint sc; a node splits only if it holds more than `leaf` points and
+// its box has positive extent.
+__global__ void k_split_decide(int a, int e, int d, int leaf, const int* __restrict__ cnt,
+                               const float* __restrict__ lo, const float* __restrict__ hi,
+                               int* __restrict__ want, int* __restrict__ sd_out,
+                               float* __restrict__ sc_out) {
+  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= e) return;
+  int sd = 0;
+  float ext = hi[(size_t)j * d] - lo[(size_t)j * d];
+  for (int k = 1; k < d; ++k) {
+    float x = hi[(size_t)j * d + k] - lo[(size_t)j * d + k];
+    if (x > ext) { ext = x; sd = k; }
+  }
+  const int w = (cnt[j] > leaf && ext > 0.f) ? 1 : 0;
+  want[j - a] = w;
+  sd_out[j - a] = sd;
+  sc_out[j - a] = 0.5f * (lo[(size_t)j * d + sd] + hi[(size_t)j * d + sd]);
+}
+
+__global__ void k_flag_left(const float* __restrict__ pts, int n, int dp, int a,
+                            const int* __restrict__ pnode, const int* __restrict__ want,
+                            const int* __restrict__ sd, const float* __restrict__ sc,
+                            int* __restrict__ flag) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nd = pnode[i];
+  int f = 0;
+  if (nd >= 0 && want[nd - a]) f = pts[(size_t)i * dp + sd[nd - a]] <= sc[nd - a] ? 1 : 0;
+  flag[i] = f;
+}
+
+__global__ void k_node_finalize(int a, int e, const int* __restrict__ beg,
+                                const int* __restrict__ cnt, const int* __restrict__ want,
+                                const int* __restrict__ leftpos, int* __restrict__ split,
+                                int* __restrict__ nleft) {
+  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= e) return;
+  const int b = beg[j], c = cnt[j];
+  const int nl = leftpos[b + c] - leftpos[b];
+  split[j - a] = (want[j - a] && nl > 0 && nl < c) ? 1 : 0;
+  nleft[j - a] = nl;
+}
+
+__global__ void k_make_children(int a, int e, int level, int d, const int* __restrict__ split,
+                                const int* __restrict__ soff, const int* __restrict__ nleft,
+                                int* beg, int* cnt, int* left, int* parent, float* lo,
+                                float* hi) {
+  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= e) return;
+  if (!split[j - a]) {
+    left[j] = -1;
+    return;
+  }
+  const int c0 = e + 2 * soff[j - a];
+  const int nl = nleft[j - a];
+  left[j] = c0;
+  beg[c0] = beg[j];
+  cnt[c0] = nl;
+  beg[c0 + 1] = beg[j] + nl;
+  cnt[c0 + 1] = cnt[j] - nl;
+  parent[c0] = parent[c0 + 1] = j;
+  left[c0] = left[c0 + 1] = -1;
+  for (int k = 0; k < d; ++k) {
+    lo[(size_t)c0 * d + k] = lo[(size_t)(c0 + 1) * d + k] = INFINITY;
+    hi[(size_t)c0 * d + k] = hi[(size_t)(c0 + 1) * d + k] = -INFINITY;
+  }
+  (void)level;
+}
+
+__global__ void k_scatter(int n, int dp, int a, const float* __restrict__ pin,
+                          const int* __restrict__ perm_in, const int* __restrict__ pnode_in,
+                          const int* __restrict__ flag, const int* __restrict__ leftpos,
+                          const int* __restrict__ beg, const int* __restrict__ left,
+                          const int* __restrict__ nleft, float* __restrict__ pout,
+                          int* __restrict__ perm_out, int* __restrict__ pnode_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int nd = pnode_in[i];
+  int dst = i, child = -1;
+  if (nd >= 0 && left[nd] >= 0) {
+    const int b0 = beg[nd];
+    const int lrank = leftpos[i] - leftpos[b0];
+    if (flag[i]) {
+      dst = b0 + lrank;
+      child = left[nd];
+    } else {
+      dst = b0 + nleft[nd - a] + (i - b0 - lrank);
+      child = left[nd] + 1;
+    }
+  }
+  for (int k = 0; k < dp; ++k) pout[(size_t)dst * dp + k] = pin[(size_t)i * dp + k];
+  perm_out[dst] = perm_in[i];
+  pnode_out[dst] = child;
+}
+
+__global__ void k_leaf_of(int nn, const int* __restrict__ beg, const int* __restrict__ cnt,
+                          const int* __restrict__ left, int* __restrict__ leaf_of) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nn || left[w] >= 0) return;
+  for (int i = lane; i < cnt[w]; i += 32) leaf_of[beg[w] + i] = w;
+}
+
+// ---------------------------------------------------------------- moments
+// alpha digit of coefficient position idx (radix PM, last dimension least
+// significant), matching the linear layout of the paper's appendix.
+template <int D, int PM>
+__device__ __forceinline__ int digit(int idx, int dd) {
+  int v = idx;
+  for (int k = D - 1; k > dd; --k) v /= PM;
+  return v % PM;
+}
+
+// Leaf moments (AccumulateFarFieldMoment): lane per coefficient position,
+// loop over the leaf's points, float64.
+template <int D>
+__global__ void k_leaf_moments(TreeView t, double* __restrict__ mom) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= t.nn || t.left[w] >= 0) return;
+  double c[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = 0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
+  const int b = t.beg[w], n = t.cnt[w];
+  for (int idx = lane; idx < P; idx += 32) {
+    int al[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) al[k] = digit<D, PM>(idx, k);
+    double acc = 0.0;
+    for (int j = 0; j < n; ++j) {
+      double term = 1.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) term *= pow_int((double)t.pts[(size_t)(b + j) * t.dp + k] - c[k], al[k]);
+      acc += term;
+    }
+    double f = 1.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) f *= fact_d(al[k]);
+    mom[(size_t)w * P + idx] = acc / f;
+  }
+}
+
+// Internal moments of one level by the far-to-far translation (Lemma 3.5,
+// Eq. far_to_far_translation, exact for gamma < p) of both children:
+// m_gamma(c') = sum_{alpha<=gamma} m_alpha(c_child) (c_child - c')^{gamma-alpha}/(gamma-alpha)!.
+template <int D>
+__global__ void k_f2f_level(TreeView t, int a, int e, double* __restrict__ mom) {
+  constexpr int PM = pmax_of(D);
+  constexpr int P = ipow_c(PM, D);
+  const int w = a + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= e || t.left[w] < 0) return;
+  double c[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = 0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
+  double acc[(P + 31) / 32];
+#pragma unroll
+  for (int s = 0; s < (P + 31) / 32; ++s) acc[s] = 0.0;
+  for (int ch = 0; ch < 2; ++ch) {
+    const int cn = t.left[w] + ch;
+    double tab[D][PM];  // (c_child - c')^e / e!
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const double x = 0.5 * ((double)t.lo[(size_t)cn * D + k] + (double)t.hi[(size_t)cn * D + k]) - c[k];
+      double v = 1.0;
+#pragma unroll
+      for (int q = 0; q < PM; ++q) {
+        tab[k][q] = v;
+        v = v * x / (double)(q + 1);
+      }
+    }
+    const double* mc = mom + (size_t)cn * P;
+#pragma unroll
+    for (int s = 0; s < (P + 31) / 32; ++s) {
+      const int idx = lane + 32 * s;
+      if (idx >= P) break;
+      int g[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) g[k] = digit<D, PM>(idx, k);
+      double sum = 0.0;
+      for (int j = 0; j < P; ++j) {
+        double term = mc[j];
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const int ak = digit<D, PM>(j, k);
+          if (ak > g[k]) ok = false;
+          else term *= tab[k][g[k] - ak];
+        }
+        if (ok) sum += term;
+      }
+      acc[s] += sum;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < (P + 31) / 32; ++s) {
+    const int idx = lane + 32 * s;
+    if (idx < P) mom[(size_t)w * P + idx] = acc[s];
+  }
+}
+
+// D >= 6: p_max = 1, the only moment is m_0 = |R|.
+__global__ void k_count_moments(TreeView t, double* __restrict__ mom) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < t.nn) mom[j] = (double)t.cnt[j];
+}
+
+template <int D>
+cudaError_t moments_d(dfgt_tree* t, cudaStream_t s, long long* launches) {
+  TreeView v = t->view();
+  const int blocks = (int)(((size_t)t->nn * 32 + kT - 1) / kT);
+  k_leaf_moments<D><<<blocks, kT, 0, s>>>(v, t->mom);
+  ++*launches;
+  for (int lev = t->depth - 2; lev >= 0; --lev) {
+    const int a = t->lvl_off[lev], e = t->lvl_off[lev + 1];
+    const int nb = (int)(((size_t)(e - a) * 32 + kT - 1) / kT);
+    k_f2f_level<D><<<nb, kT, 0, s>>>(v, a, e, t->mom);
+    ++*launches;
+  }
+  return cudaGetLastError();
+}
+
+struct Grow {
+  // grow a device array keeping its first `keep` elements
+  template <class T>
+  static cudaError_t arr(T** p, size_t keep, size_t newcap, cudaStream_t s) {
+    T* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, newcap * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (*p && keep) {
+      e = cudaMemcpyAsync(q, *p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) { cudaFree(q); return e; }
+      cudaStreamSynchronize(s);
+    }
+    if (*p) cudaFree(*p);
+    *p = q;
+    return cudaSuccess;
+  }
+};
+
+}  // namespace
+
+void free_tree(dfgt_tree* t) {
+  cudaFree(t->pts); cudaFree(t->perm); cudaFree(t->lo); cudaFree(t->hi);
+  cudaFree(t->beg); cudaFree(t->cnt); cudaFree(t->left); cudaFree(t->parent);
+  cudaFree(t->leaf_of); cudaFree(t->mom);
+  t->pts = nullptr; t->perm = nullptr; t->lo = t->hi = nullptr;
+  t->beg = t->cnt = t->left = t->parent = t->leaf_of = nullptr; t->mom = nullptr;
+}
+
+#define TRY(x)                                                   \
+  do {                                                           \
+    cudaError_t _e = (x);                                        \
+    if (_e != cudaSuccess) {                                     \
+      ctx->err = std::string(#x) + ": " + cudaGetErrorString(_e); \
+      goto fail;                                                 \
+    }                                                            \
+  } while (0)
+
+dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
+                       const dfgt_opts* opts, dfgt_tree* t) {
+  cudaStream_t s = ctx->stream;
+  long long* L = &ctx->launches;
+  const int n = (int)n64;
+  t->n = n64;
+  t->d = d;
+  t->dp = padded_dim(d);
+  t->leaf = (opts && opts->leaf_size > 0) ? opts->leaf_size : 32;
+  t->pm = pmax_of(d);
+  t->P = ipow_c(t->pm, d);
+  t->p_limit = (opts && opts->p_max > 0) ? std::min(opts->p_max, t->pm) : t->pm;
+  t->eps_fp = (opts && opts->eps_fp > 0) ? opts->eps_fp : 2e-5;
+  t->lvl_off.assign(1, 0);
+
+  // level-build scratch: two point buffers, per-point node ids, flags,
+  // prefix sums, per-level node temporaries
+  float* pbuf[2] = {nullptr, nullptr};
+  int* perm2[2] = {nullptr, nullptr};
+  int* pnode[2] = {nullptr, nullptr};
+  int *flag = nullptr, *leftpos = nullptr, *want = nullptr, *sd = nullptr, *split = nullptr,
+      *soff = nullptr, *nleft = nullptr, *status = nullptr;
+  float* sc = nullptr;
+  size_t cap = 0;
+  int cur = 0, a = 0, e = 1, level = 0;
+  int h_status = 0;
+  dfgt_status rc = DFGT_ECUDA;
+
+  const size_t np = (size_t)n;
+  TRY(cudaMalloc(&pbuf[0], np * t->dp * sizeof(float)));
+  TRY(cudaMalloc(&pbuf[1], np * t->dp * sizeof(float)));
+  TRY(cudaMalloc(&perm2[0], np * sizeof(int)));
+  TRY(cudaMalloc(&perm2[1], np * sizeof(int)));
+  TRY(cudaMalloc(&pnode[0], np * sizeof(int)));
+  TRY(cudaMalloc(&pnode[1], np * sizeof(int)));
+  TRY(cudaMalloc(&flag, np * sizeof(int)));
+  TRY(cudaMalloc(&leftpos, (np + 1) * sizeof(int)));
+  TRY(cudaMalloc(&want, (np + 1) * sizeof(int)));
+  TRY(cudaMalloc(&sd, (np + 1) * sizeof(int)));
+  TRY(cudaMalloc(&sc, (np + 1) * sizeof(float)));
+  TRY(cudaMalloc(&split, (np + 1) * sizeof(int)));
+  TRY(cudaMalloc(&soff, (np + 2) * sizeof(int)));
+  TRY(cudaMalloc(&nleft, (np + 1) * sizeof(int)));
+  TRY(cudaMalloc(&status, sizeof(int)));
+  TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
+
+  cap = std::max<size_t>(64, 4 * np / std::max(1, t->leaf) + 16);
+  TRY(cudaMalloc(&t->lo, cap * d * sizeof(float)));
+  TRY(cudaMalloc(&t->hi, cap * d * sizeof(float)));
+  TRY(cudaMalloc(&t->beg, cap * sizeof(int)));
+  TRY(cudaMalloc(&t->cnt, cap * sizeof(int)));
+  TRY(cudaMalloc(&t->left, cap * sizeof(int)));
+  TRY(cudaMalloc(&t->parent, cap * sizeof(int)));
+
+  k_pad_points<<<(n + kT - 1) / kT, kT, 0, s>>>(pts_dev, n, d, t->dp, pbuf[0], perm2[0], pnode[0], status);
+  ++*L;
+  {
+    const int zero = 0, minus1 = -1;
+    TRY(cudaMemcpyAsync(t->beg, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(t->cnt, &n, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(t->parent, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(t->left, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  k_init_nodes<<<1, 32, 0, s>>>(0, 1, d, t->lo, t->hi);
+  ++*L;
+  TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  if (h_status & kStNonFinite) {
+    ctx->err = "dfgt_build: non-finite coordinate";
+    rc = DFGT_EINVAL;
+    goto fail;
+  }
+
+  for (level = 0; level < 128; ++level) {
+    const int nl = e - a;
+    const int gp = (n + kT - 1) / kT, gn = (nl + kT - 1) / kT;
+    k_bbox<<<gp, kT, 0, s>>>(pbuf[cur], n, d, t->dp, pnode[cur], t->lo, t->hi);
+    k_split_decide<<<gn, kT, 0, s>>>(a, e, d, t->leaf, t->cnt, t->lo, t->hi, want, sd, sc);
+    k_flag_left<<<gp, kT, 0, s>>>(pbuf[cur], n, t->dp, a, pnode[cur], want, sd, sc, flag);
+    *L += 3;
+    TRY(cudaGetLastError());
+    TRY(scan_exclusive(flag, leftpos, n, ctx->scan_tmp, s, L));
+    k_node_finalize<<<gn, kT, 0, s>>>(a, e, t->beg, t->cnt, want, leftpos, split, nleft);
+    ++*L;
+    TRY(cudaGetLastError());
+    TRY(scan_exclusive(split, soff, nl, ctx->scan_tmp, s, L));
+    int nsplit = 0;
+    TRY(cudaMemcpyAsync(&nsplit, soff + nl, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    const size_t need = (size_t)e + 2 * (size_t)nsplit;
+    if (need > cap) {
+      size_t nc = std::max(need, cap * 2);
+      TRY(Grow::arr(&t->lo, (size_t)e * d, nc * d, s));
+      TRY(Grow::arr(&t->hi, (size_t)e * d, nc * d, s));
+      TRY(Grow::arr(&t->beg, (size_t)e, nc, s));
+      TRY(Grow::arr(&t->cnt, (size_t)e, nc, s));
+      TRY(Grow::arr(&t->left, (size_t)e, nc, s));
+      TRY(Grow::arr(&t->parent, (size_t)e, nc, s));
+      cap = nc;
+    }
+    k_make_children<<<gn, kT, 0, s>>>(a, e, level, d, split, soff, nleft, t->beg, t->cnt,
+                                      t->left, t->parent, t->lo, t->hi);
+    k_scatter<<<gp, kT, 0, s>>>(n, t->dp, a, pbuf[cur], perm2[cur], pnode[cur], flag, leftpos,
+                                t->beg, t->left, nleft, pbuf[cur ^ 1], perm2[cur ^ 1], pnode[cur ^ 1]);
+    *L += 2;
+    TRY(cudaGetLastError());
+    cur ^= 1;
+    t->lvl_off.push_back(e);
+    if (nsplit == 0) break;
+    a = e;
+    e = (int)need;
+  }
+  if (level >= 128) {
+    ctx->err = "dfgt_build: more than 128 tree levels";
+    rc = DFGT_ETIMEOUT;
+    goto fail;
+  }
+  t->nn = t->lvl_off.back();
+  t->depth = (int)t->lvl_off.size() - 1;
+  t->pts = pbuf[cur];
+  pbuf[cur] = nullptr;
+  t->perm = perm2[cur];
+  perm2[cur] = nullptr;
+  TRY(cudaMalloc(&t->leaf_of, np * sizeof(int)));
+  TRY(cudaMalloc(&t->mom, (size_t)t->nn * t->P * sizeof(double)));
+  k_leaf_of<<<(int)(((size_t)t->nn * 32 + kT - 1) / kT), kT, 0, s>>>(t->nn, t->beg, t->cnt, t->left, t->leaf_of);
+  ++*L;
+  switch (d) {
+    case 1: TRY(moments_d<1>(t, s, L)); break;
+    case 2: TRY(moments_d<2>(t, s, L)); break;
+    case 3: TRY(moments_d<3>(t, s, L)); break;
+    case 4: TRY(moments_d<4>(t, s, L)); break;
+    case 5: TRY(moments_d<5>(t, s, L)); break;
+    default:
+      k_count_moments<<<(t->nn + kT - 1) / kT, kT, 0, s>>>(t->view(), t->mom);
+      ++*L;
+      TRY(cudaGetLastError());
+  }
+  {
+    // count leaves on the host side from the level structure
+    std::vector<int> left_h(t->nn);
+    TRY(cudaMemcpyAsync(left_h.data(), t->left, t->nn * sizeof(int), cudaMemcpyDeviceToHost, s));
+    TRY(cudaStreamSynchronize(s));
+    t->nleaves = (int)std::count(left_h.begin(), left_h.end(), -1);
+  }
+  rc = DFGT_OK;
+fail:
+  cudaFree(pbuf[0]); cudaFree(pbuf[1]); cudaFree(perm2[0]); cudaFree(perm2[1]);
+  cudaFree(pnode[0]); cudaFree(pnode[1]); cudaFree(flag); cudaFree(leftpos); cudaFree(want);
+  cudaFree(sd); cudaFree(sc); cudaFree(split); cudaFree(soff); cudaFree(nleft); cudaFree(status);
+  if (rc != DFGT_OK) free_tree(t);
+  return rc;
+}
+
+}  // namespace dfgt

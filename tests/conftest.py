@@ -28,3 +28,20 @@ def read_golden(name):
             if line and not line.startswith("#"):
                 rows.append([float(v) for v in line.split()])
     return rows
+
+
+@pytest.fixture(scope="session")
+def dev():
+    """The DFGT library on cuda:0 (GPU tests only)."""
+    import paper_1102_2878_gb300 as dfgt
+
+    dfgt.build()
+    ctx = dfgt.Context(0)
+    yield ctx
+    ctx.close()
+
+
+def to_cuda(x):
+    import torch
+
+    return torch.from_numpy(x).cuda()

@@ -1,0 +1,37 @@
+"""Failures come back as status codes (no abort, no device fault)."""
+import numpy as np
+import pytest
+
+import paper_1102_2878_gb300 as dfgt
+from conftest import to_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_non_finite_coordinates_rejected(dev):
+    x = np.random.default_rng(0).random((100, 3)).astype(np.float32)
+    x[17, 1] = np.nan
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.Tree(dev, to_cuda(x))
+    x[17, 1] = np.inf
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.Tree(dev, to_cuda(x))
+
+
+def test_bad_arguments_rejected(dev):
+    x = np.random.default_rng(1).random((100, 3)).astype(np.float32)
+    t = dfgt.Tree(dev, to_cuda(x))
+    for hs, eps in [([0.1], 0.0), ([0.1], 1.0), ([0.0], 1e-2), ([-1.0], 1e-2), ([np.inf], 1e-2),
+                    ([0.1], 1e-6)]:
+        with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+            dfgt.kde_sum(dev, t, t, hs, eps)
+    t2 = dfgt.Tree(dev, to_cuda(x[:, :2].copy()))
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.kde_sum(dev, t, t2, [0.1], 1e-2)
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.Tree(dev, to_cuda(x), leaf_size=100000)
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dev.set_capacity(0, 10)
+    # the context stays usable after rejected calls
+    G, _ = dfgt.kde_sum(dev, t, t, [0.1], 1e-2)
+    assert np.isfinite(G.cpu().numpy()).all()
