@@ -55,6 +55,9 @@ typedef struct {
                       8 for D=1); a smaller positive value lowers it */
   double eps_fp;   /* part of eps reserved for float32 rounding in exact sums;
                       0 -> 2e-5; must be < eps */
+  long long base_block; /* a node pair that no summary can take is summed exactly,
+                      without splitting further, once |Q| |R| <= base_block;
+                      0 -> 4 leaf_size^2, -1 -> only leaf pairs (as in DFGT) */
 } dfgt_opts;
 
 /* Work counters of one dfgt_sum call, summed over its bandwidths. */
@@ -68,14 +71,14 @@ typedef struct {
   long long base_interactions;  /* sum over base pairs of |Q_leaf| * |R_leaf| */
   long long kernel_launches;    /* kernels this call launched */
   int rounds;                   /* level-synchronous traversal rounds */
-  int overflow_retries;         /* times a work list was regrown and the call redone */
-  double ms_traverse;           /* device time of the traversal rounds */
-  double ms_actions;            /* device time of the F/D/T/base kernels */
+  int list_flushes;             /* times an action list was drained before the traversal ended */
+  double ms_traverse;           /* device time of the traversal rounds (with early list drains) */
+  double ms_actions;            /* device time of the final list drains */
   double ms_post;               /* device time of the downward pass and finalisation */
-  double ms_base;               /* device time of the base-case kernel (DFGTBase) */
-  double ms_farfield;           /* device time of the far-field evaluation kernel */
-  double ms_local;              /* device time of the direct local accumulation kernel */
-  double ms_f2l;                /* device time of the far-to-local translation kernel */
+  double ms_base;               /* device time of every base-case (DFGTBase) launch */
+  double ms_farfield;           /* device time of every far-field evaluation launch */
+  double ms_local;              /* device time of every direct local accumulation launch */
+  double ms_f2l;                /* device time of every far-to-local translation launch */
 } dfgt_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
@@ -83,10 +86,12 @@ typedef struct {
  * non-blocking stream. */
 dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream);
 
-/* Set the initial capacity of the traversal's work lists (node pairs per
- * frontier, items per action list).  A call whose lists outgrow them
- * regrows them and redoes its traversal (dfgt_stats.overflow_retries);
- * larger values trade memory for fewer retries.  Both must be >= 1. */
+/* Set the capacity of the traversal's action lists (items per list) and
+ * the initial capacity of its frontier (node pairs).  A list that could
+ * overflow in the next round is drained first (its kernel runs early,
+ * counted in dfgt_stats.list_flushes); the frontier grows to the exact
+ * size each round needs.  Larger lists trade memory for fewer, larger
+ * launches.  Both must be >= 1. */
 dfgt_status dfgt_set_capacity(dfgt_ctx* ctx, int64_t frontier_pairs, int64_t list_items);
 
 /* Free a context and its cached workspace.  NULL is ignored. */

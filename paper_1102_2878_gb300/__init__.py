@@ -84,15 +84,16 @@ class Context:
             pass
 
 
-def _opts(leaf_size=0, p_max=0, eps_fp=0.0):
-    return _lib.Opts(int(leaf_size), int(p_max), float(eps_fp))
+def _opts(leaf_size=0, p_max=0, eps_fp=0.0, base_block=0):
+    return _lib.Opts(int(leaf_size), int(p_max), float(eps_fp), int(base_block))
 
 
 class Tree:
     """The mid-point kd-tree of Algorithm 2 over float32 points [n, d] on
     the context's device, with the raw far-field moments of every node."""
 
-    def __init__(self, ctx: Context, points, leaf_size: int = 0, p_max: int = 0, eps_fp: float = 0.0):
+    def __init__(self, ctx: Context, points, leaf_size: int = 0, p_max: int = 0, eps_fp: float = 0.0,
+                 base_block: int = 0):
         torch = _torch()
         if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
                 and points.dim() == 2):
@@ -100,7 +101,7 @@ class Tree:
         self.ctx = ctx
         self.points = points.contiguous()
         self.n, self.d = self.points.shape
-        opts = _opts(leaf_size, p_max, eps_fp)
+        opts = _opts(leaf_size, p_max, eps_fp, base_block)
         h = C.c_void_p()
         ctx.order_after_torch()
         st = ctx.lib.dfgt_build(ctx.h, C.c_void_p(self.points.data_ptr()), self.n, self.d,

@@ -19,7 +19,8 @@ ACT_PRUNE, ACT_FARFIELD, ACT_LOCAL, ACT_F2L, ACT_BASE = 0, 1, 2, 3, 4
 
 
 class Opts(C.Structure):
-    _fields_ = [("leaf_size", C.c_int), ("p_max", C.c_int), ("eps_fp", C.c_double)]
+    _fields_ = [("leaf_size", C.c_int), ("p_max", C.c_int), ("eps_fp", C.c_double),
+                ("base_block", C.c_longlong)]
 
 
 class Stats(C.Structure):
@@ -27,7 +28,7 @@ class Stats(C.Structure):
                 ("n_farfield", C.c_longlong), ("n_local", C.c_longlong),
                 ("n_f2l", C.c_longlong), ("n_base", C.c_longlong),
                 ("base_interactions", C.c_longlong), ("kernel_launches", C.c_longlong),
-                ("rounds", C.c_int), ("overflow_retries", C.c_int),
+                ("rounds", C.c_int), ("list_flushes", C.c_int),
                 ("ms_traverse", C.c_double), ("ms_actions", C.c_double), ("ms_post", C.c_double),
                 ("ms_base", C.c_double), ("ms_farfield", C.c_double), ("ms_local", C.c_double),
                 ("ms_f2l", C.c_double)]

@@ -70,6 +70,21 @@ __device__ __forceinline__ double center(const TreeView& T, int node, int k) {
   return 0.5 * ((double)T.lo[(size_t)node * T.d + k] + (double)T.hi[(size_t)node * T.d + k]);
 }
 
+// A box center as an unevaluated float pair hi + lo.  (p - hi) is exact for
+// a point p near the center (Sterbenz), so (p - hi) - lo carries only the
+// rounding of the difference itself, not the rounding of the center's
+// coordinate, which would be an absolute error u |c| -- large against a
+// small bandwidth.
+struct CenterHL {
+  float hi, lo;
+};
+__device__ __forceinline__ CenterHL center_hl(const TreeView& T, int node, int k) {
+  const double c = center(T, node, k);
+  const float hi = (float)c;
+  return CenterHL{hi, (float)(c - (double)hi)};
+}
+__device__ __forceinline__ float minus_center(float p, CenterHL c) { return (p - c.hi) - c.lo; }
+
 template <int D>
 __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v) {
   if constexpr (D == 1) {
@@ -164,9 +179,9 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
   float* Ms = sM[wib];
   stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, s, a.p, Ms, lane);
   __syncwarp();
-  float cR[D];
+  CenterHL cR[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) cR[k] = (float)center(R, a.r, k);
+  for (int k = 0; k < D; ++k) cR[k] = center_hl(R, a.r, k);
   const float sf = (float)s;
   const int qb = Q.beg[a.q], qn = Q.cnt[a.q];
   for (int qi = lane; qi < qn; qi += 32) {
@@ -174,7 +189,7 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
     load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
     float H[D][PM];
 #pragma unroll
-    for (int k = 0; k < D; ++k) hermite_f32<PM>((qv[k] - cR[k]) * sf, H[k]);
+    for (int k = 0; k < D; ++k) hermite_f32<PM>(minus_center(qv[k], cR[k]) * sf, H[k]);
     float acc = 0.f;
 #pragma unroll
     for (int idx = 0; idx < P; ++idx) {
@@ -209,9 +224,9 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const Acti
   const Action a = list[w];
   const double h = hv[a.h];
   const float sf = (float)(1.0 / sqrt(2.0 * h * h));
-  float cQ[D];
+  CenterHL cQ[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) cQ[k] = (float)center(Q, a.q, k);
+  for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, a.q, k);
   const int rb = R.beg[a.r], rn = R.cnt[a.r];
   double acc[S];
 #pragma unroll
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const Acti
       float rv[D];
       load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
 #pragma unroll
-      for (int k = 0; k < D; ++k) hermite_f32<PM>((cQ[k] - rv[k]) * sf, sH[wib][lane][k]);
+      for (int k = 0; k < D; ++k) hermite_f32<PM>(-minus_center(rv[k], cQ[k]) * sf, sH[wib][lane][k]);
     } else {
 #pragma unroll
       for (int k = 0; k < D; ++k)
@@ -356,16 +371,26 @@ __global__ void k_prune_apply(TreeView Q, TreeView R, const Pair* __restrict__ l
 // TransLocalToLocal (Lemma 3.6, Eq. local_to_local_translation) from every
 // node of one level to both children, order p = highest order used at the
 // node: L_alpha(c') += sum_{alpha<=beta<p} beta!/(alpha!(beta-alpha)!) L_beta(c) ((c'-c)/sqrt(2h^2))^{beta-alpha}.
-// One warp per (node, bandwidth); a child has a single parent, so its
-// coefficients are updated without atomics.
+// The binomial coefficient and the power both factor over dimensions, so
+// the shift is applied as D one-dimensional shifts (D p^D p operations
+// instead of p^{2D}), in float64, in shared memory.  One warp per (node,
+// bandwidth); a child has one parent, so its coefficients are updated
+// without atomics.
 template <int D>
 __global__ void __launch_bounds__(kT) k_l2l(TreeView Q, double* __restrict__ L,
                                             int* __restrict__ pused, const double* __restrict__ hv,
                                             int nh, int a, int e) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
-  constexpr int S = (P + 31) / 32;
-  const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
+  __shared__ double sL[kWarpsPerBlock][2][P];
+  __shared__ double sC[PM][PM];  // binomial coefficients C(b, a)
+  if (threadIdx.x < PM * PM) {
+    const int bb = threadIdx.x / PM, aa = threadIdx.x % PM;
+    sC[bb][aa] = aa <= bb ? fact_d(bb) / (fact_d(aa) * fact_d(bb - aa)) : 0.0;
+  }
+  __syncthreads();
+  const int wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarpsPerBlock + wib;
   const int lane = threadIdx.x & 31;
   const int nl = e - a;
   if (w >= nl * nh) return;
@@ -381,41 +406,33 @@ __global__ void __launch_bounds__(kT) k_l2l(TreeView Q, double* __restrict__ L,
   for (int ch = 0; ch < 2; ++ch) {
     const int c = cl + ch;
     const size_t hc = (size_t)hidx * Q.nn + c;
-    double X[D][PM];
+    for (int idx = lane; idx < P; idx += 32) sL[wib][0][idx] = Lp[idx];
+    __syncwarp();
+    int cur = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const double x = (center(Q, c, k) - center(Q, node, k)) * s;
-      double v = 1.0;
-#pragma unroll
-      for (int q = 0; q < PM; ++q) { X[k][q] = v; v *= x; }
-    }
-#pragma unroll
-    for (int sl = 0; sl < S; ++sl) {
-      const int idx = lane + 32 * sl;
-      if (idx >= P) break;
-      int al[D];
-      bool ok = true;
-      {
-        int v = idx;
-#pragma unroll
-        for (int k = D - 1; k >= 0; --k) { al[k] = v % PM; v /= PM; ok = ok && al[k] < p; }
-      }
-      if (!ok) continue;
-      double acc = 0.0;
-#pragma unroll
-      for (int j = 0; j < P; ++j) {
-        double t = Lp[j];
-        bool use = true;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const int bk = digit_c<D, PM>(j, k);
-          use = use && bk >= al[k] && bk < p;
-          if (bk >= al[k]) t *= X[k][bk - al[k]] * (fact_d(bk) / (fact_d(al[k]) * fact_d(bk - al[k])));
+      constexpr int dummy = 0;
+      (void)dummy;
+      int stride = 1;
+      for (int j = D - 1; j > k; --j) stride *= PM;
+      for (int idx = lane; idx < P; idx += 32) {
+        const int ak = (idx / stride) % PM;
+        double acc = 0.0;
+        if (ak < p) {
+          double xp = 1.0;
+          for (int bk = ak; bk < p; ++bk) {
+            acc += sC[bk][ak] * xp * sL[wib][cur][idx + (bk - ak) * stride];
+            xp *= x;
+          }
         }
-        if (use) acc += t;
+        sL[wib][cur ^ 1][idx] = acc;
       }
-      L[hc * P + idx] += acc;
+      __syncwarp();
+      cur ^= 1;
     }
+    for (int idx = lane; idx < P; idx += 32) L[hc * P + idx] += sL[wib][cur][idx];
+    __syncwarp();
     if (lane == 0 && pused[hc] < p) pused[hc] = p;
   }
 }
@@ -451,7 +468,7 @@ __global__ void __launch_bounds__(kT) k_finalize(TreeView Q, const double* __res
       float X[D][PM];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const float x = (qv[k] - (float)center(Q, leaf, k)) * sf;
+        const float x = minus_center(qv[k], center_hl(Q, leaf, k)) * sf;
         float v = 1.f;
 #pragma unroll
         for (int q = 0; q < PM; ++q) { X[k][q] = v; v *= x; }
@@ -489,7 +506,7 @@ __global__ void __launch_bounds__(kT) k_farfield_g(TreeView Q, TreeView R, const
   for (int qi = lane; qi < qn; qi += 32) {
     float d2 = 0.f;
     for (int k = 0; k < Q.d; ++k) {
-      const float t = Q.pts[(size_t)(qb + qi) * Q.dp + k] - (float)center(R, a.r, k);
+      const float t = minus_center(Q.pts[(size_t)(qb + qi) * Q.dp + k], center_hl(R, a.r, k));
       d2 = fmaf(t, t, d2);
     }
     atomicAdd(&gacc[(size_t)a.h * Q.n + qb + qi], (double)(m0 * ex2_approx(d2 * c2)));
@@ -510,7 +527,7 @@ __global__ void __launch_bounds__(kT) k_local_g(TreeView Q, TreeView R, const Ac
   for (int j = lane; j < rn; j += 32) {
     float d2 = 0.f;
     for (int k = 0; k < Q.d; ++k) {
-      const float t = (float)center(Q, a.q, k) - R.pts[(size_t)(rb + j) * R.dp + k];
+      const float t = minus_center(R.pts[(size_t)(rb + j) * R.dp + k], center_hl(Q, a.q, k));
       d2 = fmaf(t, t, d2);
     }
     part += ex2_approx(d2 * c2);

@@ -36,23 +36,12 @@ bool bad_h(const double* h, int nh) {
   return false;
 }
 
-// Shared tail of dfgt_sum and dfgt_apply_pairs: the action kernels over
-// the lists, the local-to-local pass down the query tree, finalisation.
-dfgt_status actions_and_post(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
-                             const TravBuffers& b, int n_far, int n_loc, int n_f2l, int n_base,
-                             double* G_dev, dfgt_stats* st) {
+// DFGTPost: local-to-local translation level by level down the query
+// tree, then the leaf read-out and the final sum into G_dev.
+dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, double* G_dev,
+                 dfgt_stats* st) {
   cudaStream_t s = ctx->stream;
-  const TreeView Q = qt->view(), R = rt->view();
-  CK(cudaEventRecord(ctx->ev[1], s));
-  CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), n_base, s));
-  CK(cudaEventRecord(ctx->ev[4], s));
-  CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), n_far, s));
-  CK(cudaEventRecord(ctx->ev[5], s));
-  CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), n_loc, s));
-  CK(cudaEventRecord(ctx->ev[6], s));
-  CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), n_f2l, s));
-  ctx->launches += (n_base > 0) + (n_far > 0) + (n_loc > 0) + (n_f2l > 0);
-  CK(cudaEventRecord(ctx->ev[2], s));
+  const TreeView Q = qt->view();
   for (int lev = 0; lev + 1 < qt->depth; ++lev) {
     CK(launch_l2l_level(Q, b, qt->lvl_off[lev], qt->lvl_off[lev + 1], s));
     ++ctx->launches;
@@ -63,18 +52,8 @@ dfgt_status actions_and_post(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   CK(cudaStreamSynchronize(s));
   if (st) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
-    st->ms_actions = ms;
     cudaEventElapsedTime(&ms, ctx->ev[2], ctx->ev[3]);
     st->ms_post = ms;
-    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[4]);
-    st->ms_base = ms;
-    cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
-    st->ms_farfield = ms;
-    cudaEventElapsedTime(&ms, ctx->ev[5], ctx->ev[6]);
-    st->ms_local = ms;
-    cudaEventElapsedTime(&ms, ctx->ev[6], ctx->ev[2]);
-    st->ms_f2l = ms;
   }
   return DFGT_OK;
 }
@@ -122,6 +101,47 @@ dfgt_status ensure_lists(dfgt_ctx* ctx) {
   return DFGT_OK;
 }
 
+// One kind of action list: its device buffer, its fill and the kernel that drains it.
+struct ListState {
+  int count = 0;
+  long long total = 0;
+  double ms = 0.0;       // device time of this list's kernel, all launches
+  bool timed = false;    // a launch is bracketed by its events, not yet read
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  void collect() {
+    if (!timed) return;
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    ms += t;
+    timed = false;
+  }
+};
+
+// Run the action kernel of a list over its current contents and empty it.
+// Stream order makes the next round's appends start after the kernel read
+// the list, so no synchronisation is needed.
+dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const TravBuffers& b,
+                  int which, ListState& ls, int* dcount) {
+  if (ls.count == 0) return DFGT_OK;
+  cudaStream_t s = ctx->stream;
+  const TreeView Q = qt->view(), R = rt->view();
+  if (ls.timed) {  // the previous launch of this list has finished reading by now
+    CK(cudaEventSynchronize(ls.e1));
+    ls.collect();
+  }
+  CK(cudaEventRecord(ls.e0, s));
+  if (which == 0) CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), ls.count, s));
+  else if (which == 1) CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), ls.count, s));
+  else if (which == 2) CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), ls.count, s));
+  else CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), ls.count, s));
+  ++ctx->launches;
+  CK(cudaEventRecord(ls.e1, s));
+  ls.timed = true;
+  CK(cudaMemsetAsync(dcount, 0, sizeof(int), s));
+  ls.count = 0;
+  return DFGT_OK;
+}
+
 dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const double* h_host,
                     int nh, double eps, double* G_dev, dfgt_stats* st) {
   cudaStream_t s = ctx->stream;
@@ -129,69 +149,111 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
   const TreeView Q = qt->view(), R = rt->view();
   const double eps_eff = eps - std::max(qt->eps_fp, rt->eps_fp);
   const int max_rounds = qt->depth + rt->depth + 8;
-  int retries = 0;
-  for (;;) {
-    TravBuffers b;
-    dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, &b);
-    if (rc != DFGT_OK) return rc;
-    rc = ensure_lists(ctx);
-    if (rc != DFGT_OK) return rc;
-    RoundCounters* dctr = ctx->counters.as<RoundCounters>();
-    RoundCounters* hc = ctx->h_counters;
-    CK(cudaEventRecord(ctx->ev[0], s));
-    CK(launch_init_frontier(ctx->frontier[0].as<Pair>(), nh, s));
-    ++ctx->launches;
-    int cur = 0, nF = nh, rounds = 0;
-    long long visited = 0;
-    bool overflow = false;
-    while (nF > 0) {
-      if (rounds >= max_rounds) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: traversal did not finish");
-      CK(launch_fold(b, qt->nn, s));
-      CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
-      CK(cudaMemsetAsync(&dctr->n_next, 0, sizeof(int), s));
-      CK(launch_classify(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, ctx->frontier[cur ^ 1].as<Pair>(),
-                         (int)ctx->cap_frontier, ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(),
-                         ctx->list_f2l.as<Action>(), ctx->list_base.as<Pair>(), (int)ctx->cap_lists,
-                         dctr, s));
-      ctx->launches += 3;
-      CK(cudaMemcpyAsync(hc, dctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      visited += nF;
-      ++rounds;
-      if (hc->status & kStOverflow) { overflow = true; break; }
-      nF = hc->n_next;
-      cur ^= 1;
-    }
-    if (overflow) {
-      if (++retries > 8) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work lists overflowed repeatedly");
-      const size_t need_f = (size_t)std::max(hc->n_next, 0);
-      const size_t need_l = (size_t)std::max(std::max(hc->n_far, hc->n_loc), std::max(hc->n_f2l, hc->n_base));
-      if (need_f > ctx->cap_frontier) ctx->cap_frontier = std::max(2 * ctx->cap_frontier, need_f + need_f / 2);
-      if (need_l >= ctx->cap_lists) ctx->cap_lists = std::max(2 * ctx->cap_lists, need_l + need_l / 2);
-      if (ctx->cap_frontier > kHardCap || ctx->cap_lists > kHardCap)
-        return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work lists exceed the hard size limit");
-      continue;
-    }
-    const RoundCounters fin = *hc;
-    dfgt_status r2 = actions_and_post(ctx, qt, rt, b, fin.n_far, fin.n_loc, fin.n_f2l, fin.n_base, G_dev, st);
-    if (r2 != DFGT_OK) return r2;
-    if (st) {
-      st->pairs_visited = visited;
-      st->n_prune = (long long)fin.n_prune;
-      st->n_farfield = fin.n_far;
-      st->n_local = fin.n_loc;
-      st->n_f2l = fin.n_f2l;
-      st->n_base = fin.n_base;
-      st->base_interactions = (long long)fin.base_inter;
-      st->rounds = rounds;
-      st->overflow_retries = retries;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
-      st->ms_traverse = ms;
-      st->kernel_launches = ctx->launches - launches0;
-    }
-    return DFGT_OK;
+  TravBuffers b;
+  dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, &b);
+  if (rc != DFGT_OK) return rc;
+  b.base_block = std::max(qt->base_block, rt->base_block);
+  ctx->cap_frontier = std::max<size_t>(ctx->cap_frontier, (size_t)nh);
+  rc = ensure_lists(ctx);
+  if (rc != DFGT_OK) return rc;
+  RoundCounters* dctr = ctx->counters.as<RoundCounters>();
+  RoundCounters* hc = ctx->h_counters;
+  int* dcount[4] = {&dctr->n_base, &dctr->n_far, &dctr->n_loc, &dctr->n_f2l};
+  ListState lists[4];
+  for (int w = 0; w < 4; ++w) {
+    lists[w].e0 = ctx->ev[8 + 2 * w];
+    lists[w].e1 = ctx->ev[9 + 2 * w];
   }
+  int flushes = 0;
+  CK(cudaEventRecord(ctx->ev[0], s));
+  CK(launch_init_frontier(ctx->frontier[0].as<Pair>(), nh, s));
+  ++ctx->launches;
+  int cur = 0, nF = nh, rounds = 0;
+  long long visited = 0;
+  while (nF > 0) {
+    if (rounds >= max_rounds) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: traversal did not finish");
+    if ((size_t)nF > kHardCap) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: frontier exceeds 2^28 node pairs");
+    // a round appends at most one item per pair to each list
+    for (int w = 0; w < 4; ++w) {
+      if ((size_t)lists[w].count + nF > ctx->cap_lists) {
+        rc = drain(ctx, qt, rt, b, w, lists[w], dcount[w]);
+        if (rc != DFGT_OK) return rc;
+        ++flushes;
+      }
+    }
+    if ((size_t)nF > ctx->cap_lists) {
+      for (int w = 0; w < 4; ++w) {
+        rc = drain(ctx, qt, rt, b, w, lists[w], dcount[w]);
+        if (rc != DFGT_OK) return rc;
+      }
+      CK(cudaStreamSynchronize(s));
+      ctx->cap_lists = std::max((size_t)nF, 2 * ctx->cap_lists);
+      rc = ensure_lists(ctx);
+      if (rc != DFGT_OK) return rc;
+    }
+    CK(ctx->slots.ensure((size_t)nF * sizeof(int)));
+    CK(launch_fold(b, qt->nn, s));
+    CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
+    CK(cudaMemsetAsync(&dctr->n_next, 0, sizeof(int), s));
+    CK(launch_classify(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, ctx->slots.as<int>(),
+                       ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(),
+                       ctx->list_f2l.as<Action>(), ctx->list_base.as<Pair>(), (int)ctx->cap_lists,
+                       dctr, s));
+    ctx->launches += 3;
+    CK(cudaMemcpyAsync(hc, dctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (hc->status & kStOverflow) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: action list overflow");
+    visited += nF;
+    ++rounds;
+    for (int w = 0; w < 4; ++w) lists[w].collect();
+    const int got[4] = {hc->n_base, hc->n_far, hc->n_loc, hc->n_f2l};
+    for (int w = 0; w < 4; ++w) {
+      lists[w].total += got[w] - lists[w].count;
+      lists[w].count = got[w];
+    }
+    const int n_next = hc->n_next;
+    if (n_next > 0) {
+      // size the next frontier exactly, then write the reserved child pairs
+      CK(ctx->frontier[cur ^ 1].ensure((size_t)n_next * sizeof(Pair)));
+      ctx->cap_frontier = std::max(ctx->cap_frontier, (size_t)n_next);
+      CK(launch_emit(Q, R, ctx->frontier[cur].as<Pair>(), nF, ctx->slots.as<int>(),
+                     ctx->frontier[cur ^ 1].as<Pair>(), s));
+      ++ctx->launches;
+    }
+    nF = n_next;
+    cur ^= 1;
+  }
+  CK(cudaEventRecord(ctx->ev[1], s));
+  for (int w = 0; w < 4; ++w) {
+    rc = drain(ctx, qt, rt, b, w, lists[w], dcount[w]);
+    if (rc != DFGT_OK) return rc;
+  }
+  CK(cudaEventRecord(ctx->ev[2], s));
+  rc = post(ctx, qt, b, G_dev, st);
+  if (rc != DFGT_OK) return rc;
+  for (int w = 0; w < 4; ++w) lists[w].collect();
+  if (st) {
+    st->pairs_visited = visited;
+    st->n_prune = (long long)hc->n_prune;
+    st->n_base = lists[0].total;
+    st->n_farfield = lists[1].total;
+    st->n_local = lists[2].total;
+    st->n_f2l = lists[3].total;
+    st->base_interactions = (long long)hc->base_inter;
+    st->rounds = rounds;
+    st->list_flushes = flushes;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
+    st->ms_traverse = ms;
+    cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
+    st->ms_actions = ms;
+    st->ms_base = lists[0].ms;
+    st->ms_farfield = lists[1].ms;
+    st->ms_local = lists[2].ms;
+    st->ms_f2l = lists[3].ms;
+    st->kernel_launches = ctx->launches - launches0;
+  }
+  return DFGT_OK;
 }
 
 }  // namespace
@@ -215,7 +277,7 @@ dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream) {
     ctx->own_stream = true;
   }
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, sizeof(RoundCounters));
-  for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e != cudaSuccess) {
     dfgt_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? DFGT_ENOMEM : DFGT_ECUDA;
@@ -238,12 +300,12 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1],
+  DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1], &ctx->slots,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g};
   for (DevBuf* b : bufs) b->release();
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < 16; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -259,7 +321,8 @@ dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
   *out = nullptr;
   if (!points_dev || n < 1 || n > (int64_t)std::numeric_limits<int>::max() / 4 || d < 1 || d > kMaxD)
     return fail(ctx, DFGT_EINVAL, "dfgt_build: need points, 1 <= n < 2^29, 1 <= d <= 32");
-  if (opts && (opts->leaf_size < 0 || opts->leaf_size > kMaxLeaf || opts->p_max < 0 || opts->eps_fp < 0))
+  if (opts && (opts->leaf_size < 0 || opts->leaf_size > kMaxLeaf || opts->p_max < 0 || opts->eps_fp < 0 ||
+               opts->base_block < -1))
     return fail(ctx, DFGT_EINVAL, "dfgt_build: options out of range");
   CK(cudaSetDevice(ctx->device));
   dfgt_tree* t = new dfgt_tree();
@@ -420,9 +483,14 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   CK(up(ctx->list_far, far.data(), far.size() * sizeof(Action)));
   CK(up(ctx->list_loc, loc.data(), loc.size() * sizeof(Action)));
   CK(up(ctx->list_f2l, f2l.data(), f2l.size() * sizeof(Action)));
-  CK(launch_prune_apply(qt->view(), rt->view(), b, ctx->frontier[0].as<Pair>(), (int)prune.size(), s));
-  return actions_and_post(ctx, qt, rt, b, (int)far.size(), (int)loc.size(), (int)f2l.size(),
-                          (int)base.size(), G_dev, nullptr);
+  const TreeView Q = qt->view(), R = rt->view();
+  CK(launch_prune_apply(Q, R, b, ctx->frontier[0].as<Pair>(), (int)prune.size(), s));
+  CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), (int)base.size(), s));
+  CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), (int)far.size(), s));
+  CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), (int)loc.size(), s));
+  CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), (int)f2l.size(), s));
+  CK(cudaEventRecord(ctx->ev[2], s));
+  return post(ctx, qt, b, G_dev, nullptr);
 }
 
 }  // extern "C"

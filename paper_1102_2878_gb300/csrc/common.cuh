@@ -105,6 +105,58 @@ __device__ inline double fp_allowance(double nR, int D, double r_eff, int p, int
   return c * u * nR * S;
 }
 
+// Float32 evaluations of the same bounds for order selection.  Every
+// quantity is a sum or product of positive terms, so float32 evaluation is
+// within ~16 ulps of the exact value; callers compare bound * (1 + 1e-4)
+// against tau, which keeps every accepted order valid.
+__device__ __forceinline__ float pow_int_f(float x, int e) {
+  float r = 1.f;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+__device__ inline float rsqrt_fact_f(int p) {
+  // 1/sqrt(p!) for p = 0..8
+  const float t[9] = {1.f, 1.f, 0.70710678f, 0.40824829f, 0.20412415f,
+                      0.091287093f, 0.037267800f, 0.014085904f, 0.0049801192f};
+  return t[p < 9 ? p : 8];
+}
+
+// Eq. error_bound_far_field (and error_bound_local) plus the rounding
+// allowance, float32; r < 1.
+__device__ inline float bound_ff_total(float nR, int D, float r, int p) {
+  const float rp = pow_int_f(r, p);
+  const float a = 1.f - rp, b = rp * rsqrt_fact_f(p);
+  float sum = 0.f, ak = 1.f, c = 1.f;
+  for (int k = 0; k < D; ++k) {
+    sum += c * ak * pow_int_f(b, D - k);
+    ak *= a;
+    c = c * (float)(D - k) / (float)(k + 1);
+  }
+  const float g = 1.f / (1.f - r);
+  const float gD = pow_int_f(g, D);
+  const float S = pow_int_f(a * g, D);
+  const float cfp = 2.f * (2.f * pow_int_f((float)p, D) + 6.f * D + 16.f) * 5.9604645e-08f;
+  return nR * (sum * gD + cfp * S);
+}
+
+// Eq. error_bound_far_to_local plus the rounding allowance, float32; r < 1/2.
+__device__ inline float bound_f2l_total(float nR, int D, float r, int p) {
+  const float q = pow_int_f(2.f * r, p);
+  const float a = (1.f - q) * (1.f - q), b = q * (2.f - q) * rsqrt_fact_f(p);
+  float sum = 0.f, ak = 1.f, c = 1.f;
+  for (int k = 0; k < D; ++k) {
+    sum += c * ak * pow_int_f(b, D - k);
+    ak *= a;
+    c = c * (float)(D - k) / (float)(k + 1);
+  }
+  const float g = 1.f / (1.f - 2.f * r);
+  const float g2D = pow_int_f(g, 2 * D);
+  const float S = pow_int_f((1.f - q) * g, 2 * D);
+  const float cfp = 2.f * (2.f * pow_int_f((float)p, D) + 6.f * D + 16.f) * 5.9604645e-08f;
+  return nR * (sum * g2D + cfp * S);
+}
+
 // ------------------------------------------------------------- atomics
 __device__ __forceinline__ void atomic_min_f(float* a, float v) {
   if (v >= 0.f)

@@ -53,6 +53,7 @@ struct dfgt_ctx {
   DevBuf counters;       // RoundCounters on the device
   DevBuf hvals;          // bandwidths
   DevBuf frontier[2];    // Pair
+  DevBuf slots;          // int child slot per frontier pair
   DevBuf list_far, list_loc, list_f2l, list_base;  // Action / Pair
   DevBuf node_state;     // u64 inherited/decided/incr/lbsum
   DevBuf lmom;           // double local moments [nh][nn][P]
@@ -62,13 +63,14 @@ struct dfgt_ctx {
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 20;
   RoundCounters* h_counters = nullptr;  // pinned
-  cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[16] = {};
 };
 
 struct dfgt_tree {
   int device = 0;
   int64_t n = 0;
   int d = 0, dp = 0, leaf = 32, pm = 1, P = 1, p_limit = 1;
+  long long base_block = 0;
   double eps_fp = 2e-5;
   int nn = 0, nleaves = 0, depth = 0;
   std::vector<int> lvl_off;  // nodes of level k are [lvl_off[k], lvl_off[k+1])
@@ -121,15 +123,18 @@ struct TravBuffers {
   double eps_eff;   // eps minus the float allowance for exact sums
   double fix_scale; // 2^62 / |R|
   int p_limit;
+  long long base_block;  // exact sum without recursing when |Q||R| <= this
 };
 
 cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s);
 cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
                       int nF, cudaStream_t s);
 cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Pair* F, int nF, Pair* next, int cap_next, Action* far,
-                            Action* loc, Action* f2l, Pair* base, int cap_lists,
-                            RoundCounters* counters, cudaStream_t s);
+                            const Pair* F, int nF, int* slot, Action* far, Action* loc,
+                            Action* f2l, Pair* base, int cap_lists, RoundCounters* counters,
+                            cudaStream_t s);
+cudaError_t launch_emit(const TreeView& Q, const TreeView& R, const Pair* F, int nF, const int* slot,
+                        Pair* next, cudaStream_t s);
 cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s);
 
 cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,

@@ -59,20 +59,29 @@ __device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const Tre
 }
 
 // FarFieldOrder / LocalAccumulationOrder: least p <= plim whose truncation
-// bound plus float32 rounding allowance is <= tau; 0 = none (r >= 1).
+// bound plus float32 rounding allowance is <= tau; 0 = none (r >= 1).  The
+// bound decreases with p, so the largest order is tried first and most
+// pairs are rejected after one evaluation.
+constexpr float kSafe = 1.0001f;  // covers float32 evaluation of the bounds
+
 __device__ int order_ff(double r, double nR, int D, double tau, int plim) {
   if (!(r < 1.0)) return 0;
-  for (int p = 1; p <= plim; ++p)
-    if (bound_farfield(nR, D, r, p) + fp_allowance(nR, D, r, p, 1) <= tau) return p;
-  return 0;
+  // every bound grows with r and |R|: round those up and tau down
+  const float rf = __double2float_ru(r), nf = __double2float_ru(nR), tf = __double2float_rd(tau);
+  if (!(rf < 1.f) || bound_ff_total(nf, D, rf, plim) * kSafe > tf) return 0;
+  for (int p = 1; p < plim; ++p)
+    if (bound_ff_total(nf, D, rf, p) * kSafe <= tf) return p;
+  return plim;
 }
 
 // ConvertFarFieldToLocalOrder; 0 = none (r >= 1/2).
 __device__ int order_t(double r, double nR, int D, double tau, int plim) {
   if (!(r < 0.5)) return 0;
-  for (int p = 1; p <= plim; ++p)
-    if (bound_f2l(nR, D, r, p) + fp_allowance(nR, D, 2.0 * r, p, 2) <= tau) return p;
-  return 0;
+  const float rf = __double2float_ru(r), nf = __double2float_ru(nR), tf = __double2float_rd(tau);
+  if (!(rf < 0.5f) || bound_f2l_total(nf, D, rf, plim) * kSafe > tf) return 0;
+  for (int p = 1; p < plim; ++p)
+    if (bound_f2l_total(nf, D, rf, p) * kSafe <= tf) return p;
+  return plim;
 }
 
 // All 32 lanes call this; returns the first slot of this lane's n items.
@@ -135,7 +144,7 @@ __global__ void __launch_bounds__(kT) k_lb(TreeView Q, TreeView R, TravBuffers b
 template <int D>
 __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuffers b,
                                                  const Pair* __restrict__ F, int nF,
-                                                 Pair* __restrict__ next, int cap_next,
+                                                 int* __restrict__ slot,
                                                  Action* __restrict__ far, Action* __restrict__ loc,
                                                  Action* __restrict__ f2l, Pair* __restrict__ base,
                                                  int cap_lists, RoundCounters* ctr) {
@@ -183,9 +192,16 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
         else if (pD && cD == m) { kind = 2; order = pD; }
         else if (pT && cT == m) { kind = 3; order = pT; }
         else {
+          // exact sum: at a leaf pair (DFGTBase), or for any pair small
+          // enough that recursing further cannot pay (|Q||R| <= base_block)
           const int ql = Q.left[pr.q], rl = R.left[pr.r];
-          if (ql < 0 && rl < 0) { kind = 4; inter = (unsigned long long)(nQ * nR); }
-          else { kind = 5; nchild = (ql >= 0 && rl >= 0) ? 4 : 2; }
+          if ((ql < 0 && rl < 0) || nQ * nR <= (double)b.base_block) {
+            kind = 4;
+            inter = (unsigned long long)(nQ * nR);
+          } else {
+            kind = 5;
+            nchild = (ql >= 0 && rl >= 0) ? 4 : 2;
+          }
         }
       }
       if (kind <= 4) {
@@ -193,28 +209,12 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
         if (f) atomicAdd(&b.incr[hq], f);
       }
     }
-    // warp-aggregated appends (all lanes take part)
+    // warp-aggregated appends (all lanes take part); child pairs only get
+    // their slots here and are written by k_emit once the host has sized
+    // the next frontier
     {
       const int s0 = warp_alloc(&ctr->n_next, nchild);
-      if (nchild) {
-        if (s0 + nchild <= cap_next) {
-          const int ql = Q.left[pr.q], rl = R.left[pr.r];
-          if (ql < 0) {
-            next[s0] = Pair{pr.q, rl, pr.h, 0};
-            next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
-          } else if (rl < 0) {
-            next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
-            next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
-          } else {
-            next[s0] = Pair{ql, rl, pr.h, kFlagSplitQ};
-            next[s0 + 1] = Pair{ql, rl + 1, pr.h, kFlagSplitQ};
-            next[s0 + 2] = Pair{ql + 1, rl, pr.h, kFlagSplitQ};
-            next[s0 + 3] = Pair{ql + 1, rl + 1, pr.h, kFlagSplitQ};
-          }
-        } else {
-          atomicOr(&ctr->status, kStOverflow);
-        }
-      }
+      if (i < nF) slot[i] = nchild ? s0 : -1;
     }
     {
       const int s1 = warp_alloc(&ctr->n_far, kind == 1);
@@ -231,14 +231,38 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
   }
 }
 
+// Write the child pairs of every recursing pair at the slot reserved by
+// k_classify (DFGT recursion: split both nodes, or the one that is not a leaf).
+__global__ void __launch_bounds__(kT) k_emit(const int* __restrict__ Qleft, const int* __restrict__ Rleft,
+                                             const Pair* __restrict__ F, int nF,
+                                             const int* __restrict__ slot, Pair* __restrict__ next) {
+  const int i = blockIdx.x * kT + threadIdx.x;
+  if (i >= nF) return;
+  const int s0 = slot[i];
+  if (s0 < 0) return;
+  const Pair pr = F[i];
+  const int ql = Qleft[pr.q], rl = Rleft[pr.r];
+  if (ql < 0) {
+    next[s0] = Pair{pr.q, rl, pr.h, 0};
+    next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
+  } else if (rl < 0) {
+    next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
+    next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
+  } else {
+    next[s0] = Pair{ql, rl, pr.h, kFlagSplitQ};
+    next[s0 + 1] = Pair{ql, rl + 1, pr.h, kFlagSplitQ};
+    next[s0 + 2] = Pair{ql + 1, rl, pr.h, kFlagSplitQ};
+    next[s0 + 3] = Pair{ql + 1, rl + 1, pr.h, kFlagSplitQ};
+  }
+}
+
 template <int D>
 cudaError_t classify_d(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
-                       int nF, Pair* next, int cap_next, Action* far, Action* loc, Action* f2l,
+                       int nF, int* slot, Action* far, Action* loc, Action* f2l,
                        Pair* base, int cap_lists, RoundCounters* ctr, cudaStream_t s) {
   int grid = (nF + kT - 1) / kT;
   if (grid > 152 * 16) grid = 152 * 16;
-  k_classify<D><<<grid, kT, 0, s>>>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base,
-                                     cap_lists, ctr);
+  k_classify<D><<<grid, kT, 0, s>>>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr);
   return cudaGetLastError();
 }
 
@@ -270,17 +294,23 @@ cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b
 }
 
 cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Pair* F, int nF, Pair* next, int cap_next, Action* far,
-                            Action* loc, Action* f2l, Pair* base, int cap_lists,
-                            RoundCounters* ctr, cudaStream_t s) {
+                            const Pair* F, int nF, int* slot, Action* far, Action* loc,
+                            Action* f2l, Pair* base, int cap_lists, RoundCounters* ctr,
+                            cudaStream_t s) {
   switch (Q.d) {
-    case 1: return classify_d<1>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 2: return classify_d<2>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 3: return classify_d<3>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 4: return classify_d<4>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 5: return classify_d<5>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    default: return classify_d<0>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 1: return classify_d<1>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
+    case 2: return classify_d<2>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
+    case 3: return classify_d<3>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
+    case 4: return classify_d<4>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
+    case 5: return classify_d<5>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
+    default: return classify_d<0>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
   }
+}
+
+cudaError_t launch_emit(const TreeView& Q, const TreeView& R, const Pair* F, int nF, const int* slot,
+                        Pair* next, cudaStream_t s) {
+  k_emit<<<(nF + kT - 1) / kT, kT, 0, s>>>(Q.left, R.left, F, nF, slot, next);
+  return cudaGetLastError();
 }
 
 }  // namespace dfgt

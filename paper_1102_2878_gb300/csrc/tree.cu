@@ -383,6 +383,10 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   t->P = ipow_c(t->pm, d);
   t->p_limit = (opts && opts->p_max > 0) ? std::min(opts->p_max, t->pm) : t->pm;
   t->eps_fp = (opts && opts->eps_fp > 0) ? opts->eps_fp : 2e-5;
+  {
+    const long long bb = opts ? opts->base_block : 0;
+    t->base_block = bb > 0 ? bb : bb < 0 ? 0 : 4LL * t->leaf * t->leaf;
+  }
   t->lvl_off.assign(1, 0);
 
   // level-build scratch: two point buffers, per-point node ids, flags,

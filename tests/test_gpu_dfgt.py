@@ -109,12 +109,12 @@ def test_repeatable_and_batched_equals_single(dev):
         assert np.allclose(Gi.cpu().numpy()[0], G1.cpu().numpy()[i], rtol=1e-12, atol=0)
 
 
-def test_forced_work_list_overflow_is_retried(dev, orc):
+def test_small_work_lists_are_drained_early(dev, orc):
     x = datagen.anisotropic_mixture(8000, 3, 8, 1e-4, 1e-2, seed=9)
     t = dfgt.Tree(dev, to_cuda(x), leaf_size=16)
     dev.set_capacity(64, 64)
     G, st = dfgt.kde_sum(dev, t, t, [0.01, 0.1], 1e-2)
-    assert st["overflow_retries"] > 0
+    assert st["list_flushes"] > 0
     x64 = x.astype(np.float64)
     for i, h in enumerate([0.01, 0.1]):
         check_eps(G.cpu().numpy()[i], orc.naive_kde(x64, x64, h), 1e-2)

@@ -39,7 +39,7 @@ def run_workload(dev, orc, name, nsample, n=None):
 
 def test_kde3d_n2e5_sweep10(dev, orc):
     st = run_workload(dev, orc, "kde3d_n2e5_sweep10", 200)
-    assert st["overflow_retries"] >= 0
+    assert st["rounds"] > 0
 
 
 def test_kde5d_n5e5(dev, orc):
