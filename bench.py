@@ -34,7 +34,9 @@ from paper_1102_2878_gb300 import datagen  # noqa: E402
 METRIC = "effective query-ref pairs/s (|Q|·|R|/time) at ε=1e-2, DFGT vs GPU brute force"
 UNIT = "pairs/s"
 DEFAULT_WORKLOAD = "kde3d_n2e5_sweep10"
-SM_COUNT, SFU_EX2_PER_CLK_PER_SM = 152, 16
+# GB300: 152 SMs; the special-function unit retires 32 ex2 per clock per SM
+# (a throughput probe measured 30.3 ex2/clk/SM at 2070 MHz)
+SM_COUNT, SFU_EX2_PER_CLK_PER_SM = 152, 32
 
 
 def dist_env():
@@ -176,10 +178,15 @@ def run_dfgt(args, rank, world, local):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     torch.cuda.synchronize()
 
+    ev_build = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
     def step():
+        ev_build[0].record(ctx.stream)
         tree = dfgt.Tree(ctx, pts)
+        ev_build[1].record(ctx.stream)
         G, st = dfgt.kde_sum(ctx, tree, tree, hs, eps)
         tree.close()
+        st["ms_build"] = ev_build[0].elapsed_time(ev_build[1])
         return G, st
 
     for _ in range(args.warmup):
@@ -245,17 +252,18 @@ def run_dfgt(args, rank, world, local):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the exact leaf-pair sums): one ex2 per
-    # pair interaction plus ~2D+2 FP32 ops, ALU-bound on the SFU ex2 rate
+    # roofline of the dominant kernel (the exact sums): one ex2 per pair
+    # interaction, bounded by the SFU ex2 issue rate
     inter = statistics.mean(s["base_interactions"] for s in stats)
     base_ms = statistics.mean(s["ms_base"] for s in stats)
     peaks = measured_peaks()
     sm_clk = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak = SM_COUNT * SFU_EX2_PER_CLK_PER_SM * sm_clk * 1e6
     achieved = inter / (base_ms / 1e3) if base_ms > 0 else 0.0
-    roof = {"bound": "alu", "kernel": "k_base (DFGTBase leaf-pair sums)", "achieved": achieved,
+    roof = {"bound": "alu", "kernel": "k_base (DFGTBase exact sums)", "achieved": achieved,
             "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": f"152 SMs x 16 ex2/clk x {sm_clk:.0f} MHz (unit counts)"}
+            "traffic": None,
+            "peak_source": f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz (unit counts)"}
     cpu_rate, cpu_desc, cores = (None, None, None)
     if not args.no_cpu_baseline:
         cpu_rate, cpu_desc, cores = cpu_oracle_rate(x, hs, args.cpu_seconds)
@@ -272,7 +280,8 @@ def run_dfgt(args, rank, world, local):
         "bruteforce": {"value": world * pairs_step / (bf / 1e3), "unit": UNIT, "ms_per_step": bf},
         "speedup_vs_bruteforce": bf / ms,
         "max_rel_err_vs_bruteforce": rel,
-        "breakdown_ms": {"traverse": mean("ms_traverse"), "base": mean("ms_base"),
+        "breakdown_ms": {"build": mean("ms_build"), "classify": mean("ms_classify"),
+                         "traverse": mean("ms_traverse"), "base": mean("ms_base"),
                          "farfield": mean("ms_farfield"), "local": mean("ms_local"),
                          "f2l": mean("ms_f2l"), "post": mean("ms_post")},
         "work": {"pairs_visited": mean("pairs_visited"), "prune": mean("n_prune"),

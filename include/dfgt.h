@@ -73,6 +73,7 @@ typedef struct {
   int rounds;                   /* level-synchronous traversal rounds */
   int list_flushes;             /* times an action list was drained before the traversal ended */
   double ms_traverse;           /* device time of the traversal rounds (with early list drains) */
+  double ms_classify;           /* device time of the classification kernels of all rounds */
   double ms_actions;            /* device time of the final list drains */
   double ms_post;               /* device time of the downward pass and finalisation */
   double ms_base;               /* device time of every base-case (DFGTBase) launch */

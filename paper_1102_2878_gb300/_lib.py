@@ -29,7 +29,8 @@ class Stats(C.Structure):
                 ("n_f2l", C.c_longlong), ("n_base", C.c_longlong),
                 ("base_interactions", C.c_longlong), ("kernel_launches", C.c_longlong),
                 ("rounds", C.c_int), ("list_flushes", C.c_int),
-                ("ms_traverse", C.c_double), ("ms_actions", C.c_double), ("ms_post", C.c_double),
+                ("ms_traverse", C.c_double), ("ms_classify", C.c_double), ("ms_actions", C.c_double),
+                ("ms_post", C.c_double),
                 ("ms_base", C.c_double), ("ms_farfield", C.c_double), ("ms_local", C.c_double),
                 ("ms_f2l", C.c_double)]
 

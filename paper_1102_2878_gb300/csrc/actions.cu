@@ -103,41 +103,88 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 }
 
 // ------------------------------------------------------------------ base
-// DFGTBase: exact sum over a leaf pair.  Lane per query, references read
-// as broadcast loads, float32 exp2 on the SFU.
+// DFGTBase: exact sums over the listed node pairs.  The list is first
+// grouped by (bandwidth, query node) with a counting sort; one warp then
+// owns a group, keeps its queries in registers and streams the points of
+// every reference node of the group.  For |Q| < 32 the warp is split into
+// 32/g lane groups (g = |Q| rounded up to a power of two) that share the
+// queries and divide the references; the partial sums are combined with
+// shuffles and each query receives one float64 atomic add per group.
+// Each reference node's run is summed in float32 and the runs are added
+// with Kahan compensation.
+
+__global__ void k_base_count(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Pair p = list[i];
+  atomicAdd(&cnt[(size_t)p.h * nnQ + p.q], 1);
+}
+
+__global__ void k_base_scatter(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cursor,
+                               int* __restrict__ rsorted) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Pair p = list[i];
+  rsorted[atomicAdd(&cursor[(size_t)p.h * nnQ + p.q], 1)] = p.r;
+}
+
 template <int D>
-__global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const Pair* __restrict__ list,
-                                             int n, const double* __restrict__ hv,
+__global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ off,
+                                             const int* __restrict__ rsorted, int nkeys,
+                                             const double* __restrict__ hv,
                                              double* __restrict__ gacc) {
   constexpr int DD = D > 0 ? D : kMaxD;
   const int d = D > 0 ? D : Q.d;
   const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  const Pair pr = list[w];
-  const double h = hv[pr.h];
+  if (w >= nkeys) return;
+  const int g0 = off[w], g1 = off[w + 1];
+  if (g0 == g1) return;
+  const int hidx = w / Q.nn, q = w % Q.nn;
+  const double h = hv[hidx];
   const float c2 = (float)(-kLog2e / (2.0 * h * h));
-  const int qb = Q.beg[pr.q], qn = Q.cnt[pr.q], rb = R.beg[pr.r], rn = R.cnt[pr.r];
-  for (int qi = lane; qi < qn; qi += 32) {
+  const int qb = Q.beg[q], qn = Q.cnt[q];
+  int g = 32;
+  while (g > 1 && g / 2 >= qn) g >>= 1;
+  const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
+  for (int q0 = 0; q0 < qn; q0 += g) {
+    const int qi = q0 + ql;
+    const bool ok = qi < qn;
     float qv[DD];
-    if constexpr (D > 0) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
-    else
-      for (int k = 0; k < d; ++k) qv[k] = Q.pts[(size_t)(qb + qi) * Q.dp + k];
-    float s = 0.f;
-#pragma unroll 4
-    for (int j = 0; j < rn; ++j) {
-      float rv[DD];
-      if constexpr (D > 0) load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
-      float d2 = 0.f;
-      if constexpr (D > 0) {
+    if (ok) {
+      if constexpr (D > 0) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
+      else
+        for (int k = 0; k < d; ++k) qv[k] = Q.pts[(size_t)(qb + qi) * Q.dp + k];
+    } else {
 #pragma unroll
-        for (int k = 0; k < D; ++k) { const float t = qv[k] - rv[k]; d2 = fmaf(t, t, d2); }
-      } else {
-        for (int k = 0; k < d; ++k) { const float t = qv[k] - R.pts[(size_t)(rb + j) * R.dp + k]; d2 = fmaf(t, t, d2); }
-      }
-      s += ex2_approx(d2 * c2);
+      for (int k = 0; k < DD; ++k) qv[k] = 0.f;
     }
-    atomicAdd(&gacc[(size_t)pr.h * Q.n + qb + qi], (double)s);
+    float S = 0.f, C = 0.f;
+    for (int t = g0; t < g1; ++t) {
+      const int r = rsorted[t];
+      const int rb = R.beg[r], rn = R.cnt[r];
+      float part = 0.f;
+#pragma unroll 4
+      for (int j = gid; j < rn; j += ngrp) {
+        float d2 = 0.f;
+        if constexpr (D > 0) {
+          float rv[D];
+          load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
+#pragma unroll
+          for (int k = 0; k < D; ++k) { const float tt = qv[k] - rv[k]; d2 = fmaf(tt, tt, d2); }
+        } else {
+          for (int k = 0; k < d; ++k) { const float tt = qv[k] - R.pts[(size_t)(rb + j) * R.dp + k]; d2 = fmaf(tt, tt, d2); }
+        }
+        part += ex2_approx(d2 * c2);
+      }
+      const float y = part - C;
+      const float tt = S + y;
+      C = (tt - S) - y;
+      S = tt;
+    }
+    double v = (double)S - (double)C;
+    for (int o = g; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (gid == 0 && ok) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], v);
   }
 }
 
@@ -601,14 +648,27 @@ inline int warp_grid(long items) { return (int)((items * 32 + kT - 1) / kT); }
   }
 
 cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                        const Pair* list, int n, cudaStream_t s) {
+                        const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches) {
   if (n <= 0) return cudaSuccess;
-  const int g = warp_grid(n);
+  const long nkeys = (long)b.nh * Q.nn;
+  cudaError_t e;
+  if ((e = sc.cnt->ensure((nkeys + 1) * sizeof(int))) != cudaSuccess) return e;
+  if ((e = sc.off->ensure((nkeys + 1) * sizeof(int))) != cudaSuccess) return e;
+  if ((e = sc.rsorted->ensure((size_t)n * sizeof(int))) != cudaSuccess) return e;
+  int* cnt = sc.cnt->as<int>();
+  int* off = sc.off->as<int>();
+  if ((e = cudaMemsetAsync(cnt, 0, nkeys * sizeof(int), s)) != cudaSuccess) return e;
+  k_base_count<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, cnt);
+  if ((e = scan_exclusive(cnt, off, (int)nkeys, *sc.scan_tmp, s, launches)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(cnt, off, nkeys * sizeof(int), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+  k_base_scatter<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, cnt, sc.rsorted->as<int>());
+  const int g = warp_grid(nkeys);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc));
+    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, off, sc.rsorted->as<int>(), (int)nkeys, b.h, b.gacc));
   } else {
-    k_base<0><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc);
+    k_base<0><<<g, kT, 0, s>>>(Q, R, off, sc.rsorted->as<int>(), (int)nkeys, b.h, b.gacc);
   }
+  *launches += 3;
   return cudaGetLastError();
 }
 

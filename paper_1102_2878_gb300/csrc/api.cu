@@ -130,7 +130,10 @@ dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const
     ls.collect();
   }
   CK(cudaEventRecord(ls.e0, s));
-  if (which == 0) CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), ls.count, s));
+  if (which == 0) {
+    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+    CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), ls.count, sc, s, &ctx->launches));
+  }
   else if (which == 1) CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), ls.count, s));
   else if (which == 2) CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), ls.count, s));
   else CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), ls.count, s));
@@ -165,6 +168,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     lists[w].e1 = ctx->ev[9 + 2 * w];
   }
   int flushes = 0;
+  double ms_classify = 0.0;
   CK(cudaEventRecord(ctx->ev[0], s));
   CK(launch_init_frontier(ctx->frontier[0].as<Pair>(), nh, s));
   ++ctx->launches;
@@ -192,6 +196,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       if (rc != DFGT_OK) return rc;
     }
     CK(ctx->slots.ensure((size_t)nF * sizeof(int)));
+    CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_fold(b, qt->nn, s));
     CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
     CK(cudaMemsetAsync(&dctr->n_next, 0, sizeof(int), s));
@@ -200,8 +205,14 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
                        ctx->list_f2l.as<Action>(), ctx->list_base.as<Pair>(), (int)ctx->cap_lists,
                        dctr, s));
     ctx->launches += 3;
+    CK(cudaEventRecord(ctx->ev[7], s));
     CK(cudaMemcpyAsync(hc, dctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ctx->ev[6], ctx->ev[7]);
+      ms_classify += t;
+    }
     if (hc->status & kStOverflow) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: action list overflow");
     visited += nF;
     ++rounds;
@@ -245,6 +256,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]);
     st->ms_traverse = ms;
+    st->ms_classify = ms_classify;
     cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
     st->ms_actions = ms;
     st->ms_base = lists[0].ms;
@@ -301,6 +313,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1], &ctx->slots,
+                    &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g};
   for (DevBuf* b : bufs) b->release();
@@ -485,7 +498,8 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   CK(up(ctx->list_f2l, f2l.data(), f2l.size() * sizeof(Action)));
   const TreeView Q = qt->view(), R = rt->view();
   CK(launch_prune_apply(Q, R, b, ctx->frontier[0].as<Pair>(), (int)prune.size(), s));
-  CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), (int)base.size(), s));
+  BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+  CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), (int)base.size(), sc, s, &ctx->launches));
   CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), (int)far.size(), s));
   CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), (int)loc.size(), s));
   CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), (int)f2l.size(), s));

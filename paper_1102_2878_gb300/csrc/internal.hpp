@@ -54,6 +54,7 @@ struct dfgt_ctx {
   DevBuf hvals;          // bandwidths
   DevBuf frontier[2];    // Pair
   DevBuf slots;          // int child slot per frontier pair
+  DevBuf grp_cnt, grp_off, grp_r;  // base-case grouping scratch
   DevBuf list_far, list_loc, list_f2l, list_base;  // Action / Pair
   DevBuf node_state;     // u64 inherited/decided/incr/lbsum
   DevBuf lmom;           // double local moments [nh][nn][P]
@@ -61,7 +62,7 @@ struct dfgt_ctx {
   DevBuf gacc;           // double [nh][nq]
   DevBuf io_q, io_r, io_g;  // dfgt_kde_host staging
   size_t cap_frontier = 1 << 20;
-  size_t cap_lists = 1 << 20;
+  size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned
   cudaEvent_t ev[16] = {};
 };
@@ -137,8 +138,15 @@ cudaError_t launch_emit(const TreeView& Q, const TreeView& R, const Pair* F, int
                         Pair* next, cudaStream_t s);
 cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s);
 
+// Scratch of the base-case grouping (counting sort by bandwidth and query node).
+struct BaseScratch {
+  DevBuf* cnt;
+  DevBuf* off;
+  DevBuf* rsorted;
+  DevBuf* scan_tmp;
+};
 cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                        const Pair* list, int n, cudaStream_t s);
+                        const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
 cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                             const Action* list, int n, cudaStream_t s);
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,

@@ -158,7 +158,10 @@ def test_prune_and_base_operators(setup, orc, dev):
         x = ((Qp[:, None, :] - Rp[None, :, :]) ** 2).sum(2) / (2 * h * h)
         K = np.exp(-x)
         tol[qi] += (K * (2.0 ** -21 + (D + 3) * U * x)).sum(1) + 24 * U * K.sum(1)
-    assert np.all(np.abs(G - want) <= tol + 1e-300)
+        # terms below the float32 normal range flush to zero
+        tol[qi] += np.where(K < 2.0 ** -125, K, 0.0).sum(1)
+    bad = np.abs(G - want) > tol + 1e-300
+    assert not bad.any(), (np.flatnonzero(bad)[:5], G[bad][:5], want[bad][:5], tol[bad][:5])
     assert (want > 0).sum() > 0
 
 
