@@ -103,15 +103,29 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 }
 
 // ------------------------------------------------------------------ base
-// DFGTBase: exact sums over the listed node pairs.  The list is first
-// grouped by (bandwidth, query node) with a counting sort; one warp then
-// owns a group, keeps its queries in registers and streams the points of
-// every reference node of the group.  For |Q| < 32 the warp is split into
-// 32/g lane groups (g = |Q| rounded up to a power of two) that share the
-// queries and divide the references; the partial sums are combined with
-// shuffles and each query receives one float64 atomic add per group.
-// Each reference node's run is summed in float32 and the runs are added
-// with Kahan compensation.
+// DFGTBase: exact sums over the listed node pairs.
+//
+// The list is sorted by (bandwidth, query node) with a counting sort, and
+// each warp takes a chunk of kBaseChunk consecutive sorted entries, so the
+// entries of one query node mostly share a warp: the queries stay in
+// registers across them and each query receives one float64 atomic add per
+// run of entries instead of one per pair.  The chunk's descriptors are
+// loaded in one round trip (one per lane) and broadcast with shuffles.
+//
+// Reference points are staged per warp in shared memory, negated, as
+// structure-of-arrays tiles of kTile points, so one 64-bit load yields the
+// coordinate of two consecutive references and every FP32 step works on
+// two interactions at once (packed f32x2 add / fma / mul).  Per pair of
+// interactions that is 2D+2 packed ops and two SFU ex2, so the kernel is
+// bound by the ex2 rate rather than by instruction issue.  For |Q| < 32 the
+// warp is split into 32/g lane groups (g = |Q| rounded up to a power of
+// two) that share the queries and divide the reference pairs.  A run of
+// one reference node is summed in float32; runs are added with Kahan
+// compensation and lane groups are combined in float64.
+
+constexpr int kBaseChunk = 8;
+constexpr int kTile = 64;
+constexpr float kFarNeg = -1.0e18f;  // padding point: contributes exp(-huge) = 0
 
 __global__ void k_base_count(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,70 +135,138 @@ __global__ void k_base_count(const Pair* __restrict__ list, int n, int nnQ, int*
 }
 
 __global__ void k_base_scatter(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cursor,
-                               int* __restrict__ rsorted) {
+                               int* __restrict__ rsorted, int* __restrict__ ksorted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Pair p = list[i];
-  rsorted[atomicAdd(&cursor[(size_t)p.h * nnQ + p.q], 1)] = p.r;
+  const int key = p.h * nnQ + p.q;
+  const int pos = atomicAdd(&cursor[key], 1);
+  rsorted[pos] = p.r;
+  ksorted[pos] = key;
 }
 
 template <int D>
-__global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ off,
-                                             const int* __restrict__ rsorted, int nkeys,
+__global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
+                                             const int* __restrict__ ksorted, int n,
                                              const double* __restrict__ hv,
                                              double* __restrict__ gacc) {
-  constexpr int DD = D > 0 ? D : kMaxD;
-  const int d = D > 0 ? D : Q.d;
-  const int w = (blockIdx.x * kT + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= nkeys) return;
-  const int g0 = off[w], g1 = off[w + 1];
-  if (g0 == g1) return;
-  const int hidx = w / Q.nn, q = w % Q.nn;
-  const double h = hv[hidx];
-  const float c2 = (float)(-kLog2e / (2.0 * h * h));
-  const int qb = Q.beg[q], qn = Q.cnt[q];
-  int g = 32;
-  while (g > 1 && g / 2 >= qn) g >>= 1;
-  const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
-  for (int q0 = 0; q0 < qn; q0 += g) {
-    const int qi = q0 + ql;
-    const bool ok = qi < qn;
-    float qv[DD];
-    if (ok) {
-      if constexpr (D > 0) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
+  __shared__ __align__(16) float sR[kWarpsPerBlock][D][kTile];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
+  if (i0 >= n) return;
+  const int m = (int)min((long)kBaseChunk, n - i0);
+  int my_key = -1, my_rb = 0, my_rn = 0;
+  if (lane < m) {
+    my_key = ksorted[i0 + lane];
+    const int r = rsorted[i0 + lane];
+    my_rb = R.beg[r];
+    my_rn = R.cnt[r];
+  }
+  int t = 0;
+  while (t < m) {
+    const int key = __shfl_sync(0xffffffffu, my_key, t);
+    int e = t + 1;
+    while (e < m && __shfl_sync(0xffffffffu, my_key, e) == key) ++e;
+    const int hidx = key / Q.nn, q = key % Q.nn;
+    const double h = hv[hidx];
+    const float c2 = (float)(-kLog2e / (2.0 * h * h));
+    const float2 c2p = make_float2(c2, c2);
+    const int qb = Q.beg[q], qn = Q.cnt[q];
+    int g = 32;
+    while (g > 1 && g / 2 >= qn) g >>= 1;
+    const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
+    for (int q0 = 0; q0 < qn; q0 += g) {
+      const int qi = q0 + ql;
+      const bool ok = qi < qn;
+      float qv[D];
+      if (ok) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
       else
-        for (int k = 0; k < d; ++k) qv[k] = Q.pts[(size_t)(qb + qi) * Q.dp + k];
-    } else {
 #pragma unroll
-      for (int k = 0; k < DD; ++k) qv[k] = 0.f;
+        for (int k = 0; k < D; ++k) qv[k] = 0.f;
+      float2 qq[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) qq[k] = make_float2(qv[k], qv[k]);
+      float S = 0.f, C = 0.f;
+      for (int u = t; u < e; ++u) {
+        const int rb = __shfl_sync(0xffffffffu, my_rb, u);
+        const int rn = __shfl_sync(0xffffffffu, my_rn, u);
+        float2 part = make_float2(0.f, 0.f);
+        for (int j0 = 0; j0 < rn; j0 += kTile) {
+          const int tn = min(kTile, rn - j0);
+          const int tn2 = (tn + 1) & ~1;
+          __syncwarp();
+          for (int jj = lane; jj < tn2; jj += 32) {
+            if (jj < tn) {
+              float rv[D];
+              load_point<D>(R.pts + (size_t)(rb + j0 + jj) * R.dp, rv);
+#pragma unroll
+              for (int k = 0; k < D; ++k) sR[wib][k][jj] = -rv[k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < D; ++k) sR[wib][k][jj] = kFarNeg;
+            }
+          }
+          __syncwarp();
+#pragma unroll 2
+          for (int jp = 2 * gid; jp < tn2; jp += 2 * ngrp) {
+            float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+              const float2 rr = *reinterpret_cast<const float2*>(&sR[wib][k][jp]);
+              const float2 dd = __fadd2_rn(qq[k], rr);
+              d2 = __ffma2_rn(dd, dd, d2);
+            }
+            const float2 a = __fmul2_rn(d2, c2p);
+            part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
+          }
+        }
+        const float y = (part.x + part.y) - C;
+        const float tt = S + y;
+        C = (tt - S) - y;
+        S = tt;
+      }
+      double v = (double)S - (double)C;
+      for (int o = g; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (gid == 0 && ok) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], v);
     }
-    float S = 0.f, C = 0.f;
-    for (int t = g0; t < g1; ++t) {
-      const int r = rsorted[t];
-      const int rb = R.beg[r], rn = R.cnt[r];
-      float part = 0.f;
-#pragma unroll 4
-      for (int j = gid; j < rn; j += ngrp) {
-        float d2 = 0.f;
-        if constexpr (D > 0) {
-          float rv[D];
-          load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
+    t = e;
+  }
+}
+
+// D >= 6: the same chunked walk with runtime dimension and scalar math.
+__global__ void __launch_bounds__(kT) k_base_g(TreeView Q, TreeView R, const int* __restrict__ rsorted,
+                                               const int* __restrict__ ksorted, int n,
+                                               const double* __restrict__ hv,
+                                               double* __restrict__ gacc) {
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
+  if (i0 >= n) return;
+  const int m = (int)min((long)kBaseChunk, n - i0);
+  const int d = Q.d;
+  for (int u = 0; u < m; ++u) {
+    const int key = ksorted[i0 + u], r = rsorted[i0 + u];
+    const int hidx = key / Q.nn, q = key % Q.nn;
+    const double h = hv[hidx];
+    const float c2 = (float)(-kLog2e / (2.0 * h * h));
+    const int qb = Q.beg[q], qn = Q.cnt[q], rb = R.beg[r], rn = R.cnt[r];
+    for (int qi = lane; qi < qn; qi += 32) {
+      float qv[kMaxD];
 #pragma unroll
-          for (int k = 0; k < D; ++k) { const float tt = qv[k] - rv[k]; d2 = fmaf(tt, tt, d2); }
-        } else {
-          for (int k = 0; k < d; ++k) { const float tt = qv[k] - R.pts[(size_t)(rb + j) * R.dp + k]; d2 = fmaf(tt, tt, d2); }
+      for (int k = 0; k < kMaxD; ++k) qv[k] = k < d ? Q.pts[(size_t)(qb + qi) * Q.dp + k] : 0.f;
+      float part = 0.f;
+      for (int j = 0; j < rn; ++j) {
+        float d2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < kMaxD; ++k) {
+          if (k < d) {
+            const float tt = qv[k] - R.pts[(size_t)(rb + j) * R.dp + k];
+            d2 = fmaf(tt, tt, d2);
+          }
         }
         part += ex2_approx(d2 * c2);
       }
-      const float y = part - C;
-      const float tt = S + y;
-      C = (tt - S) - y;
-      S = tt;
+      atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], (double)part);
     }
-    double v = (double)S - (double)C;
-    for (int o = g; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (gid == 0 && ok) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], v);
   }
 }
 
@@ -654,19 +736,21 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
   cudaError_t e;
   if ((e = sc.cnt->ensure((nkeys + 1) * sizeof(int))) != cudaSuccess) return e;
   if ((e = sc.off->ensure((nkeys + 1) * sizeof(int))) != cudaSuccess) return e;
-  if ((e = sc.rsorted->ensure((size_t)n * sizeof(int))) != cudaSuccess) return e;
+  if ((e = sc.rsorted->ensure(2 * (size_t)n * sizeof(int))) != cudaSuccess) return e;
   int* cnt = sc.cnt->as<int>();
   int* off = sc.off->as<int>();
+  int* rsorted = sc.rsorted->as<int>();
+  int* ksorted = rsorted + n;
   if ((e = cudaMemsetAsync(cnt, 0, nkeys * sizeof(int), s)) != cudaSuccess) return e;
   k_base_count<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, cnt);
   if ((e = scan_exclusive(cnt, off, (int)nkeys, *sc.scan_tmp, s, launches)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(cnt, off, nkeys * sizeof(int), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
-  k_base_scatter<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, cnt, sc.rsorted->as<int>());
-  const int g = warp_grid(nkeys);
+  k_base_scatter<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, off, rsorted, ksorted);
+  const long warps = (n + kBaseChunk - 1) / kBaseChunk;
+  const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, off, sc.rsorted->as<int>(), (int)nkeys, b.h, b.gacc));
+    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc));
   } else {
-    k_base<0><<<g, kT, 0, s>>>(Q, R, off, sc.rsorted->as<int>(), (int)nkeys, b.h, b.gacc);
+    k_base_g<<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc);
   }
   *launches += 3;
   return cudaGetLastError();

@@ -2,18 +2,23 @@
 // (NaiveKDE without its normalisation), for several bandwidths at once.
 //
 // One thread owns one query; the block streams reference tiles through
-// shared memory.  The squared distance of a pair is computed once (direct
-// differences, float32) and reused for every bandwidth of the chunk:
-// exp(-d2/2h^2) = 2^(d2 * c_h) with c_h = -log2(e)/(2h^2) on the SFU.
-// Each run of 32 references is summed in float32 and the runs are added
-// with Kahan compensation, so the result is accurate to a few float32 ulps.
+// shared memory, stored negated as structure-of-arrays so one 64-bit load
+// gives one coordinate of two consecutive references.  The squared
+// distances of the two pairs (direct differences) are formed with packed
+// f32x2 add / fma and reused for every bandwidth of the chunk:
+// exp(-d2/2h^2) = 2^(d2 * c_h), c_h = -log2(e)/(2h^2), on the SFU.  With
+// n_h bandwidths a pair of references costs 2D + 2 n_h packed FP32 ops and
+// 2 n_h ex2, so the loop is bound by the ex2 rate.  Each run of 32
+// references is summed in float32 and the runs are added with Kahan
+// compensation.
 #include "internal.hpp"
 
 namespace dfgt {
 namespace {
 
 constexpr int kBfThreads = 128;
-constexpr int kBfTile = 128;
+constexpr int kBfTile = 128;           // references per shared-memory tile (even)
+constexpr float kFarNeg = -1.0e18f;    // padding reference: contributes 0
 
 template <int NHB>
 struct HChunk {
@@ -23,19 +28,82 @@ struct HChunk {
 template <int D, int NHB>
 __global__ void __launch_bounds__(kBfThreads) k_bruteforce(const float* __restrict__ q, int nq,
                                                            const float* __restrict__ r, int nr,
-                                                           int d_rt, HChunk<NHB> hc,
-                                                           double* __restrict__ G, int ldg) {
-  constexpr int DD = D > 0 ? D : kMaxD;
-  const int d = D > 0 ? D : d_rt;
-  __shared__ float sr[kBfTile * DD];
+                                                           HChunk<NHB> hc, double* __restrict__ G,
+                                                           int ldg) {
+  __shared__ __align__(16) float sr[D][kBfTile];
   const int qi = blockIdx.x * kBfThreads + threadIdx.x;
-  float qv[DD];
+  float2 qq[D];
 #pragma unroll
-  for (int k = 0; k < DD; ++k) qv[k] = (k < d && qi < nq) ? q[(size_t)qi * d + k] : 0.f;
+  for (int k = 0; k < D; ++k) {
+    const float v = qi < nq ? q[(size_t)qi * D + k] : 0.f;
+    qq[k] = make_float2(v, v);
+  }
+  float2 cp[NHB];
+  float S[NHB], C[NHB];
+#pragma unroll
+  for (int hh = 0; hh < NHB; ++hh) {
+    cp[hh] = make_float2(hc.c[hh], hc.c[hh]);
+    S[hh] = C[hh] = 0.f;
+  }
+  for (int t0 = 0; t0 < nr; t0 += kBfTile) {
+    const int tn = min(kBfTile, nr - t0);
+    const int tn2 = (tn + 1) & ~1;
+    __syncthreads();
+    for (int e = threadIdx.x; e < tn2 * D; e += kBfThreads) {
+      const int j = e / D, k = e % D;
+      sr[k][j] = j < tn ? -r[(size_t)(t0 + j) * D + k] : kFarNeg;
+    }
+    __syncthreads();
+    for (int j0 = 0; j0 < tn2; j0 += 32) {
+      const int je = min(j0 + 32, tn2);
+      float2 part[NHB];
+#pragma unroll
+      for (int hh = 0; hh < NHB; ++hh) part[hh] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int j = j0; j < je; j += 2) {
+        float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float2 rr = *reinterpret_cast<const float2*>(&sr[k][j]);
+          const float2 dd = __fadd2_rn(qq[k], rr);
+          d2 = __ffma2_rn(dd, dd, d2);
+        }
+#pragma unroll
+        for (int hh = 0; hh < NHB; ++hh) {
+          const float2 a = __fmul2_rn(d2, cp[hh]);
+          part[hh] = __fadd2_rn(part[hh], make_float2(ex2_approx(a.x), ex2_approx(a.y)));
+        }
+      }
+#pragma unroll
+      for (int hh = 0; hh < NHB; ++hh) {
+        const float y = (part[hh].x + part[hh].y) - C[hh];
+        const float t = S[hh] + y;
+        C[hh] = (t - S[hh]) - y;
+        S[hh] = t;
+      }
+    }
+  }
+  if (qi < nq) {
+#pragma unroll
+    for (int hh = 0; hh < NHB; ++hh) G[(size_t)hh * ldg + qi] = (double)S[hh] - (double)C[hh];
+  }
+}
+
+// Any dimension up to 32, scalar math (dimensions above 5 are not the
+// exp-bound case: the 2D distance flops dominate there).
+template <int NHB>
+__global__ void __launch_bounds__(kBfThreads) k_bruteforce_g(const float* __restrict__ q, int nq,
+                                                             const float* __restrict__ r, int nr,
+                                                             int d, HChunk<NHB> hc,
+                                                             double* __restrict__ G, int ldg) {
+  __shared__ float sr[kBfTile * kMaxD];
+  const int qi = blockIdx.x * kBfThreads + threadIdx.x;
+  float qv[kMaxD];
+#pragma unroll
+  for (int k = 0; k < kMaxD; ++k) qv[k] = (k < d && qi < nq) ? q[(size_t)qi * d + k] : 0.f;
   float S[NHB], C[NHB];
 #pragma unroll
   for (int hh = 0; hh < NHB; ++hh) S[hh] = C[hh] = 0.f;
-
   for (int t0 = 0; t0 < nr; t0 += kBfTile) {
     const int tn = min(kBfTile, nr - t0);
     __syncthreads();
@@ -46,13 +114,12 @@ __global__ void __launch_bounds__(kBfThreads) k_bruteforce(const float* __restri
       float part[NHB];
 #pragma unroll
       for (int hh = 0; hh < NHB; ++hh) part[hh] = 0.f;
-#pragma unroll 4
       for (int j = j0; j < je; ++j) {
         float d2 = 0.f;
 #pragma unroll
-        for (int k = 0; k < DD; ++k) {
+        for (int k = 0; k < kMaxD; ++k) {
           if (k < d) {
-            float t = qv[k] - sr[j * d + k];
+            const float t = qv[k] - sr[j * d + k];
             d2 = fmaf(t, t, d2);
           }
         }
@@ -61,8 +128,8 @@ __global__ void __launch_bounds__(kBfThreads) k_bruteforce(const float* __restri
       }
 #pragma unroll
       for (int hh = 0; hh < NHB; ++hh) {
-        float y = part[hh] - C[hh];
-        float t = S[hh] + y;
+        const float y = part[hh] - C[hh];
+        const float t = S[hh] + y;
         C[hh] = (t - S[hh]) - y;
         S[hh] = t;
       }
@@ -80,23 +147,33 @@ cudaError_t launch_chunk(const float* q, int nq, const float* r, int nr, int d, 
   HChunk<NHB> hc;
   for (int i = 0; i < NHB; ++i) hc.c[i] = (float)(-kLog2e / (2.0 * h[i] * h[i]));
   const int grid = (nq + kBfThreads - 1) / kBfThreads;
-  k_bruteforce<D, NHB><<<grid, kBfThreads, 0, s>>>(q, nq, r, nr, d, hc, G, ldg);
+  if constexpr (D > 0)
+    k_bruteforce<D, NHB><<<grid, kBfThreads, 0, s>>>(q, nq, r, nr, hc, G, ldg);
+  else
+    k_bruteforce_g<NHB><<<grid, kBfThreads, 0, s>>>(q, nq, r, nr, d, hc, G, ldg);
   return cudaGetLastError();
 }
 
+// Bandwidths are processed in chunks whose sizes have a compiled variant;
+// the largest variant that fits the remainder is taken.
 template <int D>
 cudaError_t launch_d(const float* q, int nq, const float* r, int nr, int d, const double* h,
                      int nh, double* G, cudaStream_t s, long long* launches) {
   int done = 0;
   while (done < nh) {
     const int rem = nh - done;
+    const double* hp = h + done;
+    double* Gp = G + (size_t)done * nq;
     cudaError_t e;
     int take;
-    if (rem >= 16) { take = 16; e = launch_chunk<D, 16>(q, nq, r, nr, d, h + done, G + (size_t)done * nq, nq, s); }
-    else if (rem >= 8) { take = 8; e = launch_chunk<D, 8>(q, nq, r, nr, d, h + done, G + (size_t)done * nq, nq, s); }
-    else if (rem >= 4) { take = 4; e = launch_chunk<D, 4>(q, nq, r, nr, d, h + done, G + (size_t)done * nq, nq, s); }
-    else if (rem >= 2) { take = 2; e = launch_chunk<D, 2>(q, nq, r, nr, d, h + done, G + (size_t)done * nq, nq, s); }
-    else { take = 1; e = launch_chunk<D, 1>(q, nq, r, nr, d, h + done, G + (size_t)done * nq, nq, s); }
+    if (rem >= 16) { take = 16; e = launch_chunk<D, 16>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else if (rem >= 12) { take = 12; e = launch_chunk<D, 12>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else if (rem >= 10) { take = 10; e = launch_chunk<D, 10>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else if (rem >= 8) { take = 8; e = launch_chunk<D, 8>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else if (rem >= 6) { take = 6; e = launch_chunk<D, 6>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else if (rem >= 4) { take = 4; e = launch_chunk<D, 4>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else if (rem >= 2) { take = 2; e = launch_chunk<D, 2>(q, nq, r, nr, d, hp, Gp, nq, s); }
+    else { take = 1; e = launch_chunk<D, 1>(q, nq, r, nr, d, hp, Gp, nq, s); }
     ++*launches;
     if (e != cudaSuccess) return e;
     done += take;
