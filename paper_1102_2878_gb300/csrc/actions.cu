@@ -124,7 +124,7 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 // compensation and lane groups are combined in float64.
 
 constexpr int kBaseChunk = 8;
-constexpr int kTile = 64;
+constexpr int kTile = 256;
 constexpr float kFarNeg = -1.0e18f;  // padding point: contributes exp(-huge) = 0
 
 __global__ void k_base_count(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cnt) {
@@ -143,6 +143,22 @@ __global__ void k_base_scatter(const Pair* __restrict__ list, int n, int nnQ, in
   const int pos = atomicAdd(&cursor[key], 1);
   rsorted[pos] = p.r;
   ksorted[pos] = key;
+}
+
+// Lane-group width for |Q| queries: the power of two g <= 32 that leaves the
+// fewest idle query slots in ceil(|Q|/g) passes (ties go to the larger g).
+__device__ __forceinline__ int pick_group(int qn) {
+  if (qn <= 8) {
+    int g = 1;
+    while (g < qn) g <<= 1;
+    return g;
+  }
+  int best = 32, waste = ((qn + 31) / 32) * 32 - qn;
+  for (int g = 16; g >= 8; g >>= 1) {
+    const int wst = ((qn + g - 1) / g) * g - qn;
+    if (wst < waste) { waste = wst; best = g; }
+  }
+  return best;
 }
 
 template <int D>
@@ -164,17 +180,51 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
   }
   int t = 0;
   while (t < m) {
+    // a run: consecutive entries of the same (bandwidth, query node)
     const int key = __shfl_sync(0xffffffffu, my_key, t);
     int e = t + 1;
     while (e < m && __shfl_sync(0xffffffffu, my_key, e) == key) ++e;
+    int tot = 0;
+    for (int u = t; u < e; ++u) tot += __shfl_sync(0xffffffffu, my_rn, u);
     const int hidx = key / Q.nn, q = key % Q.nn;
     const double h = hv[hidx];
     const float c2 = (float)(-kLog2e / (2.0 * h * h));
     const float2 c2p = make_float2(c2, c2);
     const int qb = Q.beg[q], qn = Q.cnt[q];
-    int g = 32;
-    while (g > 1 && g / 2 >= qn) g >>= 1;
+    const int g = pick_group(qn);
     const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
+    const bool one_tile = tot <= kTile;
+    // Stage references [j0, j0 + tn) of the run's concatenated point list,
+    // negated, padded with far points to an even count.
+    auto stage = [&](int j0, int tn) {
+      const int tn2 = (tn + 1) & ~1;
+      __syncwarp();
+      // uniform trip count: every lane takes part in the shuffles
+      for (int jb = 0; jb < tn2; jb += 32) {
+        const int jj = jb + lane;
+        const int jg = j0 + jj;
+        int src = -1, basej = 0;
+        for (int u = t; u < e; ++u) {
+          const int rn_u = __shfl_sync(0xffffffffu, my_rn, u);
+          const int rb_u = __shfl_sync(0xffffffffu, my_rb, u);
+          if (src < 0 && jj < tn && jg < basej + rn_u) src = rb_u + (jg - basej);
+          basej += rn_u;
+        }
+        if (jj >= tn2) continue;
+        if (src >= 0) {
+          float rv[D];
+          load_point<D>(R.pts + (size_t)src * R.dp, rv);
+#pragma unroll
+          for (int k = 0; k < D; ++k) sR[wib][k][jj] = -rv[k];
+        } else {
+#pragma unroll
+          for (int k = 0; k < D; ++k) sR[wib][k][jj] = kFarNeg;
+        }
+      }
+      __syncwarp();
+      return tn2;
+    };
+    int staged2 = one_tile ? stage(0, tot) : 0;
     for (int q0 = 0; q0 < qn; q0 += g) {
       const int qi = q0 + ql;
       const bool ok = qi < qn;
@@ -187,28 +237,14 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
 #pragma unroll
       for (int k = 0; k < D; ++k) qq[k] = make_float2(qv[k], qv[k]);
       float S = 0.f, C = 0.f;
-      for (int u = t; u < e; ++u) {
-        const int rb = __shfl_sync(0xffffffffu, my_rb, u);
-        const int rn = __shfl_sync(0xffffffffu, my_rn, u);
-        float2 part = make_float2(0.f, 0.f);
-        for (int j0 = 0; j0 < rn; j0 += kTile) {
-          const int tn = min(kTile, rn - j0);
-          const int tn2 = (tn + 1) & ~1;
-          __syncwarp();
-          for (int jj = lane; jj < tn2; jj += 32) {
-            if (jj < tn) {
-              float rv[D];
-              load_point<D>(R.pts + (size_t)(rb + j0 + jj) * R.dp, rv);
-#pragma unroll
-              for (int k = 0; k < D; ++k) sR[wib][k][jj] = -rv[k];
-            } else {
-#pragma unroll
-              for (int k = 0; k < D; ++k) sR[wib][k][jj] = kFarNeg;
-            }
-          }
-          __syncwarp();
+      for (int j0 = 0; j0 < tot; j0 += kTile) {
+        const int tn2 = one_tile ? staged2 : stage(j0, min(kTile, tot - j0));
+        // 16 reference pairs of each lane group per compensated run
+        for (int jr = 2 * gid; jr < tn2; jr += 32 * ngrp) {
+          const int je = min(jr + 32 * ngrp, tn2);
+          float2 part = make_float2(0.f, 0.f);
 #pragma unroll 2
-          for (int jp = 2 * gid; jp < tn2; jp += 2 * ngrp) {
+          for (int jp = jr; jp < je; jp += 2 * ngrp) {
             float2 d2 = make_float2(0.f, 0.f);
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -219,11 +255,11 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
             const float2 a = __fmul2_rn(d2, c2p);
             part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
           }
+          const float y = (part.x + part.y) - C;
+          const float tt = S + y;
+          C = (tt - S) - y;
+          S = tt;
         }
-        const float y = (part.x + part.y) - C;
-        const float tt = S + y;
-        C = (tt - S) - y;
-        S = tt;
       }
       double v = (double)S - (double)C;
       for (int o = g; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -63,13 +63,22 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
                         const double* h_host, int nh, double eps_eff, TravBuffers* b) {
   cudaStream_t s = ctx->stream;
   const size_t nodes = (size_t)nh * qt->nn;
-  CK(ctx->hvals.ensure(nh * sizeof(double)));
+  CK(ctx->hvals.ensure(3 * nh * sizeof(double)));
   CK(ctx->node_state.ensure(4 * nodes * sizeof(u64)));
   CK(ctx->lmom.ensure(nodes * qt->P * sizeof(double)));
   CK(ctx->pused.ensure(nodes * sizeof(int)));
   CK(ctx->gacc.ensure((size_t)nh * qt->n * sizeof(double)));
   CK(ctx->counters.ensure(sizeof(RoundCounters)));
-  CK(cudaMemcpyAsync(ctx->hvals.p, h_host, nh * sizeof(double), cudaMemcpyHostToDevice, s));
+  {
+    std::vector<double> hv(3 * (size_t)nh);
+    for (int i = 0; i < nh; ++i) {
+      hv[i] = h_host[i];
+      hv[nh + i] = 1.0 / (2.0 * h_host[i] * h_host[i]);
+      hv[2 * nh + i] = 1.0 / (2.0 * h_host[i]);
+    }
+    CK(cudaMemcpyAsync(ctx->hvals.p, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));  // hv is a stack buffer
+  }
   CK(cudaMemsetAsync(ctx->node_state.p, 0, 4 * nodes * sizeof(u64), s));
   CK(cudaMemsetAsync(ctx->lmom.p, 0, nodes * qt->P * sizeof(double), s));
   CK(cudaMemsetAsync(ctx->pused.p, 0, nodes * sizeof(int), s));
@@ -84,9 +93,14 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->pused = ctx->pused.as<int>();
   b->gacc = ctx->gacc.as<double>();
   b->h = ctx->hvals.as<double>();
+  b->inv2h2 = ctx->hvals.as<double>() + nh;
+  b->inv_2h = ctx->hvals.as<double>() + 2 * nh;
+  b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
   b->fix_scale = std::ldexp(1.0, 62) / (double)rt->n;
+  b->inv_fix = 1.0 / b->fix_scale;
+  b->inv_nr = 1.0 / (double)rt->n;
   b->p_limit = std::min(qt->p_limit, rt->p_limit);
   return DFGT_OK;
 }
@@ -196,6 +210,8 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       if (rc != DFGT_OK) return rc;
     }
     CK(ctx->slots.ensure((size_t)nF * sizeof(int)));
+    CK(ctx->kus.ensure((size_t)nF * sizeof(double)));
+    b.ku = ctx->kus.as<double>();
     CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_fold(b, qt->nn, s));
     CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
@@ -313,7 +329,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1], &ctx->slots,
-                    &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r,
+                    &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g};
   for (DevBuf* b : bufs) b->release();

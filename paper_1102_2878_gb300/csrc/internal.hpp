@@ -51,7 +51,8 @@ struct dfgt_ctx {
   // cached workspace
   DevBuf scan_tmp;
   DevBuf counters;       // RoundCounters on the device
-  DevBuf hvals;          // bandwidths
+  DevBuf hvals;          // bandwidths, then 1/(2h^2)
+  DevBuf kus;            // double K(d^u) per frontier pair
   DevBuf frontier[2];    // Pair
   DevBuf slots;          // int child slot per frontier pair
   DevBuf grp_cnt, grp_off, grp_r;  // base-case grouping scratch
@@ -120,9 +121,14 @@ struct TravBuffers {
   int* pused;       // [nh][nnQ]
   double* gacc;     // [nh][nq] (permuted order)
   const double* h;  // [nh]
+  const double* inv2h2;  // [nh] 1/(2h^2)
+  const double* inv_2h;  // [nh] 1/(2h)
+  double* ku;       // [frontier] K(d^u) of each pending pair, from the bound pass
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums
   double fix_scale; // 2^62 / |R|
+  double inv_fix;   // 1 / fix_scale
+  double inv_nr;    // 1 / |R|
   int p_limit;
   long long base_block;  // exact sum without recursing when |Q||R| <= this
 };

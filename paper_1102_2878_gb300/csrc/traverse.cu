@@ -135,9 +135,9 @@ __global__ void __launch_bounds__(kT) k_lb(TreeView Q, TreeView R, TravBuffers b
   }
   double dl2, du2, sq, sr;
   box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
-  const double h = b.h[pr.h];
-  const double delta_l = (double)R.cnt[pr.r] * exp(-du2 / (2.0 * h * h));
-  const u64 f = to_fix(delta_l, b.fix_scale);
+  const double Ku = exp(-du2 * b.inv2h2[pr.h]);
+  b.ku[i] = Ku;  // reused by the classification of the same pair
+  const u64 f = to_fix((double)R.cnt[pr.r] * Ku, b.fix_scale);
   if (f) atomicAdd(&b.lbsum[hq], f);
 }
 
@@ -161,15 +161,15 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
       pr = F[i];
       const size_t hq = (size_t)pr.h * Q.nn + pr.q;
       const double nQ = (double)Q.cnt[pr.q], nR = (double)R.cnt[pr.r];
-      const double h = b.h[pr.h];
-      const double inv2h2 = 1.0 / (2.0 * h * h);
       double dl2, du2, sideQ, sideR;
       box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
-      const double Kl = exp(-dl2 * inv2h2), Ku = exp(-du2 * inv2h2);
+      const double Kl = dl2 > 0.0 ? exp(-dl2 * b.inv2h2[pr.h]) : 1.0;
+      const double Ku = b.ku[i];
       const double delta_l = nR * Ku;
       const u64 lbf = b.inherited[hq] + b.decided[hq] + b.lbsum[hq];
-      const double Gl = (double)lbf / b.fix_scale;
-      const double tau = b.eps_eff * nR * Gl / (double)R.n;
+      const double Gl = (double)lbf * b.inv_fix;
+      const double tau = b.eps_eff * nR * Gl * b.inv_nr;
+      const double inv_2h = b.inv_2h[pr.h];
       if (0.5 * nR * (Kl - Ku) <= tau) {
         kind = 0;
         atomicAdd(&b.L[hq * P], 0.5 * nR * (Kl + Ku));
@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
       } else {
         int pF = 0, pD = 0, pT = 0;
         if (tau > 0.0) {
-          pF = order_ff(sideR / (2.0 * h), nR, d, tau, b.p_limit);
-          pD = order_ff(sideQ / (2.0 * h), nR, d, tau, b.p_limit);
-          pT = order_t(fmax(sideQ, sideR) / (2.0 * h), nR, d, tau, b.p_limit);
+          pF = order_ff(sideR * inv_2h, nR, d, tau, b.p_limit);
+          pD = order_ff(sideQ * inv_2h, nR, d, tau, b.p_limit);
+          pT = order_t(fmax(sideQ, sideR) * inv_2h, nR, d, tau, b.p_limit);
         }
         // ChooseBestMethod with c_F = D N_Q p^D, c_D = D N_R p^D,
         // c_T = D p^{2D}, c_E = D N_Q N_R; ties go F, D, T, E.

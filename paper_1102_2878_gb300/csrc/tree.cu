@@ -256,59 +256,57 @@ __global__ void k_leaf_moments(TreeView t, double* __restrict__ mom) {
 // Internal moments of one level by the far-to-far translation (Lemma 3.5,
 // Eq. far_to_far_translation, exact for gamma < p) of both children:
 // m_gamma(c') = sum_{alpha<=gamma} m_alpha(c_child) (c_child - c')^{gamma-alpha}/(gamma-alpha)!.
+// The factor (x)^{gamma-alpha}/(gamma-alpha)! is a product over dimensions,
+// so the shift is applied one dimension at a time (D p^D p operations per
+// child instead of p^{2D}), in float64 shared memory, one warp per node.
 template <int D>
 __global__ void k_f2f_level(TreeView t, int a, int e, double* __restrict__ mom) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
-  const int w = a + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  constexpr int W = kT / 32;
+  __shared__ double sM[W][2][P];
+  const int wib = threadIdx.x >> 5;
+  const int w = a + blockIdx.x * W + wib;
   const int lane = threadIdx.x & 31;
   if (w >= e || t.left[w] < 0) return;
-  double c[D];
-#pragma unroll
-  for (int k = 0; k < D; ++k) c[k] = 0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
   double acc[(P + 31) / 32];
 #pragma unroll
-  for (int s = 0; s < (P + 31) / 32; ++s) acc[s] = 0.0;
+  for (int sl = 0; sl < (P + 31) / 32; ++sl) acc[sl] = 0.0;
   for (int ch = 0; ch < 2; ++ch) {
     const int cn = t.left[w] + ch;
-    double tab[D][PM];  // (c_child - c')^e / e!
+    for (int idx = lane; idx < P; idx += 32) sM[wib][0][idx] = mom[(size_t)cn * P + idx];
+    __syncwarp();
+    int cur = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const double x = 0.5 * ((double)t.lo[(size_t)cn * D + k] + (double)t.hi[(size_t)cn * D + k]) - c[k];
-      double v = 1.0;
-#pragma unroll
-      for (int q = 0; q < PM; ++q) {
-        tab[k][q] = v;
-        v = v * x / (double)(q + 1);
-      }
-    }
-    const double* mc = mom + (size_t)cn * P;
-#pragma unroll
-    for (int s = 0; s < (P + 31) / 32; ++s) {
-      const int idx = lane + 32 * s;
-      if (idx >= P) break;
-      int g[D];
-#pragma unroll
-      for (int k = 0; k < D; ++k) g[k] = digit<D, PM>(idx, k);
-      double sum = 0.0;
-      for (int j = 0; j < P; ++j) {
-        double term = mc[j];
-        bool ok = true;
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const int ak = digit<D, PM>(j, k);
-          if (ak > g[k]) ok = false;
-          else term *= tab[k][g[k] - ak];
+      const double x = 0.5 * ((double)t.lo[(size_t)cn * D + k] + (double)t.hi[(size_t)cn * D + k]) -
+                       0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
+      int stride = 1;
+      for (int j = D - 1; j > k; --j) stride *= PM;
+      for (int idx = lane; idx < P; idx += 32) {
+        const int gk = (idx / stride) % PM;
+        // sum over alpha_k <= gamma_k of m[.. alpha_k ..] x^{gamma_k - alpha_k} / (gamma_k - alpha_k)!
+        double sum = 0.0, term = 1.0;
+        for (int dlt = 0; dlt <= gk; ++dlt) {
+          sum += sM[wib][cur][idx - dlt * stride] * term;
+          term = term * x / (double)(dlt + 1);
         }
-        if (ok) sum += term;
+        sM[wib][cur ^ 1][idx] = sum;
       }
-      acc[s] += sum;
+      __syncwarp();
+      cur ^= 1;
     }
+#pragma unroll
+    for (int sl = 0; sl < (P + 31) / 32; ++sl) {
+      const int idx = lane + 32 * sl;
+      if (idx < P) acc[sl] += sM[wib][cur][idx];
+    }
+    __syncwarp();
   }
 #pragma unroll
-  for (int s = 0; s < (P + 31) / 32; ++s) {
-    const int idx = lane + 32 * s;
-    if (idx < P) mom[(size_t)w * P + idx] = acc[s];
+  for (int sl = 0; sl < (P + 31) / 32; ++sl) {
+    const int idx = lane + 32 * sl;
+    if (idx < P) mom[(size_t)w * P + idx] = acc[sl];
   }
 }
 

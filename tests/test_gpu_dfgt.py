@@ -100,13 +100,15 @@ def test_repeatable_and_batched_equals_single(dev):
     t = dfgt.Tree(dev, to_cuda(x))
     G1, s1 = dfgt.kde_sum(dev, t, t, hs, 1e-2)
     G2, s2 = dfgt.kde_sum(dev, t, t, hs, 1e-2)
-    # decisions are deterministic (fixed-point bounds); only float64 atomic
-    # summation order may differ
+    # decisions are deterministic (fixed-point bounds, so the same pairs are
+    # pruned, summarised and summed); the order in which float32 partial
+    # sums meet varies with atomics, so values agree to float32 rounding
     assert s1["n_base"] == s2["n_base"] and s1["n_prune"] == s2["n_prune"]
-    assert np.allclose(G1.cpu().numpy(), G2.cpu().numpy(), rtol=1e-12, atol=0)
+    assert s1["n_farfield"] == s2["n_farfield"] and s1["n_local"] == s2["n_local"]
+    assert np.allclose(G1.cpu().numpy(), G2.cpu().numpy(), rtol=2e-6, atol=0)
     for i, h in enumerate(hs):
         Gi, _ = dfgt.kde_sum(dev, t, t, [h], 1e-2)
-        assert np.allclose(Gi.cpu().numpy()[0], G1.cpu().numpy()[i], rtol=1e-12, atol=0)
+        assert np.allclose(Gi.cpu().numpy()[0], G1.cpu().numpy()[i], rtol=2e-6, atol=0)
 
 
 def test_small_work_lists_are_drained_early(dev, orc):
@@ -126,7 +128,7 @@ def test_host_buffer_entry_matches_device_entry(dev):
     t = dfgt.Tree(dev, to_cuda(x))
     Gd, _ = dfgt.kde_sum(dev, t, t, hs, 1e-2)
     Gh, st = dfgt.kde_host(dev, x, None, hs, 1e-2)
-    assert np.allclose(Gh, Gd.cpu().numpy(), rtol=1e-12)
+    assert np.allclose(Gh, Gd.cpu().numpy(), rtol=2e-6)
 
 
 def test_dfgt_against_gpu_bruteforce(dev):
