@@ -224,6 +224,13 @@ def run_dfgt(args, rank, world, local):
     pairs_step = N * N * nh
     value = world * pairs_step / (ms / 1e3)
 
+    if args.only_dfgt:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * N * N * nh / (ms / 1e3), "unit": UNIT,
+                              "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+                              "config": {"workload": args.workload}, "note": "dual-tree steps only"}))
+        ctx.close()
+        return
     # GPU brute force on the same data (the comparison named by the metric)
     Gb = dfgt.kde_sum_bruteforce(ctx, pts, pts, hs)
     bf_ms = []
@@ -307,6 +314,8 @@ def main():
     ap.add_argument("--impl", choices=["dfgt", "reference"], default="dfgt")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-dfgt", action="store_true",
+                    help="time the dual-tree steps only (no brute force, e2e or CPU legs); for profiling")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     args = ap.parse_args()
     rank, world, local = dist_env()

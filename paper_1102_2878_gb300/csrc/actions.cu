@@ -124,7 +124,6 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 // compensation and lane groups are combined in float64.
 
 constexpr int kBaseChunk = 8;
-constexpr int kTile = 256;
 constexpr float kFarNeg = -1.0e18f;  // padding point: contributes exp(-huge) = 0
 
 __global__ void k_base_count(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cnt) {
@@ -161,12 +160,19 @@ __device__ __forceinline__ int pick_group(int qn) {
   return best;
 }
 
+// References staged per warp: as many as 48 KB of shared memory per block allows.
+template <int D>
+constexpr int base_tile() {
+  return ((48 * 1024 / 4 / kWarpsPerBlock) / D) & ~1;
+}
+
 template <int D>
 __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                              const int* __restrict__ ksorted, int n,
                                              const double* __restrict__ hv,
                                              double* __restrict__ gacc) {
-  __shared__ __align__(16) float sR[kWarpsPerBlock][D][kTile];
+  constexpr int TILE = base_tile<D>();
+  __shared__ __align__(16) float sR[kWarpsPerBlock][D][TILE];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
   if (i0 >= n) return;
@@ -193,38 +199,34 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
     const int qb = Q.beg[q], qn = Q.cnt[q];
     const int g = pick_group(qn);
     const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
-    const bool one_tile = tot <= kTile;
     // Stage references [j0, j0 + tn) of the run's concatenated point list,
-    // negated, padded with far points to an even count.
+    // negated, padded with far points to an even count; entry by entry, so
+    // no lane searches for its source.
     auto stage = [&](int j0, int tn) {
       const int tn2 = (tn + 1) & ~1;
       __syncwarp();
-      // uniform trip count: every lane takes part in the shuffles
-      for (int jb = 0; jb < tn2; jb += 32) {
-        const int jj = jb + lane;
-        const int jg = j0 + jj;
-        int src = -1, basej = 0;
-        for (int u = t; u < e; ++u) {
-          const int rn_u = __shfl_sync(0xffffffffu, my_rn, u);
-          const int rb_u = __shfl_sync(0xffffffffu, my_rb, u);
-          if (src < 0 && jj < tn && jg < basej + rn_u) src = rb_u + (jg - basej);
-          basej += rn_u;
-        }
-        if (jj >= tn2) continue;
-        if (src >= 0) {
+      int base = 0;
+      for (int u = t; u < e; ++u) {
+        const int rn_u = __shfl_sync(0xffffffffu, my_rn, u);
+        const int rb_u = __shfl_sync(0xffffffffu, my_rb, u);
+        const int lo = max(j0 - base, 0), hi = min(j0 + tn - base, rn_u);
+        for (int jj = lo + lane; jj < hi; jj += 32) {
           float rv[D];
-          load_point<D>(R.pts + (size_t)src * R.dp, rv);
+          load_point<D>(R.pts + (size_t)(rb_u + jj) * R.dp, rv);
 #pragma unroll
-          for (int k = 0; k < D; ++k) sR[wib][k][jj] = -rv[k];
-        } else {
-#pragma unroll
-          for (int k = 0; k < D; ++k) sR[wib][k][jj] = kFarNeg;
+          for (int k = 0; k < D; ++k) sR[wib][k][base + jj - j0] = -rv[k];
         }
+        base += rn_u;
+      }
+      if (lane == 0 && tn2 > tn) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) sR[wib][k][tn] = kFarNeg;
       }
       __syncwarp();
       return tn2;
     };
-    int staged2 = one_tile ? stage(0, tot) : 0;
+    const bool one_tile = tot <= TILE;
+    const int staged2 = one_tile ? stage(0, tot) : 0;
     for (int q0 = 0; q0 < qn; q0 += g) {
       const int qi = q0 + ql;
       const bool ok = qi < qn;
@@ -237,9 +239,9 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
 #pragma unroll
       for (int k = 0; k < D; ++k) qq[k] = make_float2(qv[k], qv[k]);
       float S = 0.f, C = 0.f;
-      for (int j0 = 0; j0 < tot; j0 += kTile) {
-        const int tn2 = one_tile ? staged2 : stage(j0, min(kTile, tot - j0));
-        // 16 reference pairs of each lane group per compensated run
+      for (int j0 = 0; j0 < tot; j0 += TILE) {
+        const int tn2 = one_tile ? staged2 : stage(j0, min(TILE, tot - j0));
+        // 16 reference pairs per lane per compensated run
         for (int jr = 2 * gid; jr < tn2; jr += 32 * ngrp) {
           const int je = min(jr + 32 * ngrp, tn2);
           float2 part = make_float2(0.f, 0.f);
