@@ -163,13 +163,13 @@ __device__ __forceinline__ int pick_group(int qn) {
 // References staged per warp: as many as 48 KB of shared memory per block allows.
 template <int D>
 constexpr int base_tile() {
-  return ((48 * 1024 / 4 / kWarpsPerBlock) / D) & ~1;
+  return ((24 * 1024 / 4 / kWarpsPerBlock) / D) & ~1;
 }
 
 template <int D>
 __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                              const int* __restrict__ ksorted, int n,
-                                             const double* __restrict__ hv,
+                                             const float* __restrict__ c2v,
                                              double* __restrict__ gacc) {
   constexpr int TILE = base_tile<D>();
   __shared__ __align__(16) float sR[kWarpsPerBlock][D][TILE];
@@ -193,8 +193,7 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
     int tot = 0;
     for (int u = t; u < e; ++u) tot += __shfl_sync(0xffffffffu, my_rn, u);
     const int hidx = key / Q.nn, q = key % Q.nn;
-    const double h = hv[hidx];
-    const float c2 = (float)(-kLog2e / (2.0 * h * h));
+    const float c2 = c2v[hidx];
     const float2 c2p = make_float2(c2, c2);
     const int qb = Q.beg[q], qn = Q.cnt[q];
     const int g = pick_group(qn);
@@ -263,9 +262,9 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
           S = tt;
         }
       }
-      double v = (double)S - (double)C;
+      float v = S - C;
       for (int o = g; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (gid == 0 && ok) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], v);
+      if (gid == 0 && ok) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], (double)v);
     }
     t = e;
   }
@@ -786,7 +785,7 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
   const long warps = (n + kBaseChunk - 1) / kBaseChunk;
   const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc));
+    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc));
   } else {
     k_base_g<<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc);
   }

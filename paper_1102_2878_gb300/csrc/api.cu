@@ -63,18 +63,20 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
                         const double* h_host, int nh, double eps_eff, TravBuffers* b) {
   cudaStream_t s = ctx->stream;
   const size_t nodes = (size_t)nh * qt->nn;
-  CK(ctx->hvals.ensure(3 * nh * sizeof(double)));
+  CK(ctx->hvals.ensure(4 * nh * sizeof(double)));
   CK(ctx->node_state.ensure(4 * nodes * sizeof(u64)));
   CK(ctx->lmom.ensure(nodes * qt->P * sizeof(double)));
   CK(ctx->pused.ensure(nodes * sizeof(int)));
   CK(ctx->gacc.ensure((size_t)nh * qt->n * sizeof(double)));
   CK(ctx->counters.ensure(sizeof(RoundCounters)));
   {
-    std::vector<double> hv(3 * (size_t)nh);
+    std::vector<double> hv(4 * (size_t)nh);
+    float* c2 = reinterpret_cast<float*>(hv.data() + 3 * (size_t)nh);
     for (int i = 0; i < nh; ++i) {
       hv[i] = h_host[i];
       hv[nh + i] = 1.0 / (2.0 * h_host[i] * h_host[i]);
       hv[2 * nh + i] = 1.0 / (2.0 * h_host[i]);
+      c2[i] = (float)(-kLog2e / (2.0 * h_host[i] * h_host[i]));
     }
     CK(cudaMemcpyAsync(ctx->hvals.p, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // hv is a stack buffer
@@ -95,6 +97,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->h = ctx->hvals.as<double>();
   b->inv2h2 = ctx->hvals.as<double>() + nh;
   b->inv_2h = ctx->hvals.as<double>() + 2 * nh;
+  b->c2 = reinterpret_cast<const float*>(ctx->hvals.as<double>() + 3 * nh);
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
@@ -331,7 +334,8 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1], &ctx->slots,
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
-                    &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g};
+                    &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,
+                    &ctx->bf_partials};
   for (DevBuf* b : bufs) b->release();
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
   for (int i = 0; i < 16; ++i)
@@ -399,7 +403,8 @@ dfgt_status dfgt_sum_bruteforce(dfgt_ctx* ctx, const float* q_dev, int64_t nq, c
   if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_bruteforce: need 1..1024 finite bandwidths > 0");
   CK(cudaSetDevice(ctx->device));
   ctx->err.clear();
-  CK(launch_bruteforce(q_dev, (int)nq, r_dev, (int)nr, d, h_host, nh, G_dev, ctx->stream, &ctx->launches));
+  CK(launch_bruteforce(q_dev, (int)nq, r_dev, (int)nr, d, h_host, nh, G_dev, ctx->bf_partials,
+                       ctx->stream, &ctx->launches));
   CK(cudaStreamSynchronize(ctx->stream));
   return DFGT_OK;
 }

@@ -62,6 +62,7 @@ struct dfgt_ctx {
   DevBuf pused;          // int [nh][nn]
   DevBuf gacc;           // double [nh][nq]
   DevBuf io_q, io_r, io_g;  // dfgt_kde_host staging
+  DevBuf bf_partials;       // brute-force slice partials
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned
@@ -102,9 +103,15 @@ cudaError_t scan_exclusive(const int* in, int* out, int n, DevBuf& tmp, cudaStre
                            long long* launches);
 
 // bruteforce.cu
+// Slices the references are split into for nq queries (1 = no split).
+int bruteforce_slices(int nq, int nr);
+// With slices > 1, `partials` must hold slices * nh * nq doubles.
+cudaError_t launch_bruteforce_split(const float* q, int nq, const float* r, int nr, int d,
+                                    const double* h_host, int nh, double* G, int slices,
+                                    double* partials, cudaStream_t s, long long* launches);
 cudaError_t launch_bruteforce(const float* q, int nq, const float* r, int nr, int d,
-                              const double* h_host, int nh, double* G, cudaStream_t s,
-                              long long* launches);
+                              const double* h_host, int nh, double* G, DevBuf& scratch,
+                              cudaStream_t s, long long* launches);
 
 // tree.cu: build the tree (points, nodes, raw moments) on ctx's stream.
 dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n, int d,
@@ -123,6 +130,7 @@ struct TravBuffers {
   const double* h;  // [nh]
   const double* inv2h2;  // [nh] 1/(2h^2)
   const double* inv_2h;  // [nh] 1/(2h)
+  const float* c2;       // [nh] -log2(e)/(2h^2) as float, the exp2 scale of exact sums
   double* ku;       // [frontier] K(d^u) of each pending pair, from the bound pass
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums

@@ -44,3 +44,17 @@ def test_bruteforce_edge_sizes(dev, orc):
         G = dfgt.kde_sum_bruteforce(dev, to_cuda(q), to_cuda(r), [0.3]).cpu().numpy()
         ref = orc.naive_kde(q.astype(np.float64), r.astype(np.float64), 0.3)
         assert np.allclose(G[0], ref, rtol=TOL, atol=0)
+
+
+@pytest.mark.parametrize("nq,nr,D", [(1, 50_000, 3), (257, 70_001, 3), (100, 9_999, 5), (64, 20_000, 8)])
+def test_bruteforce_small_query_batch_split_over_references(dev, orc, nq, nr, D):
+    # a query batch too small to fill the GPU splits the references into
+    # slices whose partial sums are added afterwards
+    q = datagen.isotropic_mixture(nq, D, 4, 0.1, seed=nq)
+    r = datagen.isotropic_mixture(nr, D, 4, 0.1, seed=nr)
+    hs = list(datagen.logspace_bandwidths(0.02, 0.5, 10))
+    G = dfgt.kde_sum_bruteforce(dev, to_cuda(q), to_cuda(r), hs).cpu().numpy()
+    for i, h in enumerate(hs):
+        ref = orc.naive_kde(q.astype(np.float64), r.astype(np.float64), h)
+        ok = ref > 1e-30
+        assert np.all(np.abs(G[i][ok] - ref[ok]) <= TOL * ref[ok]), (nq, nr, D, h)
