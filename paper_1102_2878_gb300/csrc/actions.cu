@@ -163,7 +163,7 @@ __device__ __forceinline__ int pick_group(int qn) {
 // References staged per warp: as many as 48 KB of shared memory per block allows.
 template <int D>
 constexpr int base_tile() {
-  return ((24 * 1024 / 4 / kWarpsPerBlock) / D) & ~1;
+  return ((48 * 1024 / 4 / kWarpsPerBlock) / D) & ~1;
 }
 
 template <int D>
