@@ -101,6 +101,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def replica_points(x, rank):
+    """Points of rank `rank`: the workload itself on rank 0, an independent
+    draw of the same recipe (permuted, jittered by 1e-4) on other ranks."""
+    if rank == 0:
+        return x
+    rng = np.random.default_rng(1000 + rank)
+    y = x[rng.permutation(len(x))] + rng.normal(0, 1e-4, size=x.shape).astype(np.float32)
+    return np.ascontiguousarray(np.clip(y, 0, 1).astype(np.float32))
+
+
+def max_over_ranks(value, world):
+    """Largest per-step time over all ranks (host-side gloo all-reduce)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -167,11 +189,7 @@ def run_dfgt(args, rank, world, local):
     torch.cuda.set_device(local)
     dfgt.build()
     x, hs, eps = datagen.workload(args.workload)
-    if rank > 0:  # an independent replica: same recipe, another seed
-        rng = np.random.default_rng(1000 + rank)
-        x = np.ascontiguousarray(x[rng.permutation(len(x))] +
-                                 rng.normal(0, 1e-4, size=x.shape).astype(np.float32))
-        x = np.clip(x, 0, 1).astype(np.float32)
+    x = replica_points(x, rank)  # independent replica per rank (weak scaling)
     N, D, nh = x.shape[0], x.shape[1], len(hs)
     ctx = dfgt.Context(local)
     pts = torch.from_numpy(x).to(f"cuda:{local}")
@@ -214,12 +232,9 @@ def run_dfgt(args, rank, world, local):
     launches = ctx.launch_count() - launches0
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = statistics.mean(times)
+    ms = max_over_ranks(statistics.mean(times), world)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     pairs_step = N * N * nh
     value = world * pairs_step / (ms / 1e3)
