@@ -153,6 +153,33 @@ dfgt_status dfgt_kde_host(dfgt_ctx* ctx, const float* q_host, int64_t nq, const 
                           int64_t nr, int d, const double* h_host, int nh, double eps,
                           const dfgt_opts* opts, double* G_host, dfgt_stats* stats);
 
+/* Exact sums as dfgt_sum_bruteforce, for callers that cannot allocate
+ * device memory: code running while a CUDA graph is captured, hosts that
+ * give the library a fixed memory budget and forbid allocations of its own,
+ * and loops where an allocation's implicit synchronisation is not
+ * acceptable.  The paper has no counterpart; this is a library service.
+ *
+ * No context is needed and nothing is allocated: the references are split
+ * into slices whose float64 partial sums live in a 16 MiB static device
+ * array that every GPU loading the library reserves until the process
+ * exits.  Limit: nh * nq <= 1,048,576 (partials of two slices must fit);
+ * larger requests return DFGT_ECAPACITY before anything is launched.
+ *   q_dev, r_dev : float32 [n][d] on the current device (caller-owned)
+ *   h_host       : nh finite bandwidths > 0 (host), 1 <= nh <= 1024
+ *   G_dev        : float64 [nh][nq] on the current device (caller-owned)
+ *   cuda_stream  : cudaStream_t to run on (NULL = the legacy default stream)
+ * The call enqueues its kernels and returns; G_dev is complete once the
+ * stream reaches that point.  All calls share the static array: calls whose
+ * kernels overlap on the GPU (different streams, or several host threads)
+ * race on it and corrupt each other's results; calls on one stream are
+ * ordered and safe.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, which may load the module); make
+ * that first call before any stream capture.  Errors: DFGT_EINVAL for bad
+ * arguments, DFGT_ECAPACITY past the limit, DFGT_ECUDA if a launch fails. */
+dfgt_status dfgt_sum_bruteforce_static(const float* q_dev, int64_t nq, const float* r_dev,
+                                       int64_t nr, int d, const double* h_host, int nh,
+                                       double* G_dev, void* cuda_stream);
+
 /* ---- introspection (used by the tests; not on the hot path) ---- */
 
 typedef struct {

@@ -16,8 +16,8 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_bruteforce", "kde_host",
-           "apply_pairs", "build"]
+__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_bruteforce", "kde_sum_bruteforce_static",
+           "kde_host", "apply_pairs", "build"]
 
 
 class DFGTError(RuntimeError):
@@ -169,6 +169,26 @@ def kde_sum_bruteforce(ctx: Context, q, r, hs, out=None):
     st = ctx.lib.dfgt_sum_bruteforce(ctx.h, C.c_void_p(q.data_ptr()), q.shape[0], C.c_void_p(r.data_ptr()),
                                      r.shape[0], q.shape[1], hp, len(ha), C.c_void_p(out.data_ptr()))
     ctx.check(st, "dfgt_sum_bruteforce")
+    return out
+
+
+def kde_sum_bruteforce_static(q, r, hs, out, stream=None):
+    """Exact G [nh, nq] into a preallocated float64 CUDA tensor `out`,
+    without any device allocation by the library (static scratch; see
+    dfgt_sum_bruteforce_static in include/dfgt.h for the limit and the
+    rule that overlapping calls race).  Runs on `stream` (a torch CUDA
+    stream, default: the current one) and returns without waiting."""
+    torch = _torch()
+    lib = _lib.load()
+    ha, hp = _hs(hs)
+    q = q.contiguous()
+    r = r.contiguous()
+    stream = torch.cuda.current_stream(q.device) if stream is None else stream
+    st = lib.dfgt_sum_bruteforce_static(C.c_void_p(q.data_ptr()), q.shape[0], C.c_void_p(r.data_ptr()),
+                                        r.shape[0], q.shape[1], hp, len(ha), C.c_void_p(out.data_ptr()),
+                                        C.c_void_p(stream.cuda_stream))
+    if st != 0:
+        raise DFGTError(st, "dfgt_sum_bruteforce_static failed")
     return out
 
 

@@ -58,6 +58,8 @@ SIGNATURES = {
                            C.c_double, C.c_void_p, C.POINTER(Stats)]),
     "dfgt_sum_bruteforce": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                       C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p]),
+    "dfgt_sum_bruteforce_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int,
+                                             C.POINTER(C.c_double), C.c_int, C.c_void_p, C.c_void_p]),
     "dfgt_kde_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int,
                                 C.POINTER(C.c_double), C.c_int, C.c_double, C.POINTER(Opts),
                                 C.c_void_p, C.POINTER(Stats)]),
