@@ -124,23 +124,28 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 // compensation and lane groups are combined in float64.
 
 constexpr int kBaseChunk = 8;
+constexpr int kNodeBits = 27;  // node indices stay below 2^27 (checked by the tree build)
+constexpr int kNodeMask = (1 << kNodeBits) - 1;
 constexpr float kFarNeg = -1.0e18f;  // padding point: contributes exp(-huge) = 0
 
-__global__ void k_base_count(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cnt) {
+// Counting sort of a pair list by (bandwidth, query node).  Pair and Action
+// records share the layout {q, r, h, w}; the sorted value packs r with the
+// fourth field w (order p of an action, 0 for a base pair) as r | w << 27.
+__global__ void k_sort_count(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Pair p = list[i];
   atomicAdd(&cnt[(size_t)p.h * nnQ + p.q], 1);
 }
 
-__global__ void k_base_scatter(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cursor,
-                               int* __restrict__ rsorted, int* __restrict__ ksorted) {
+__global__ void k_sort_scatter(const Pair* __restrict__ list, int n, int nnQ, int* __restrict__ cursor,
+                               int* __restrict__ vsorted, int* __restrict__ ksorted) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Pair p = list[i];
   const int key = p.h * nnQ + p.q;
   const int pos = atomicAdd(&cursor[key], 1);
-  rsorted[pos] = p.r;
+  vsorted[pos] = p.r | (p.flags << kNodeBits);
   ksorted[pos] = key;
 }
 
@@ -180,7 +185,7 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
   int my_key = -1, my_rb = 0, my_rn = 0;
   if (lane < m) {
     my_key = ksorted[i0 + lane];
-    const int r = rsorted[i0 + lane];
+    const int r = rsorted[i0 + lane] & kNodeMask;
     my_rb = R.beg[r];
     my_rn = R.cnt[r];
   }
@@ -281,7 +286,7 @@ __global__ void __launch_bounds__(kT) k_base_g(TreeView Q, TreeView R, const int
   const int m = (int)min((long)kBaseChunk, n - i0);
   const int d = Q.d;
   for (int u = 0; u < m; ++u) {
-    const int key = ksorted[i0 + u], r = rsorted[i0 + u];
+    const int key = ksorted[i0 + u], r = rsorted[i0 + u] & kNodeMask;
     const int hidx = key / Q.nn, q = key % Q.nn;
     const double h = hv[hidx];
     const float c2 = (float)(-kLog2e / (2.0 * h * h));
@@ -310,18 +315,17 @@ __global__ void __launch_bounds__(kT) k_base_g(TreeView Q, TreeView R, const int
 // Scaled far-field moments M_alpha = m_alpha (2h^2)^(-|alpha|/2) for alpha < p
 // (zero elsewhere) into shared memory, float32.
 template <int D, int PM, int P>
-__device__ __forceinline__ void stage_moments(const double* __restrict__ m, double s, int p,
-                                              float* Ms, int lane) {
+__device__ __forceinline__ void stage_moments(const double* __restrict__ m, const double* __restrict__ spow,
+                                              int p, float* Ms, int lane) {
   for (int idx = lane; idx < P; idx += 32) {
-    int a[D];
     int ab = 0;
     bool ok = true;
     {
       int v = idx;
 #pragma unroll
-      for (int k = D - 1; k >= 0; --k) { a[k] = v % PM; v /= PM; ab += a[k]; ok = ok && a[k] < p; }
+      for (int k = D - 1; k >= 0; --k) { const int a = v % PM; v /= PM; ab += a; ok = ok && a < p; }
     }
-    Ms[idx] = ok ? (float)(m[idx] * pow_int(s, ab)) : 0.f;
+    Ms[idx] = ok ? (float)(m[idx] * spow[ab]) : 0.f;
   }
 }
 
@@ -331,6 +335,7 @@ template <int D>
 __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
                                                  const Action* __restrict__ list, int n,
                                                  const double* __restrict__ hv,
+                                                 const double* __restrict__ spow,
                                                  double* __restrict__ gacc) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
   const double h = hv[a.h];
   const double s = 1.0 / sqrt(2.0 * h * h);
   float* Ms = sM[wib];
-  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, s, a.p, Ms, lane);
+  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, spow + (size_t)a.h * kPowTable, a.p, Ms, lane);
   __syncwarp();
   CenterHL cR[D];
 #pragma unroll
@@ -371,83 +376,107 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
 // ------------------------------------------------------------ direct local
 // AccumulateDirectLocalMoment:
 // L_beta(Q) += ((-1)^{|beta|}/beta!) sum_{r in R} h_beta((Q.c - r)/sqrt(2h^2)).
-// Each lane tabulates the 1-D Hermite functions of one reference point in
-// shared memory; each lane then owns coefficient positions and sums over
-// the 32 tabulated points.  Runs of 32 are summed in float32 and added in
-// float64.
+// The list is sorted by (bandwidth, query node) like the base case, and a
+// warp takes kBaseChunk consecutive sorted entries: every run of one query
+// node accumulates its coefficients in registers (lane per coefficient
+// position) and adds them to L once.  For each batch of 32 reference points
+// each lane tabulates the 1-D Hermite functions of one point in shared
+// memory, then every lane sums its coefficient over the batch; batches are
+// summed in float32 and added in float64.  An entry of order p contributes
+// only to beta < p.
 template <int D>
-__global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const Action* __restrict__ list,
-                                              int n, const double* __restrict__ hv,
+__global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
+                                              const int* __restrict__ ksorted, int n,
+                                              const double* __restrict__ hv,
                                               double* __restrict__ L, int* __restrict__ pused) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
   constexpr int S = (P + 31) / 32;
   __shared__ float sH[kWarpsPerBlock][32][D][PM];
-  const int wib = threadIdx.x >> 5;
-  const int w = blockIdx.x * kWarpsPerBlock + wib;
-  const int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  const Action a = list[w];
-  const double h = hv[a.h];
-  const float sf = (float)(1.0 / sqrt(2.0 * h * h));
-  CenterHL cQ[D];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
+  if (i0 >= n) return;
+  const int m = (int)min((long)kBaseChunk, n - i0);
+  int my_key = -1, my_r = 0, my_p = 0;
+  if (lane < m) {
+    my_key = ksorted[i0 + lane];
+    const int v = rsorted[i0 + lane];
+    my_r = v & kNodeMask;
+    my_p = v >> kNodeBits;
+  }
+  int al[S][D];
+  double fsign[S];
 #pragma unroll
-  for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, a.q, k);
-  const int rb = R.beg[a.r], rn = R.cnt[a.r];
-  double acc[S];
+  for (int sl = 0; sl < S; ++sl) {
+    int v = lane + 32 * sl, ab = 0;
+    double f = 1.0;
 #pragma unroll
-  for (int s = 0; s < S; ++s) acc[s] = 0.0;
-  for (int j0 = 0; j0 < rn; j0 += 32) {
-    const int j = j0 + lane;
-    if (j < rn) {
-      float rv[D];
-      load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
+    for (int k = D - 1; k >= 0; --k) { al[sl][k] = v % PM; v /= PM; ab += al[sl][k]; f *= fact_d(al[sl][k]); }
+    fsign[sl] = ((ab & 1) ? -1.0 : 1.0) / f;
+  }
+  int t = 0;
+  while (t < m) {
+    const int key = __shfl_sync(0xffffffffu, my_key, t);
+    int e = t + 1;
+    while (e < m && __shfl_sync(0xffffffffu, my_key, e) == key) ++e;
+    const int hidx = key / Q.nn, q = key % Q.nn;
+    const double h = hv[hidx];
+    const float sf = (float)(1.0 / sqrt(2.0 * h * h));
+    CenterHL cQ[D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) hermite_f32<PM>(-minus_center(rv[k], cQ[k]) * sf, sH[wib][lane][k]);
-    } else {
+    for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, q, k);
+    double acc[S];
 #pragma unroll
-      for (int k = 0; k < D; ++k)
+    for (int sl = 0; sl < S; ++sl) acc[sl] = 0.0;
+    int prun = 0;
+    for (int u = t; u < e; ++u) {
+      const int r = __shfl_sync(0xffffffffu, my_r, u);
+      const int p = __shfl_sync(0xffffffffu, my_p, u);
+      prun = max(prun, p);
+      const int rb = R.beg[r], rn = R.cnt[r];
+      for (int j0 = 0; j0 < rn; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < rn) {
+          float rv[D];
+          load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
 #pragma unroll
-        for (int e = 0; e < PM; ++e) sH[wib][lane][k][e] = 0.f;
-    }
-    __syncwarp();
+          for (int k = 0; k < D; ++k) hermite_f32<PM>(-minus_center(rv[k], cQ[k]) * sf, sH[wib][lane][k]);
+        } else {
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const int idx = lane + 32 * s;
-      if (idx < P) {
-        int al[D];
-        {
-          int v = idx;
+          for (int k = 0; k < D; ++k)
 #pragma unroll
-          for (int k = D - 1; k >= 0; --k) { al[k] = v % PM; v /= PM; }
+            for (int e2 = 0; e2 < PM; ++e2) sH[wib][lane][k][e2] = 0.f;
         }
-        float part = 0.f;
-        for (int jj = 0; jj < 32; ++jj) {
-          float t = sH[wib][jj][0][al[0]];
+        __syncwarp();
 #pragma unroll
-          for (int k = 1; k < D; ++k) t *= sH[wib][jj][k][al[k]];
-          part += t;
+        for (int sl = 0; sl < S; ++sl) {
+          const int idx = lane + 32 * sl;
+          bool ok = idx < P;
+#pragma unroll
+          for (int k = 0; k < D; ++k) ok = ok && al[sl][k] < p;
+          if (ok) {
+            float part = 0.f;
+            for (int jj = 0; jj < 32; ++jj) {
+              float tt = sH[wib][jj][0][al[sl][0]];
+#pragma unroll
+              for (int k = 1; k < D; ++k) tt *= sH[wib][jj][k][al[sl][k]];
+              part += tt;
+            }
+            acc[sl] += (double)part;
+          }
         }
-        acc[s] += (double)part;
+        __syncwarp();
       }
     }
-    __syncwarp();
-  }
-  const size_t hq = (size_t)a.h * Q.nn + a.q;
+    const size_t hq = (size_t)hidx * Q.nn + q;
 #pragma unroll
-  for (int s = 0; s < S; ++s) {
-    const int idx = lane + 32 * s;
-    if (idx < P) {
-      int ab = 0;
-      bool ok = true;
-      double f = 1.0;
-      int v = idx;
-#pragma unroll
-      for (int k = D - 1; k >= 0; --k) { const int e = v % PM; v /= PM; ab += e; ok = ok && e < a.p; f *= fact_d(e); }
-      if (ok) atomicAdd(&L[hq * P + idx], ((ab & 1) ? -acc[s] : acc[s]) / f);
+    for (int sl = 0; sl < S; ++sl) {
+      const int idx = lane + 32 * sl;
+      if (idx < P && acc[sl] != 0.0) atomicAdd(&L[hq * P + idx], acc[sl] * fsign[sl]);
     }
+    if (lane == 0) atomicMax(&pused[hq], prun);
+    t = e;
   }
-  if (lane == 0) atomicMax(&pused[hq], a.p);
 }
 
 // --------------------------------------------------------- far to local
@@ -457,6 +486,7 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const Acti
 template <int D>
 __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action* __restrict__ list,
                                             int n, const double* __restrict__ hv,
+                                            const double* __restrict__ spow,
                                             double* __restrict__ L, int* __restrict__ pused) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
@@ -477,7 +507,7 @@ __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action
 #pragma unroll
     for (int e = 0; e < NH; ++e) sH[wib][lane][e] = (float)H[e];
   }
-  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, s, a.p, sM[wib], lane);
+  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, spow + (size_t)a.h * kPowTable, a.p, sM[wib], lane);
   __syncwarp();
   const size_t hq = (size_t)a.h * Q.nn + a.q;
 #pragma unroll
@@ -766,22 +796,32 @@ inline int warp_grid(long items) { return (int)((items * 32 + kT - 1) / kT); }
     default: break;                                    \
   }
 
-cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                        const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches) {
-  if (n <= 0) return cudaSuccess;
-  const long nkeys = (long)b.nh * Q.nn;
+// Sort a list by (bandwidth, query node) into sc: vsorted, ksorted.
+static cudaError_t sort_by_query(const Pair* list, int n, int nnQ, int nh, BaseScratch& sc,
+                                 cudaStream_t s, long long* launches, int** vs, int** ks) {
+  const long nkeys = (long)nh * nnQ;
   cudaError_t e;
   if ((e = sc.cnt->ensure((nkeys + 1) * sizeof(int))) != cudaSuccess) return e;
   if ((e = sc.off->ensure((nkeys + 1) * sizeof(int))) != cudaSuccess) return e;
   if ((e = sc.rsorted->ensure(2 * (size_t)n * sizeof(int))) != cudaSuccess) return e;
   int* cnt = sc.cnt->as<int>();
   int* off = sc.off->as<int>();
-  int* rsorted = sc.rsorted->as<int>();
-  int* ksorted = rsorted + n;
+  *vs = sc.rsorted->as<int>();
+  *ks = *vs + n;
   if ((e = cudaMemsetAsync(cnt, 0, nkeys * sizeof(int), s)) != cudaSuccess) return e;
-  k_base_count<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, cnt);
+  k_sort_count<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, nnQ, cnt);
   if ((e = scan_exclusive(cnt, off, (int)nkeys, *sc.scan_tmp, s, launches)) != cudaSuccess) return e;
-  k_base_scatter<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, Q.nn, off, rsorted, ksorted);
+  k_sort_scatter<<<(n + kT - 1) / kT, kT, 0, s>>>(list, n, nnQ, off, *vs, *ks);
+  *launches += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                        const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches) {
+  if (n <= 0) return cudaSuccess;
+  int *rsorted, *ksorted;
+  cudaError_t e = sort_by_query(list, n, Q.nn, b.nh, sc, s, launches, &rsorted, &ksorted);
+  if (e != cudaSuccess) return e;
   const long warps = (n + kBaseChunk - 1) / kBaseChunk;
   const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (Q.d <= 5) {
@@ -789,7 +829,7 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
   } else {
     k_base_g<<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc);
   }
-  *launches += 3;
+  ++*launches;
   return cudaGetLastError();
 }
 
@@ -798,7 +838,7 @@ cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuff
   if (n <= 0) return cudaSuccess;
   const int g = warp_grid(n);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_farfield<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc));
+    DISPATCH_D(Q.d, k_farfield<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.spow, b.gacc));
   } else {
     k_farfield_g<<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc);
   }
@@ -806,14 +846,21 @@ cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuff
 }
 
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                         const Action* list, int n, cudaStream_t s) {
+                         const Action* list, int n, BaseScratch& sc, cudaStream_t s,
+                         long long* launches) {
   if (n <= 0) return cudaSuccess;
-  const int g = warp_grid(n);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused));
+    int *vsorted, *ksorted;
+    cudaError_t e = sort_by_query(reinterpret_cast<const Pair*>(list), n, Q.nn, b.nh, sc, s, launches,
+                                  &vsorted, &ksorted);
+    if (e != cudaSuccess) return e;
+    const long warps = (n + kBaseChunk - 1) / kBaseChunk;
+    const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, vsorted, ksorted, n, b.h, b.L, b.pused));
   } else {
-    k_local_g<<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
+    k_local_g<<<warp_grid(n), kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
   }
+  ++*launches;
   return cudaGetLastError();
 }
 
@@ -822,7 +869,7 @@ cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& 
   if (n <= 0) return cudaSuccess;
   if (Q.d <= 5) {
     const int g = warp_grid(n);
-    DISPATCH_D(Q.d, k_f2l<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused));
+    DISPATCH_D(Q.d, k_f2l<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.spow, b.L, b.pused));
   } else {
     k_f2l_g<<<(n + kT - 1) / kT, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
   }

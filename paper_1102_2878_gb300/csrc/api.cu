@@ -63,20 +63,24 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
                         const double* h_host, int nh, double eps_eff, TravBuffers* b) {
   cudaStream_t s = ctx->stream;
   const size_t nodes = (size_t)nh * qt->nn;
-  CK(ctx->hvals.ensure(4 * nh * sizeof(double)));
+  CK(ctx->hvals.ensure((4 + kPowTable) * nh * sizeof(double)));
   CK(ctx->node_state.ensure(4 * nodes * sizeof(u64)));
   CK(ctx->lmom.ensure(nodes * qt->P * sizeof(double)));
   CK(ctx->pused.ensure(nodes * sizeof(int)));
   CK(ctx->gacc.ensure((size_t)nh * qt->n * sizeof(double)));
   CK(ctx->counters.ensure(sizeof(RoundCounters)));
   {
-    std::vector<double> hv(4 * (size_t)nh);
+    std::vector<double> hv((4 + kPowTable) * (size_t)nh);
     float* c2 = reinterpret_cast<float*>(hv.data() + 3 * (size_t)nh);
+    double* spow = hv.data() + 4 * (size_t)nh;
     for (int i = 0; i < nh; ++i) {
       hv[i] = h_host[i];
       hv[nh + i] = 1.0 / (2.0 * h_host[i] * h_host[i]);
       hv[2 * nh + i] = 1.0 / (2.0 * h_host[i]);
       c2[i] = (float)(-kLog2e / (2.0 * h_host[i] * h_host[i]));
+      const double sc = 1.0 / std::sqrt(2.0 * h_host[i] * h_host[i]);
+      double v = 1.0;
+      for (int k = 0; k < kPowTable; ++k, v *= sc) spow[(size_t)i * kPowTable + k] = v;
     }
     CK(cudaMemcpyAsync(ctx->hvals.p, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // hv is a stack buffer
@@ -98,6 +102,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->inv2h2 = ctx->hvals.as<double>() + nh;
   b->inv_2h = ctx->hvals.as<double>() + 2 * nh;
   b->c2 = reinterpret_cast<const float*>(ctx->hvals.as<double>() + 3 * nh);
+  b->spow = ctx->hvals.as<double>() + 4 * nh;
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
@@ -152,7 +157,10 @@ dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const
     CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), ls.count, sc, s, &ctx->launches));
   }
   else if (which == 1) CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), ls.count, s));
-  else if (which == 2) CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), ls.count, s));
+  else if (which == 2) {
+    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+    CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), ls.count, sc, s, &ctx->launches));
+  }
   else CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), ls.count, s));
   ++ctx->launches;
   CK(cudaEventRecord(ls.e1, s));
@@ -522,7 +530,7 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
   CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), (int)base.size(), sc, s, &ctx->launches));
   CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), (int)far.size(), s));
-  CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), (int)loc.size(), s));
+  CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), (int)loc.size(), sc, s, &ctx->launches));
   CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), (int)f2l.size(), s));
   CK(cudaEventRecord(ctx->ev[2], s));
   return post(ctx, qt, b, G_dev, nullptr);

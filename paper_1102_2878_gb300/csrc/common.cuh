@@ -19,6 +19,10 @@ __host__ __device__ constexpr int pmax_of(int D) {
 }
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e <= 0 ? 1 : b * ipow_c(b, e - 1); }
 
+// Entries per bandwidth of the moment-scale table (2h^2)^(-k/2), k < 16;
+// the largest |alpha| is D (p_max - 1) <= 10.
+constexpr int kPowTable = 16;
+
 // Row stride of the permuted point copy: float2 rows for D<=2, float4-aligned otherwise.
 inline int padded_dim(int d) { return d <= 2 ? d : ((d + 3) & ~3); }
 

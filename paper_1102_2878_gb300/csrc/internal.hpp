@@ -131,6 +131,7 @@ struct TravBuffers {
   const double* inv2h2;  // [nh] 1/(2h^2)
   const double* inv_2h;  // [nh] 1/(2h)
   const float* c2;       // [nh] -log2(e)/(2h^2) as float, the exp2 scale of exact sums
+  const double* spow;    // [nh][kPowTable] (2h^2)^(-k/2), the moment scales
   double* ku;       // [frontier] K(d^u) of each pending pair, from the bound pass
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums
@@ -164,7 +165,8 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
 cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                             const Action* list, int n, cudaStream_t s);
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                         const Action* list, int n, cudaStream_t s);
+                         const Action* list, int n, BaseScratch& sc, cudaStream_t s,
+                         long long* launches);
 cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                        const Action* list, int n, cudaStream_t s);
 cudaError_t launch_prune_apply(const TreeView& Q, const TreeView& R, const TravBuffers& b,

@@ -491,6 +491,11 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   }
   t->nn = t->lvl_off.back();
   t->depth = (int)t->lvl_off.size() - 1;
+  if (t->nn >= (1 << 27)) {  // node indices share a word with a 4-bit order in the sorted lists
+    ctx->err = "dfgt_build: more than 2^27 tree nodes (raise leaf_size)";
+    rc = DFGT_ECAPACITY;
+    goto fail;
+  }
   t->pts = pbuf[cur];
   pbuf[cur] = nullptr;
   t->perm = perm2[cur];
