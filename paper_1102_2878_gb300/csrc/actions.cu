@@ -541,25 +541,17 @@ __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action
 // Distance-bound prune applied to listed pairs (the traversal applies it
 // inline): L_0(Q) += |R| (K(d^l) + K(d^u)) / 2.
 __global__ void k_prune_apply(TreeView Q, TreeView R, const Pair* __restrict__ list, int n,
-                              const double* __restrict__ hv, double* __restrict__ L,
-                              int* __restrict__ pused) {
+                              const float* __restrict__ inv2h2_dn, const float* __restrict__ inv2h2_up,
+                              double* __restrict__ L, int* __restrict__ pused) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const Pair pr = list[i];
-  const int d = Q.d;
-  double dl2 = 0.0, du2 = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const double ql = Q.lo[(size_t)pr.q * d + k], qu = Q.hi[(size_t)pr.q * d + k];
-    const double rl = R.lo[(size_t)pr.r * d + k], ru = R.hi[(size_t)pr.r * d + k];
-    const double gap = fmax(0.0, fmax(rl - qu, ql - ru));
-    const double far = fmax(ru - ql, qu - rl);
-    dl2 += gap * gap;
-    du2 += far * far;
-  }
-  const double h = hv[pr.h];
-  const double inv = 1.0 / (2.0 * h * h);
+  float dl2, du2, sq, sr;
+  box_geometry<0>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
+  const float Kl = kernel_upper(dl2, inv2h2_dn[pr.h]);
+  const float Ku = kernel_lower(du2, inv2h2_up[pr.h]);
   const size_t hq = (size_t)pr.h * Q.nn + pr.q;
-  atomicAdd(&L[hq * Q.P], 0.5 * (double)R.cnt[pr.r] * (exp(-dl2 * inv) + exp(-du2 * inv)));
+  atomicAdd(&L[hq * Q.P], (double)(0.5f * (float)R.cnt[pr.r]) * ((double)Kl + (double)Ku));
   atomicMax(&pused[hq], 1);
 }
 
@@ -597,6 +589,14 @@ __global__ void __launch_bounds__(kT) k_l2l(TreeView Q, double* __restrict__ L,
   const int p = pused[hq];
   if (p == 0) return;
   const double* Lp = L + hq * P;
+  if (p == 1) {  // only the constant term (prune values): it shifts unchanged
+    if (lane < 2) {
+      const size_t hc = (size_t)hidx * Q.nn + cl + lane;
+      L[hc * P] += Lp[0];
+      if (pused[hc] < 1) pused[hc] = 1;
+    }
+    return;
+  }
   const double h = hv[hidx];
   const double s = 1.0 / sqrt(2.0 * h * h);
   for (int ch = 0; ch < 2; ++ch) {
@@ -879,7 +879,7 @@ cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& 
 cudaError_t launch_prune_apply(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                                const Pair* list, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_prune_apply<<<(n + kT - 1) / kT, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
+  k_prune_apply<<<(n + kT - 1) / kT, kT, 0, s>>>(Q, R, list, n, b.inv2h2_dn, b.inv2h2_up, b.L, b.pused);
   return cudaGetLastError();
 }
 

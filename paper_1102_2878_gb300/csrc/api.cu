@@ -70,14 +70,21 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   CK(ctx->gacc.ensure((size_t)nh * qt->n * sizeof(double)));
   CK(ctx->counters.ensure(sizeof(RoundCounters)));
   {
+    // layout: h | four float arrays packed in three double slots | power table
     std::vector<double> hv((4 + kPowTable) * (size_t)nh);
-    float* c2 = reinterpret_cast<float*>(hv.data() + 3 * (size_t)nh);
+    float* fl = reinterpret_cast<float*>(hv.data() + (size_t)nh);
+    float* inv_dn = fl;
+    float* inv_up = fl + nh;
+    float* i2h_up = fl + 2 * (size_t)nh;
+    float* c2 = fl + 3 * (size_t)nh;
     double* spow = hv.data() + 4 * (size_t)nh;
     for (int i = 0; i < nh; ++i) {
       hv[i] = h_host[i];
-      hv[nh + i] = 1.0 / (2.0 * h_host[i] * h_host[i]);
-      hv[2 * nh + i] = 1.0 / (2.0 * h_host[i]);
-      c2[i] = (float)(-kLog2e / (2.0 * h_host[i] * h_host[i]));
+      const double inv = 1.0 / (2.0 * h_host[i] * h_host[i]);
+      inv_dn[i] = std::nextafter((float)inv, 0.f);
+      inv_up[i] = std::nextafter((float)inv, INFINITY);
+      i2h_up[i] = std::nextafter((float)(1.0 / (2.0 * h_host[i])), INFINITY);
+      c2[i] = (float)(-kLog2e * inv);
       const double sc = 1.0 / std::sqrt(2.0 * h_host[i] * h_host[i]);
       double v = 1.0;
       for (int k = 0; k < kPowTable; ++k, v *= sc) spow[(size_t)i * kPowTable + k] = v;
@@ -99,15 +106,18 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->pused = ctx->pused.as<int>();
   b->gacc = ctx->gacc.as<double>();
   b->h = ctx->hvals.as<double>();
-  b->inv2h2 = ctx->hvals.as<double>() + nh;
-  b->inv_2h = ctx->hvals.as<double>() + 2 * nh;
-  b->c2 = reinterpret_cast<const float*>(ctx->hvals.as<double>() + 3 * nh);
+  const float* fl = reinterpret_cast<const float*>(ctx->hvals.as<double>() + nh);
+  b->inv2h2_dn = fl;
+  b->inv2h2_up = fl + nh;
+  b->inv_2h_up = fl + 2 * nh;
+  b->c2 = fl + 3 * nh;
   b->spow = ctx->hvals.as<double>() + 4 * nh;
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
   b->fix_scale = std::ldexp(1.0, 62) / (double)rt->n;
   b->inv_fix = 1.0 / b->fix_scale;
+  b->fix_scale_dn = std::nextafter((float)b->fix_scale, 0.f);
   b->inv_nr = 1.0 / (double)rt->n;
   b->p_limit = std::min(qt->p_limit, rt->p_limit);
   return DFGT_OK;
@@ -221,8 +231,8 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       if (rc != DFGT_OK) return rc;
     }
     CK(ctx->slots.ensure((size_t)nF * sizeof(int)));
-    CK(ctx->kus.ensure((size_t)nF * sizeof(double)));
-    b.ku = ctx->kus.as<double>();
+    CK(ctx->kus.ensure((size_t)nF * sizeof(float)));
+    b.ku = ctx->kus.as<float>();
     CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_fold(b, qt->nn, s));
     CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));

@@ -175,6 +175,39 @@ __device__ __forceinline__ void atomic_max_f(float* a, float v) {
     atomicMin(reinterpret_cast<unsigned*>(a), __float_as_uint(v));
 }
 
+// Squared distance bounds of two boxes, Eqs. (6)-(7), and their largest
+// sides, in float32 with directed rounding: dl2 never exceeds and du2 never
+// falls below the exact value, and the sides are rounded up, so every
+// kernel value and every truncation bound derived from them stays on the
+// safe side.  (x + |x|)/2 summed over the two orderings of Eq. (6) is
+// max(rl - qu, ql - ru, 0).
+template <int D>
+__device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const TreeView& R, int r,
+                                             float& dl2, float& du2, float& sideQ, float& sideR) {
+  const int d = D > 0 ? D : Q.d;
+  dl2 = du2 = sideQ = sideR = 0.f;
+  for (int k = 0; k < d; ++k) {
+    const float ql = Q.lo[(size_t)q * d + k], qu = Q.hi[(size_t)q * d + k];
+    const float rl = R.lo[(size_t)r * d + k], ru = R.hi[(size_t)r * d + k];
+    const float gap = fmaxf(0.f, fmaxf(__fsub_rd(rl, qu), __fsub_rd(ql, ru)));
+    dl2 = __fmaf_rd(gap, gap, dl2);
+    const float far = fmaxf(__fsub_ru(ru, ql), __fsub_ru(qu, rl));
+    du2 = __fmaf_ru(far, far, du2);
+    sideQ = fmaxf(sideQ, __fsub_ru(qu, ql));
+    sideR = fmaxf(sideR, __fsub_ru(ru, rl));
+  }
+}
+
+// Bounds on the kernel over a node pair: Kl >= K(d^l) and Ku <= K(d^u).
+// expf is within 2 ulps; the 1e-6 factors cover it, and the tiny additive
+// term keeps Kl an upper bound where expf underflows.
+__device__ __forceinline__ float kernel_upper(float dl2, float inv2h2_dn) {
+  return __fmaf_ru(expf(-__fmul_rd(dl2, inv2h2_dn)), 1.000001f, 1e-37f);
+}
+__device__ __forceinline__ float kernel_lower(float du2, float inv2h2_up) {
+  return __fmul_rd(expf(-__fmul_ru(du2, inv2h2_up)), 0.999999f);
+}
+
 // Packed work item of the traversal: query node, reference node,
 // bandwidth index and flags (bit 0: q was just split from its parent).
 struct Pair {

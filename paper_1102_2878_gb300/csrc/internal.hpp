@@ -52,7 +52,7 @@ struct dfgt_ctx {
   DevBuf scan_tmp;
   DevBuf counters;       // RoundCounters on the device
   DevBuf hvals;          // bandwidths, then 1/(2h^2)
-  DevBuf kus;            // double K(d^u) per frontier pair
+  DevBuf kus;            // float lower bound on K(d^u) per frontier pair
   DevBuf frontier[2];    // Pair
   DevBuf slots;          // int child slot per frontier pair
   DevBuf grp_cnt, grp_off, grp_r;  // base-case grouping scratch
@@ -128,15 +128,17 @@ struct TravBuffers {
   int* pused;       // [nh][nnQ]
   double* gacc;     // [nh][nq] (permuted order)
   const double* h;  // [nh]
-  const double* inv2h2;  // [nh] 1/(2h^2)
-  const double* inv_2h;  // [nh] 1/(2h)
+  const float* inv2h2_dn;  // [nh] 1/(2h^2) rounded down
+  const float* inv2h2_up;  // [nh] 1/(2h^2) rounded up
+  const float* inv_2h_up;  // [nh] 1/(2h) rounded up
   const float* c2;       // [nh] -log2(e)/(2h^2) as float, the exp2 scale of exact sums
   const double* spow;    // [nh][kPowTable] (2h^2)^(-k/2), the moment scales
-  double* ku;       // [frontier] K(d^u) of each pending pair, from the bound pass
+  float* ku;        // [frontier] lower bound on K(d^u) of each pending pair
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums
   double fix_scale; // 2^62 / |R|
   double inv_fix;   // 1 / fix_scale
+  float fix_scale_dn;  // fix_scale rounded down
   double inv_nr;    // 1 / |R|
   int p_limit;
   long long base_block;  // exact sum without recursing when |Q||R| <= this

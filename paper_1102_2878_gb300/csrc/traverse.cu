@@ -33,29 +33,9 @@ namespace {
 
 constexpr int kT = 256;
 
-__device__ __forceinline__ u64 to_fix(double x, double scale) {
-  const double v = x * scale * (1.0 - 1e-14);
-  return v > 0.0 ? __double2ull_rz(v) : 0ull;
-}
-
-// Squared distance bounds of two boxes, Eqs. (6)-(7), and their largest sides.
-template <int D>
-__device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const TreeView& R, int r,
-                                             double& dl2, double& du2, double& sideQ,
-                                             double& sideR) {
-  const int d = D > 0 ? D : Q.d;
-  dl2 = du2 = sideQ = sideR = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const double ql = Q.lo[(size_t)q * d + k], qu = Q.hi[(size_t)q * d + k];
-    const double rl = R.lo[(size_t)r * d + k], ru = R.hi[(size_t)r * d + k];
-    // (x + |x|)/2 summed over the two orderings = max(rl-qu, ql-ru, 0)
-    const double gap = fmax(0.0, fmax(rl - qu, ql - ru));
-    dl2 += gap * gap;
-    const double far = fmax(ru - ql, qu - rl);
-    du2 += far * far;
-    sideQ = fmax(sideQ, qu - ql);
-    sideR = fmax(sideR, ru - rl);
-  }
+// Fixed-point units of a lower bound (rounded down).
+__device__ __forceinline__ u64 to_fix_f(float nR, float K, float scale_dn) {
+  return __float2ull_rz(__fmul_rd(__fmul_rd(nR, K), scale_dn));
 }
 
 // FarFieldOrder / LocalAccumulationOrder: least p <= plim whose truncation
@@ -64,23 +44,21 @@ __device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const Tre
 // pairs are rejected after one evaluation.
 constexpr float kSafe = 1.0001f;  // covers float32 evaluation of the bounds
 
-__device__ int order_ff(double r, double nR, int D, double tau, int plim) {
-  if (!(r < 1.0)) return 0;
-  // every bound grows with r and |R|: round those up and tau down
-  const float rf = __double2float_ru(r), nf = __double2float_ru(nR), tf = __double2float_rd(tau);
-  if (!(rf < 1.f) || bound_ff_total(nf, D, rf, plim) * kSafe > tf) return 0;
+// r, |R| arrive rounded up and tau rounded down; every bound grows with r and |R|.
+__device__ int order_ff(float r, float nR, int D, float tau, int plim) {
+  if (!(r < 1.f)) return 0;
+  if (bound_ff_total(nR, D, r, plim) * kSafe > tau) return 0;
   for (int p = 1; p < plim; ++p)
-    if (bound_ff_total(nf, D, rf, p) * kSafe <= tf) return p;
+    if (bound_ff_total(nR, D, r, p) * kSafe <= tau) return p;
   return plim;
 }
 
 // ConvertFarFieldToLocalOrder; 0 = none (r >= 1/2).
-__device__ int order_t(double r, double nR, int D, double tau, int plim) {
-  if (!(r < 0.5)) return 0;
-  const float rf = __double2float_ru(r), nf = __double2float_ru(nR), tf = __double2float_rd(tau);
-  if (!(rf < 0.5f) || bound_f2l_total(nf, D, rf, plim) * kSafe > tf) return 0;
+__device__ int order_t(float r, float nR, int D, float tau, int plim) {
+  if (!(r < 0.5f)) return 0;
+  if (bound_f2l_total(nR, D, r, plim) * kSafe > tau) return 0;
   for (int p = 1; p < plim; ++p)
-    if (bound_f2l_total(nf, D, rf, p) * kSafe <= tf) return p;
+    if (bound_f2l_total(nR, D, r, p) * kSafe <= tau) return p;
   return plim;
 }
 
@@ -133,11 +111,11 @@ __global__ void __launch_bounds__(kT) k_lb(TreeView Q, TreeView R, TravBuffers b
     const size_t hp = (size_t)pr.h * Q.nn + Q.parent[pr.q];
     b.inherited[hq] = b.inherited[hp] + b.decided[hp];  // same value from every pair of q
   }
-  double dl2, du2, sq, sr;
+  float dl2, du2, sq, sr;
   box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
-  const double Ku = exp(-du2 * b.inv2h2[pr.h]);
+  const float Ku = kernel_lower(du2, b.inv2h2_up[pr.h]);
   b.ku[i] = Ku;  // reused by the classification of the same pair
-  const u64 f = to_fix((double)R.cnt[pr.r] * Ku, b.fix_scale);
+  const u64 f = to_fix_f((float)R.cnt[pr.r], Ku, b.fix_scale_dn);
   if (f) atomicAdd(&b.lbsum[hq], f);
 }
 
@@ -160,34 +138,36 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
     if (i < nF) {
       pr = F[i];
       const size_t hq = (size_t)pr.h * Q.nn + pr.q;
-      const double nQ = (double)Q.cnt[pr.q], nR = (double)R.cnt[pr.r];
-      double dl2, du2, sideQ, sideR;
+      const float nQ = (float)Q.cnt[pr.q], nR = (float)R.cnt[pr.r];
+      float dl2, du2, sideQ, sideR;
       box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
-      const double Kl = dl2 > 0.0 ? exp(-dl2 * b.inv2h2[pr.h]) : 1.0;
-      const double Ku = b.ku[i];
-      const double delta_l = nR * Ku;
+      const float Kl = kernel_upper(dl2, b.inv2h2_dn[pr.h]);
+      const float Ku = b.ku[i];
       const u64 lbf = b.inherited[hq] + b.decided[hq] + b.lbsum[hq];
-      const double Gl = (double)lbf * b.inv_fix;
-      const double tau = b.eps_eff * nR * Gl * b.inv_nr;
-      const double inv_2h = b.inv_2h[pr.h];
-      if (0.5 * nR * (Kl - Ku) <= tau) {
+      // tau = eps |R| G^l(Q) / |R_total| (CanSummarize), rounded down
+      const float tau = __double2float_rd(b.eps_eff * (double)nR * ((double)lbf * b.inv_fix) * b.inv_nr);
+      // prune: the kernel over the pair lies in [Ku, Kl]; the midpoint is off by
+      // at most half the width
+      const float err_prune = __fmul_ru(0.5f * nR, __fsub_ru(Kl, Ku));
+      if (err_prune <= tau) {
         kind = 0;
-        atomicAdd(&b.L[hq * P], 0.5 * nR * (Kl + Ku));
+        atomicAdd(&b.L[hq * P], (double)(0.5f * nR) * ((double)Kl + (double)Ku));
         atomicMax(&b.pused[hq], 1);
       } else {
         int pF = 0, pD = 0, pT = 0;
-        if (tau > 0.0) {
-          pF = order_ff(sideR * inv_2h, nR, d, tau, b.p_limit);
-          pD = order_ff(sideQ * inv_2h, nR, d, tau, b.p_limit);
-          pT = order_t(fmax(sideQ, sideR) * inv_2h, nR, d, tau, b.p_limit);
+        if (tau > 0.f) {
+          const float inv_2h = b.inv_2h_up[pr.h];
+          pF = order_ff(__fmul_ru(sideR, inv_2h), nR, d, tau, b.p_limit);
+          pD = order_ff(__fmul_ru(sideQ, inv_2h), nR, d, tau, b.p_limit);
+          pT = order_t(__fmul_ru(fmaxf(sideQ, sideR), inv_2h), nR, d, tau, b.p_limit);
         }
         // ChooseBestMethod with c_F = D N_Q p^D, c_D = D N_R p^D,
         // c_T = D p^{2D}, c_E = D N_Q N_R; ties go F, D, T, E.
-        const double cF = pF ? d * nQ * pow((double)pF, (double)d) : INFINITY;
-        const double cD = pD ? d * nR * pow((double)pD, (double)d) : INFINITY;
-        const double cT = pT ? d * pow((double)pT, 2.0 * d) : INFINITY;
-        const double cE = d * nQ * nR;
-        const double m = fmin(fmin(cF, cD), fmin(cT, cE));
+        const float cF = pF ? d * nQ * pow_int_f((float)pF, d) : INFINITY;
+        const float cD = pD ? d * nR * pow_int_f((float)pD, d) : INFINITY;
+        const float cT = pT ? d * pow_int_f((float)pT, 2 * d) : INFINITY;
+        const float cE = d * nQ * nR;
+        const float m = fminf(fminf(cF, cD), fminf(cT, cE));
         if (pF && cF == m) { kind = 1; order = pF; }
         else if (pD && cD == m) { kind = 2; order = pD; }
         else if (pT && cT == m) { kind = 3; order = pT; }
@@ -195,7 +175,7 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
           // exact sum: at a leaf pair (DFGTBase), or for any pair small
           // enough that recursing further cannot pay (|Q||R| <= base_block)
           const int ql = Q.left[pr.q], rl = R.left[pr.r];
-          if ((ql < 0 && rl < 0) || nQ * nR <= (double)b.base_block) {
+          if ((ql < 0 && rl < 0) || (double)nQ * nR <= (double)b.base_block) {
             kind = 4;
             inter = (unsigned long long)(nQ * nR);
           } else {
@@ -205,7 +185,7 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
         }
       }
       if (kind <= 4) {
-        const u64 f = to_fix(delta_l, b.fix_scale);
+        const u64 f = to_fix_f(nR, Ku, b.fix_scale_dn);
         if (f) atomicAdd(&b.incr[hq], f);
       }
     }

@@ -222,34 +222,73 @@ __device__ __forceinline__ int digit(int idx, int dd) {
   return v % PM;
 }
 
-// Leaf moments (AccumulateFarFieldMoment): lane per coefficient position,
-// loop over the leaf's points, float64.
+// 1/n! for n < 16.
+__constant__ double c_inv_fact[16] = {
+    1.0, 1.0, 0.5, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320,
+    1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
+    1.0 / 87178291200.0, 1.0 / 1307674368000.0};
+
+// Leaf moments (AccumulateFarFieldMoment): for each batch of 32 points the
+// lanes tabulate the powers (r_k - c_k)^e, e < p_max, of one point each in
+// shared memory; then each lane owns coefficient positions and accumulates
+// prod_k table[j][k][alpha_k] over the batch.  Float64 throughout.
 template <int D>
-__global__ void k_leaf_moments(TreeView t, double* __restrict__ mom) {
+__global__ void __launch_bounds__(kT) k_leaf_moments(TreeView t, double* __restrict__ mom) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  constexpr int S = (P + 31) / 32;
+  constexpr int W = kT / 32;
+  __shared__ double sPow[W][32][D][PM];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * W + wib;
   if (w >= t.nn || t.left[w] >= 0) return;
   double c[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) c[k] = 0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
+  int al[S][D];
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    int v = lane + 32 * sl;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) { al[sl][k] = v % PM; v /= PM; }
+  }
+  double acc[S];
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) acc[sl] = 0.0;
   const int b = t.beg[w], n = t.cnt[w];
-  for (int idx = lane; idx < P; idx += 32) {
-    int al[D];
+  for (int j0 = 0; j0 < n; j0 += 32) {
+    const int j = j0 + lane;
 #pragma unroll
-    for (int k = 0; k < D; ++k) al[k] = digit<D, PM>(idx, k);
-    double acc = 0.0;
-    for (int j = 0; j < n; ++j) {
-      double term = 1.0;
+    for (int k = 0; k < D; ++k) {
+      const double x = j < n ? (double)t.pts[(size_t)(b + j) * t.dp + k] - c[k] : 0.0;
+      double v = j < n ? 1.0 : 0.0;  // padding points contribute nothing
 #pragma unroll
-      for (int k = 0; k < D; ++k) term *= pow_int((double)t.pts[(size_t)(b + j) * t.dp + k] - c[k], al[k]);
-      acc += term;
+      for (int e = 0; e < PM; ++e) { sPow[wib][lane][k][e] = v; v *= x; }
     }
+    __syncwarp();
+    const int jn = min(32, n - j0);
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+      if (lane + 32 * sl >= P) break;
+      double a = 0.0;
+      for (int jj = 0; jj < jn; ++jj) {
+        double term = sPow[wib][jj][0][al[sl][0]];
+#pragma unroll
+        for (int k = 1; k < D; ++k) term *= sPow[wib][jj][k][al[sl][k]];
+        a += term;
+      }
+      acc[sl] += a;
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) {
+    const int idx = lane + 32 * sl;
+    if (idx >= P) break;
     double f = 1.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) f *= fact_d(al[k]);
-    mom[(size_t)w * P + idx] = acc / f;
+    for (int k = 0; k < D; ++k) f *= c_inv_fact[al[sl][k]];
+    mom[(size_t)w * P + idx] = acc[sl] * f;
   }
 }
 
@@ -283,14 +322,17 @@ __global__ void k_f2f_level(TreeView t, int a, int e, double* __restrict__ mom) 
                        0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
       int stride = 1;
       for (int j = D - 1; j > k; --j) stride *= PM;
+      double T[PM];  // x^e / e!
+      T[0] = 1.0;
+#pragma unroll
+      for (int e2 = 1; e2 < PM; ++e2) T[e2] = T[e2 - 1] * x * (1.0 / (double)e2);
       for (int idx = lane; idx < P; idx += 32) {
         const int gk = (idx / stride) % PM;
         // sum over alpha_k <= gamma_k of m[.. alpha_k ..] x^{gamma_k - alpha_k} / (gamma_k - alpha_k)!
-        double sum = 0.0, term = 1.0;
-        for (int dlt = 0; dlt <= gk; ++dlt) {
-          sum += sM[wib][cur][idx - dlt * stride] * term;
-          term = term * x / (double)(dlt + 1);
-        }
+        double sum = 0.0;
+#pragma unroll
+        for (int dlt = 0; dlt < PM; ++dlt)
+          if (dlt <= gk) sum += sM[wib][cur][idx - dlt * stride] * T[dlt];
         sM[wib][cur ^ 1][idx] = sum;
       }
       __syncwarp();
