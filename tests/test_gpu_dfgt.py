@@ -74,7 +74,9 @@ def test_each_reference_counted_once(dev):
     q = datagen.isotropic_mixture(999, 3, 6, 0.05, seed=2)
     qt, rt = dfgt.Tree(dev, to_cuda(q), leaf_size=8), dfgt.Tree(dev, to_cuda(r), leaf_size=8)
     G, _ = dfgt.kde_sum(dev, qt, rt, [1e6], 1e-2)
-    assert np.allclose(G.cpu().numpy(), 5000.0, rtol=1e-9, atol=0)
+    # summaries and exact sums carry float32 rounding; a reference point
+    # counted twice or missed would be off by 1/5000
+    assert np.allclose(G.cpu().numpy(), 5000.0, rtol=1e-6, atol=0)
 
 
 def test_degenerate_inputs(dev, orc):
