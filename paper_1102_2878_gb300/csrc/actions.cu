@@ -165,29 +165,43 @@ __device__ __forceinline__ int pick_group(int qn) {
   return best;
 }
 
-// References staged per warp: as many as 48 KB of shared memory per block allows.
+// References staged per warp: D+1 rows of as many points as 48 KB of
+// shared memory per block allows.
 template <int D>
 constexpr int base_tile() {
-  return ((48 * 1024 / 4 / kWarpsPerBlock) / D) & ~1;
+  return ((48 * 1024 / 4 / kWarpsPerBlock) / (D + 1)) & ~1;
 }
+
+// Two forms of the exponent x = c |q - r|^2, c = -log2(e)/(2h^2):
+//  * direct: differences q - r, D packed add + D packed fma per pair of
+//    references; rounding changes a term by at most (D+3) u x relative;
+//  * expanded about the query node's center m, with q~ = q - m, r~ = r - m:
+//    x = A_q + B_r + sum_k W_qk r~_k, A_q = c|q~|^2, W_q = -2c q~, B_r = c|r~|^2
+//    staged with the reference; one packed add + D packed fma per pair.
+//    Its rounding error in x is at most (D+3) u |c| (|q~| + |r~|)^2, the
+//    same for every term, so a run uses it only when that bound, taken over
+//    the query box and the farthest corner of every reference box, is at
+//    most kExpandedErr relative; otherwise the direct form.
+constexpr float kExpandedErr = 5e-6f;
 
 template <int D>
 __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                              const int* __restrict__ ksorted, int n,
                                              const float* __restrict__ c2v,
+                                             const float* __restrict__ inv2h2_up,
                                              double* __restrict__ gacc) {
   constexpr int TILE = base_tile<D>();
-  __shared__ __align__(16) float sR[kWarpsPerBlock][D][TILE];
+  __shared__ __align__(16) float sR[kWarpsPerBlock][D + 1][TILE];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
   if (i0 >= n) return;
   const int m = (int)min((long)kBaseChunk, n - i0);
-  int my_key = -1, my_rb = 0, my_rn = 0;
+  int my_key = -1, my_r = 0, my_rb = 0, my_rn = 0;
   if (lane < m) {
     my_key = ksorted[i0 + lane];
-    const int r = rsorted[i0 + lane] & kNodeMask;
-    my_rb = R.beg[r];
-    my_rn = R.cnt[r];
+    my_r = rsorted[i0 + lane] & kNodeMask;
+    my_rb = R.beg[my_r];
+    my_rn = R.cnt[my_r];
   }
   int t = 0;
   while (t < m) {
@@ -199,13 +213,34 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
     for (int u = t; u < e; ++u) tot += __shfl_sync(0xffffffffu, my_rn, u);
     const int hidx = key / Q.nn, q = key % Q.nn;
     const float c2 = c2v[hidx];
-    const float2 c2p = make_float2(c2, c2);
     const int qb = Q.beg[q], qn = Q.cnt[q];
     const int g = pick_group(qn);
     const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
+    // expansion center and the error test of the expanded form
+    float mc[D];
+    float rhoQ2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float lo = Q.lo[(size_t)q * D + k], hi = Q.hi[(size_t)q * D + k];
+      mc[k] = 0.5f * (lo + hi);
+      const float w = fmaxf(__fsub_ru(hi, mc[k]), __fsub_ru(mc[k], lo));
+      rhoQ2 = __fmaf_ru(w, w, rhoQ2);
+    }
+    float far2 = 0.f;  // farthest reference-box corner from mc, squared
+    if (lane >= t && lane < e) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const float lo = R.lo[(size_t)my_r * D + k], hi = R.hi[(size_t)my_r * D + k];
+        const float w = fmaxf(fabsf(__fsub_ru(hi, mc[k])), fabsf(__fsub_rd(lo, mc[k])));
+        far2 = __fmaf_ru(w, w, far2);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) far2 = fmaxf(far2, __shfl_xor_sync(0xffffffffu, far2, o));
+    const float span = __fadd_ru(__fsqrt_ru(rhoQ2), __fsqrt_ru(far2));
+    const bool expanded =
+        (float)(D + 3) * 5.9604645e-08f * span * span * inv2h2_up[hidx] <= kExpandedErr;
     // Stage references [j0, j0 + tn) of the run's concatenated point list,
-    // negated, padded with far points to an even count; entry by entry, so
-    // no lane searches for its source.
+    // padded with a far point to an even count; entry by entry.
     auto stage = [&](int j0, int tn) {
       const int tn2 = (tn + 1) & ~1;
       __syncwarp();
@@ -217,14 +252,27 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
         for (int jj = lo + lane; jj < hi; jj += 32) {
           float rv[D];
           load_point<D>(R.pts + (size_t)(rb_u + jj) * R.dp, rv);
+          const int j = base + jj - j0;
+          if (expanded) {
+            float b2 = 0.f;
 #pragma unroll
-          for (int k = 0; k < D; ++k) sR[wib][k][base + jj - j0] = -rv[k];
+            for (int k = 0; k < D; ++k) {
+              const float rt = rv[k] - mc[k];
+              sR[wib][k][j] = rt;
+              b2 = fmaf(rt, rt, b2);
+            }
+            sR[wib][D][j] = c2 * b2;
+          } else {
+#pragma unroll
+            for (int k = 0; k < D; ++k) sR[wib][k][j] = -rv[k];
+          }
         }
         base += rn_u;
       }
       if (lane == 0 && tn2 > tn) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) sR[wib][k][tn] = kFarNeg;
+        for (int k = 0; k < D; ++k) sR[wib][k][tn] = expanded ? 0.f : kFarNeg;
+        sR[wib][D][tn] = -1.0e30f;
       }
       __syncwarp();
       return tn2;
@@ -238,10 +286,21 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
       if (ok) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
       else
 #pragma unroll
-        for (int k = 0; k < D; ++k) qv[k] = 0.f;
-      float2 qq[D];
+        for (int k = 0; k < D; ++k) qv[k] = mc[k];
+      float2 qq[D];  // direct: (q, q); expanded: (W, W)
+      float2 aa;     // expanded: (A, A)
+      {
+        float a2 = 0.f;
 #pragma unroll
-      for (int k = 0; k < D; ++k) qq[k] = make_float2(qv[k], qv[k]);
+        for (int k = 0; k < D; ++k) {
+          const float qt = qv[k] - mc[k];
+          a2 = fmaf(qt, qt, a2);
+          const float wv = expanded ? -2.f * c2 * qt : qv[k];
+          qq[k] = make_float2(wv, wv);
+        }
+        aa = make_float2(c2 * a2, c2 * a2);
+      }
+      const float2 c2p = make_float2(c2, c2);
       float S = 0.f, C = 0.f;
       for (int j0 = 0; j0 < tot; j0 += TILE) {
         const int tn2 = one_tile ? staged2 : stage(j0, min(TILE, tot - j0));
@@ -249,17 +308,27 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
         for (int jr = 2 * gid; jr < tn2; jr += 32 * ngrp) {
           const int je = min(jr + 32 * ngrp, tn2);
           float2 part = make_float2(0.f, 0.f);
+          if (expanded) {
 #pragma unroll 2
-          for (int jp = jr; jp < je; jp += 2 * ngrp) {
-            float2 d2 = make_float2(0.f, 0.f);
+            for (int jp = jr; jp < je; jp += 2 * ngrp) {
+              float2 a = __fadd2_rn(aa, *reinterpret_cast<const float2*>(&sR[wib][D][jp]));
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              const float2 rr = *reinterpret_cast<const float2*>(&sR[wib][k][jp]);
-              const float2 dd = __fadd2_rn(qq[k], rr);
-              d2 = __ffma2_rn(dd, dd, d2);
+              for (int k = 0; k < D; ++k)
+                a = __ffma2_rn(qq[k], *reinterpret_cast<const float2*>(&sR[wib][k][jp]), a);
+              part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
             }
-            const float2 a = __fmul2_rn(d2, c2p);
-            part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
+          } else {
+#pragma unroll 2
+            for (int jp = jr; jp < je; jp += 2 * ngrp) {
+              float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+              for (int k = 0; k < D; ++k) {
+                const float2 dd = __fadd2_rn(qq[k], *reinterpret_cast<const float2*>(&sR[wib][k][jp]));
+                d2 = __ffma2_rn(dd, dd, d2);
+              }
+              const float2 a = __fmul2_rn(d2, c2p);
+              part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
+            }
           }
           const float y = (part.x + part.y) - C;
           const float tt = S + y;
@@ -825,7 +894,7 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
   const long warps = (n + kBaseChunk - 1) / kBaseChunk;
   const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc));
+    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc));
   } else {
     k_base_g<<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc);
   }
