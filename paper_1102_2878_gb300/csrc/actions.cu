@@ -149,20 +149,84 @@ __global__ void k_sort_scatter(const Pair* __restrict__ list, int n, int nnQ, in
   ksorted[pos] = key;
 }
 
-// Lane-group width for |Q| queries: the power of two g <= 32 that leaves the
-// fewest idle query slots in ceil(|Q|/g) passes (ties go to the larger g).
+// Lane-group width g (a power of two <= 32) for |Q| queries when every lane
+// holds two queries (a pass covers 2g of them): the width that leaves the
+// fewest idle query slots, ties going to the larger g.
 __device__ __forceinline__ int pick_group(int qn) {
-  if (qn <= 8) {
-    int g = 1;
-    while (g < qn) g <<= 1;
-    return g;
-  }
-  int best = 32, waste = ((qn + 31) / 32) * 32 - qn;
-  for (int g = 16; g >= 8; g >>= 1) {
-    const int wst = ((qn + g - 1) / g) * g - qn;
+  int best = 32, waste = ((qn + 63) / 64) * 64 - qn;
+  for (int g = 16; g >= 1; g >>= 1) {
+    const int wst = ((qn + 2 * g - 1) / (2 * g)) * (2 * g) - qn;
     if (wst < waste) { waste = wst; best = g; }
   }
   return best;
+}
+
+// Kahan step of a float32 running sum.
+__device__ __forceinline__ void kahan_add(float& S, float& C, float v) {
+  const float y = v - C;
+  const float t = S + y;
+  C = (t - S) - y;
+  S = t;
+}
+
+// One lane's share of a staged tile: reference pairs jp = 2*gid, 2*gid + 2*NG, ...
+// against the lane's two queries a and b.  EXP selects the expanded form
+// (qa/qb hold W, aa/ab hold A) or the direct form (qa/qb hold the query).
+template <int D, int NG, bool EXP, int TILE>
+__device__ __forceinline__ void base_tile_sums(const float (*sR)[TILE], int tn2, int gid,
+                                               const float2* qa, const float2* qb, float2 aa, float2 ab,
+                                               float2 c2p, float& Sa, float& Ca, float& Sb, float& Cb) {
+  constexpr int STEP = 2 * NG;
+  for (int jr = 2 * gid; jr < tn2; jr += 16 * STEP) {
+    const int je = min(jr + 16 * STEP, tn2);
+    float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int jp = jr; jp < je; jp += STEP) {
+      float2 rr[D + 1];
+#pragma unroll
+      for (int k = 0; k < (EXP ? D + 1 : D); ++k) rr[k] = *reinterpret_cast<const float2*>(&sR[k][jp]);
+      float2 xa, xb;
+      if constexpr (EXP) {
+        xa = __fadd2_rn(aa, rr[D]);
+        xb = __fadd2_rn(ab, rr[D]);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          xa = __ffma2_rn(qa[k], rr[k], xa);
+          xb = __ffma2_rn(qb[k], rr[k], xb);
+        }
+      } else {
+        float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float2 ta = __fadd2_rn(qa[k], rr[k]);
+          const float2 tb = __fadd2_rn(qb[k], rr[k]);
+          da = __ffma2_rn(ta, ta, da);
+          db = __ffma2_rn(tb, tb, db);
+        }
+        xa = __fmul2_rn(da, c2p);
+        xb = __fmul2_rn(db, c2p);
+      }
+      pa = __fadd2_rn(pa, make_float2(ex2_approx(xa.x), ex2_approx(xa.y)));
+      pb = __fadd2_rn(pb, make_float2(ex2_approx(xb.x), ex2_approx(xb.y)));
+    }
+    kahan_add(Sa, Ca, pa.x + pa.y);
+    kahan_add(Sb, Cb, pb.x + pb.y);
+  }
+}
+
+template <int D, bool EXP, int TILE>
+__device__ __forceinline__ void base_tile_dispatch(int ngrp, const float (*sR)[TILE], int tn2, int gid,
+                                                   const float2* qa, const float2* qb, float2 aa,
+                                                   float2 ab, float2 c2p, float& Sa, float& Ca,
+                                                   float& Sb, float& Cb) {
+  switch (ngrp) {
+    case 1: base_tile_sums<D, 1, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
+    case 2: base_tile_sums<D, 2, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
+    case 4: base_tile_sums<D, 4, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
+    case 8: base_tile_sums<D, 8, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
+    case 16: base_tile_sums<D, 16, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
+    default: base_tile_sums<D, 32, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
+  }
 }
 
 // References staged per warp: D+1 rows of as many points as 48 KB of
@@ -185,7 +249,7 @@ constexpr int base_tile() {
 constexpr float kExpandedErr = 5e-6f;
 
 template <int D>
-__global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
+__global__ void __launch_bounds__(kT, 3) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                              const int* __restrict__ ksorted, int n,
                                              const float* __restrict__ c2v,
                                              const float* __restrict__ inv2h2_up,
@@ -279,66 +343,51 @@ __global__ void __launch_bounds__(kT) k_base(TreeView Q, TreeView R, const int* 
     };
     const bool one_tile = tot <= TILE;
     const int staged2 = one_tile ? stage(0, tot) : 0;
-    for (int q0 = 0; q0 < qn; q0 += g) {
-      const int qi = q0 + ql;
-      const bool ok = qi < qn;
-      float qv[D];
-      if (ok) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
-      else
-#pragma unroll
-        for (int k = 0; k < D; ++k) qv[k] = mc[k];
-      float2 qq[D];  // direct: (q, q); expanded: (W, W)
-      float2 aa;     // expanded: (A, A)
+    const float2 c2p = make_float2(c2, c2);
+    // every lane holds queries q0 + ql and q0 + g + ql
+    for (int q0 = 0; q0 < qn; q0 += 2 * g) {
+      const int qia = q0 + ql, qib = q0 + g + ql;
+      const bool oka = qia < qn, okb = qib < qn;
+      float2 wqa[D], wqb[D], aa, ab;
       {
-        float a2 = 0.f;
+        float va[D], vb[D];
+        if (oka) load_point<D>(Q.pts + (size_t)(qb + qia) * Q.dp, va);
+        else
+#pragma unroll
+          for (int k = 0; k < D; ++k) va[k] = mc[k];
+        if (okb) load_point<D>(Q.pts + (size_t)(qb + qib) * Q.dp, vb);
+        else
+#pragma unroll
+          for (int k = 0; k < D; ++k) vb[k] = mc[k];
+        float a2 = 0.f, b2 = 0.f;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const float qt = qv[k] - mc[k];
-          a2 = fmaf(qt, qt, a2);
-          const float wv = expanded ? -2.f * c2 * qt : qv[k];
-          qq[k] = make_float2(wv, wv);
+          const float ta = va[k] - mc[k], tb = vb[k] - mc[k];
+          a2 = fmaf(ta, ta, a2);
+          b2 = fmaf(tb, tb, b2);
+          const float wa = expanded ? -2.f * c2 * ta : va[k];
+          const float wb = expanded ? -2.f * c2 * tb : vb[k];
+          wqa[k] = make_float2(wa, wa);
+          wqb[k] = make_float2(wb, wb);
         }
         aa = make_float2(c2 * a2, c2 * a2);
+        ab = make_float2(c2 * b2, c2 * b2);
       }
-      const float2 c2p = make_float2(c2, c2);
-      float S = 0.f, C = 0.f;
+      float Sa = 0.f, Ca = 0.f, Sb = 0.f, Cb = 0.f;
       for (int j0 = 0; j0 < tot; j0 += TILE) {
         const int tn2 = one_tile ? staged2 : stage(j0, min(TILE, tot - j0));
-        // 16 reference pairs per lane per compensated run
-        for (int jr = 2 * gid; jr < tn2; jr += 32 * ngrp) {
-          const int je = min(jr + 32 * ngrp, tn2);
-          float2 part = make_float2(0.f, 0.f);
-          if (expanded) {
-#pragma unroll 2
-            for (int jp = jr; jp < je; jp += 2 * ngrp) {
-              float2 a = __fadd2_rn(aa, *reinterpret_cast<const float2*>(&sR[wib][D][jp]));
-#pragma unroll
-              for (int k = 0; k < D; ++k)
-                a = __ffma2_rn(qq[k], *reinterpret_cast<const float2*>(&sR[wib][k][jp]), a);
-              part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
-            }
-          } else {
-#pragma unroll 2
-            for (int jp = jr; jp < je; jp += 2 * ngrp) {
-              float2 d2 = make_float2(0.f, 0.f);
-#pragma unroll
-              for (int k = 0; k < D; ++k) {
-                const float2 dd = __fadd2_rn(qq[k], *reinterpret_cast<const float2*>(&sR[wib][k][jp]));
-                d2 = __ffma2_rn(dd, dd, d2);
-              }
-              const float2 a = __fmul2_rn(d2, c2p);
-              part = __fadd2_rn(part, make_float2(ex2_approx(a.x), ex2_approx(a.y)));
-            }
-          }
-          const float y = (part.x + part.y) - C;
-          const float tt = S + y;
-          C = (tt - S) - y;
-          S = tt;
-        }
+        if (expanded)
+          base_tile_dispatch<D, true, TILE>(ngrp, sR[wib], tn2, gid, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
+        else
+          base_tile_dispatch<D, false, TILE>(ngrp, sR[wib], tn2, gid, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
       }
-      float v = S - C;
-      for (int o = g; o < 32; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (gid == 0 && ok) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], (double)v);
+      float va = Sa - Ca, vb = Sb - Cb;
+      for (int o = g; o < 32; o <<= 1) {
+        va += __shfl_xor_sync(0xffffffffu, va, o);
+        vb += __shfl_xor_sync(0xffffffffu, vb, o);
+      }
+      if (gid == 0 && oka) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qia], (double)va);
+      if (gid == 0 && okb) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qib], (double)vb);
     }
     t = e;
   }

@@ -32,6 +32,9 @@ namespace dfgt {
 namespace {
 
 constexpr int kT = 256;
+constexpr float kMaxSummaryPoints = 4096.f;
+constexpr int kSlotBits = 28;  // frontier slots stay below 2^28 (checked by the host)
+constexpr int kSplitROnly = 1, kSplitQOnly = 2;
 
 // Fixed-point units of a lower bound (rounded down).
 __device__ __forceinline__ u64 to_fix_f(float nR, float K, float scale_dn) {
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
   for (int i0 = blockIdx.x * kT; i0 < nF; i0 += stride) {
     const int i = i0 + threadIdx.x;
     // kind: -1 none, 0 prune, 1 F, 2 D, 3 T, 4 base, 5 recurse
-    int kind = -1, order = 0, nchild = 0;
+    int kind = -1, order = 0, nchild = 0, split = 0;
     Pair pr{0, 0, 0, 0};
     unsigned long long inter = 0;
     if (i < nF) {
@@ -183,6 +186,18 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
             nchild = (ql >= 0 && rl >= 0) ? 4 : 2;
           }
         }
+        // Work cap: a far-field evaluation over more than kMaxSummaryPoints
+        // queries, or a local accumulation over more than that many
+        // references, recurses into the children of that side instead.  Both
+        // summaries are additive over a partition of that side and their
+        // order depends only on the other side's box, so the parts take the
+        // same order within their own (proportional) budgets: no accuracy is
+        // lost and the work of one warp stays bounded.
+        if (kind == 1 && nQ > kMaxSummaryPoints && Q.left[pr.q] >= 0) {
+          kind = 5; nchild = 2; split = kSplitQOnly;
+        } else if (kind == 2 && nR > kMaxSummaryPoints && R.left[pr.r] >= 0) {
+          kind = 5; nchild = 2; split = kSplitROnly;
+        }
       }
       if (kind <= 4) {
         const u64 f = to_fix_f(nR, Ku, b.fix_scale_dn);
@@ -194,7 +209,7 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
     // the next frontier
     {
       const int s0 = warp_alloc(&ctr->n_next, nchild);
-      if (i < nF) slot[i] = nchild ? s0 : -1;
+      if (i < nF) slot[i] = nchild ? (s0 | (split << kSlotBits)) : -1;
     }
     {
       const int s1 = warp_alloc(&ctr->n_far, kind == 1);
@@ -218,11 +233,18 @@ __global__ void __launch_bounds__(kT) k_emit(const int* __restrict__ Qleft, cons
                                              const int* __restrict__ slot, Pair* __restrict__ next) {
   const int i = blockIdx.x * kT + threadIdx.x;
   if (i >= nF) return;
-  const int s0 = slot[i];
-  if (s0 < 0) return;
+  const int sv = slot[i];
+  if (sv < 0) return;
+  const int s0 = sv & ((1 << kSlotBits) - 1), split = sv >> kSlotBits;
   const Pair pr = F[i];
   const int ql = Qleft[pr.q], rl = Rleft[pr.r];
-  if (ql < 0) {
+  if (split == kSplitROnly) {
+    next[s0] = Pair{pr.q, rl, pr.h, 0};
+    next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
+  } else if (split == kSplitQOnly) {
+    next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
+    next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
+  } else if (ql < 0) {
     next[s0] = Pair{pr.q, rl, pr.h, 0};
     next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
   } else if (rl < 0) {
