@@ -169,19 +169,19 @@ __device__ __forceinline__ void kahan_add(float& S, float& C, float v) {
   S = t;
 }
 
-// One lane's share of a staged tile: reference pairs jp = 2*gid, 2*gid + 2*NG, ...
-// against the lane's two queries a and b.  EXP selects the expanded form
-// (qa/qb hold W, aa/ab hold A) or the direct form (qa/qb hold the query).
-template <int D, int NG, bool EXP, int TILE>
-__device__ __forceinline__ void base_tile_sums(const float (*sR)[TILE], int tn2, int gid,
+// One lane's share of a staged tile: reference pairs jp = 2*gid, 2*gid + step, ...
+// (step = 2 * number of lane groups) against the lane's two queries a and b.
+// EXP selects the expanded form (qa/qb hold W, aa/ab hold A) or the direct
+// form (qa/qb hold the query).  Runs of 16 pairs are Kahan-compensated.
+template <int D, bool EXP, int TILE>
+__device__ __forceinline__ void base_tile_sums(const float (*sR)[TILE], int tn2, int gid, int step,
                                                const float2* qa, const float2* qb, float2 aa, float2 ab,
                                                float2 c2p, float& Sa, float& Ca, float& Sb, float& Cb) {
-  constexpr int STEP = 2 * NG;
-  for (int jr = 2 * gid; jr < tn2; jr += 16 * STEP) {
-    const int je = min(jr + 16 * STEP, tn2);
+  for (int jr = 2 * gid; jr < tn2; jr += 16 * step) {
+    const int je = min(jr + 16 * step, tn2);
     float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
 #pragma unroll 2
-    for (int jp = jr; jp < je; jp += STEP) {
+    for (int jp = jr; jp < je; jp += step) {
       float2 rr[D + 1];
 #pragma unroll
       for (int k = 0; k < (EXP ? D + 1 : D); ++k) rr[k] = *reinterpret_cast<const float2*>(&sR[k][jp]);
@@ -211,21 +211,6 @@ __device__ __forceinline__ void base_tile_sums(const float (*sR)[TILE], int tn2,
     }
     kahan_add(Sa, Ca, pa.x + pa.y);
     kahan_add(Sb, Cb, pb.x + pb.y);
-  }
-}
-
-template <int D, bool EXP, int TILE>
-__device__ __forceinline__ void base_tile_dispatch(int ngrp, const float (*sR)[TILE], int tn2, int gid,
-                                                   const float2* qa, const float2* qb, float2 aa,
-                                                   float2 ab, float2 c2p, float& Sa, float& Ca,
-                                                   float& Sb, float& Cb) {
-  switch (ngrp) {
-    case 1: base_tile_sums<D, 1, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
-    case 2: base_tile_sums<D, 2, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
-    case 4: base_tile_sums<D, 4, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
-    case 8: base_tile_sums<D, 8, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
-    case 16: base_tile_sums<D, 16, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
-    default: base_tile_sums<D, 32, EXP, TILE>(sR, tn2, gid, qa, qb, aa, ab, c2p, Sa, Ca, Sb, Cb); break;
   }
 }
 
@@ -377,9 +362,9 @@ __global__ void __launch_bounds__(kT, 3) k_base(TreeView Q, TreeView R, const in
       for (int j0 = 0; j0 < tot; j0 += TILE) {
         const int tn2 = one_tile ? staged2 : stage(j0, min(TILE, tot - j0));
         if (expanded)
-          base_tile_dispatch<D, true, TILE>(ngrp, sR[wib], tn2, gid, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
+          base_tile_sums<D, true, TILE>(sR[wib], tn2, gid, 2 * ngrp, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
         else
-          base_tile_dispatch<D, false, TILE>(ngrp, sR[wib], tn2, gid, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
+          base_tile_sums<D, false, TILE>(sR[wib], tn2, gid, 2 * ngrp, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
       }
       float va = Sa - Ca, vb = Sb - Cb;
       for (int o = g; o < 32; o <<= 1) {
