@@ -149,14 +149,20 @@ __global__ void k_sort_scatter(const Pair* __restrict__ list, int n, int nnQ, in
   ksorted[pos] = key;
 }
 
-// Lane-group width g (a power of two <= 32) for |Q| queries when every lane
-// holds two queries (a pass covers 2g of them): the width that leaves the
-// fewest idle query slots, ties going to the larger g.
-__device__ __forceinline__ int pick_group(int qn) {
-  int best = 32, waste = ((qn + 63) / 64) * 64 - qn;
-  for (int g = 16; g >= 1; g >>= 1) {
-    const int wst = ((qn + 2 * g - 1) / (2 * g)) * (2 * g) - qn;
-    if (wst < waste) { waste = wst; best = g; }
+// Lane-group width g (a power of two <= 32) for a run of |Q| queries and
+// `tot` references when every lane holds two queries: a pass covers 2g
+// queries and each lane walks tot / (2 * 32/g) reference pairs; a pass
+// also costs a fixed overhead (query set-up, reduction, atomics) worth
+// about kPassCost pair iterations.  Pick the g of least modelled cost.
+constexpr int kPassCost = 16;
+__device__ __forceinline__ int pick_group(int qn, int tot) {
+  const int pairs = (tot + 1) / 2;
+  int best = 32, cost = 1 << 30;
+  for (int g = 32; g >= 1; g >>= 1) {
+    const int passes = (qn + 2 * g - 1) / (2 * g);
+    const int iters = (pairs + (32 / g) - 1) / (32 / g);
+    const int c = passes * (iters + kPassCost);
+    if (c < cost) { cost = c; best = g; }
   }
   return best;
 }
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kT, 3) k_base(TreeView Q, TreeView R, const in
     const int hidx = key / Q.nn, q = key % Q.nn;
     const float c2 = c2v[hidx];
     const int qb = Q.beg[q], qn = Q.cnt[q];
-    const int g = pick_group(qn);
+    const int g = pick_group(qn, tot);
     const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
     // expansion center and the error test of the expanded form
     float mc[D];
