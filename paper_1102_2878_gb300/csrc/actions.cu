@@ -79,9 +79,7 @@ struct CenterHL {
   float hi, lo;
 };
 __device__ __forceinline__ CenterHL center_hl(const TreeView& T, int node, int k) {
-  const double c = center(T, node, k);
-  const float hi = (float)c;
-  return CenterHL{hi, (float)(c - (double)hi)};
+  return CenterHL{T.chi[(size_t)node * T.d + k], T.clo[(size_t)node * T.d + k]};
 }
 __device__ __forceinline__ float minus_center(float p, CenterHL c) { return (p - c.hi) - c.lo; }
 
@@ -424,8 +422,9 @@ __global__ void __launch_bounds__(kT) k_base_g(TreeView Q, TreeView R, const int
 // Scaled far-field moments M_alpha = m_alpha (2h^2)^(-|alpha|/2) for alpha < p
 // (zero elsewhere) into shared memory, float32.
 template <int D, int PM, int P>
-__device__ __forceinline__ void stage_moments(const double* __restrict__ m, const double* __restrict__ spow,
-                                              int p, float* Ms, int lane) {
+__device__ __forceinline__ void stage_moments(const float* __restrict__ mn, float ws, int p, float* Ms,
+                                              int lane) {
+  // M_alpha = m~_alpha (w s)^|alpha| for alpha < p, 0 elsewhere (float32)
   for (int idx = lane; idx < P; idx += 32) {
     int ab = 0;
     bool ok = true;
@@ -434,7 +433,7 @@ __device__ __forceinline__ void stage_moments(const double* __restrict__ m, cons
 #pragma unroll
       for (int k = D - 1; k >= 0; --k) { const int a = v % PM; v /= PM; ab += a; ok = ok && a < p; }
     }
-    Ms[idx] = ok ? (float)(m[idx] * spow[ab]) : 0.f;
+    Ms[idx] = ok ? mn[idx] * pow_int_f(ws, ab) : 0.f;
   }
 }
 
@@ -443,8 +442,7 @@ __device__ __forceinline__ void stage_moments(const double* __restrict__ m, cons
 template <int D>
 __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
                                                  const Action* __restrict__ list, int n,
-                                                 const double* __restrict__ hv,
-                                                 const double* __restrict__ spow,
+                                                 const float* __restrict__ sfv,
                                                  double* __restrict__ gacc) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
@@ -454,15 +452,13 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
   const int lane = threadIdx.x & 31;
   if (w >= n) return;
   const Action a = list[w];
-  const double h = hv[a.h];
-  const double s = 1.0 / sqrt(2.0 * h * h);
+  const float sf = sfv[a.h];
   float* Ms = sM[wib];
-  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, spow + (size_t)a.h * kPowTable, a.p, Ms, lane);
+  stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * sf, a.p, Ms, lane);
   __syncwarp();
   CenterHL cR[D];
 #pragma unroll
   for (int k = 0; k < D; ++k) cR[k] = center_hl(R, a.r, k);
-  const float sf = (float)s;
   const int qb = Q.beg[a.q], qn = Q.cnt[a.q];
   for (int qi = lane; qi < qn; qi += 32) {
     float qv[D];
@@ -496,7 +492,7 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
 template <int D>
 __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                               const int* __restrict__ ksorted, int n,
-                                              const double* __restrict__ hv,
+                                              const float* __restrict__ sfv,
                                               double* __restrict__ L, int* __restrict__ pused) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
@@ -529,14 +525,13 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int*
     int e = t + 1;
     while (e < m && __shfl_sync(0xffffffffu, my_key, e) == key) ++e;
     const int hidx = key / Q.nn, q = key % Q.nn;
-    const double h = hv[hidx];
-    const float sf = (float)(1.0 / sqrt(2.0 * h * h));
+    const float sf = sfv[hidx];
     CenterHL cQ[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, q, k);
-    double acc[S];
+    float accS[S], accC[S];
 #pragma unroll
-    for (int sl = 0; sl < S; ++sl) acc[sl] = 0.0;
+    for (int sl = 0; sl < S; ++sl) accS[sl] = accC[sl] = 0.f;
     int prun = 0;
     for (int u = t; u < e; ++u) {
       const int r = __shfl_sync(0xffffffffu, my_r, u);
@@ -571,7 +566,7 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int*
               for (int k = 1; k < D; ++k) tt *= sH[wib][jj][k][al[sl][k]];
               part += tt;
             }
-            acc[sl] += (double)part;
+            kahan_add(accS[sl], accC[sl], part);
           }
         }
         __syncwarp();
@@ -581,7 +576,8 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int*
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
       const int idx = lane + 32 * sl;
-      if (idx < P && acc[sl] != 0.0) atomicAdd(&L[hq * P + idx], acc[sl] * fsign[sl]);
+      const double v = (double)accS[sl] - (double)accC[sl];
+      if (idx < P && v != 0.0) atomicAdd(&L[hq * P + idx], v * fsign[sl]);
     }
     if (lane == 0) atomicMax(&pused[hq], prun);
     t = e;
@@ -595,7 +591,6 @@ __global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int*
 template <int D>
 __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action* __restrict__ list,
                                             int n, const double* __restrict__ hv,
-                                            const double* __restrict__ spow,
                                             double* __restrict__ L, int* __restrict__ pused) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
@@ -616,7 +611,7 @@ __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action
 #pragma unroll
     for (int e = 0; e < NH; ++e) sH[wib][lane][e] = (float)H[e];
   }
-  stage_moments<D, PM, P>(R.mom + (size_t)a.r * P, spow + (size_t)a.h * kPowTable, a.p, sM[wib], lane);
+  stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * (float)s, a.p, sM[wib], lane);
   __syncwarp();
   const size_t hq = (size_t)a.h * Q.nn + a.q;
 #pragma unroll
@@ -751,7 +746,7 @@ template <int D>
 __global__ void __launch_bounds__(kT) k_finalize(TreeView Q, const double* __restrict__ gacc,
                                                  const double* __restrict__ L,
                                                  const int* __restrict__ pused,
-                                                 const double* __restrict__ hv, int nh,
+                                                 const float* __restrict__ sfv, int nh,
                                                  double* __restrict__ G) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
@@ -766,8 +761,7 @@ __global__ void __launch_bounds__(kT) k_finalize(TreeView Q, const double* __res
     const double* Lq = L + hq * P;
     val += Lq[0];
     if (p > 1) {
-      const double h = hv[hidx];
-      const float sf = (float)(1.0 / sqrt(2.0 * h * h));
+      const float sf = sfv[hidx];
       float qv[D];
       load_point<D>(Q.pts + (size_t)i * Q.dp, qv);
       float X[D][PM];
@@ -806,7 +800,7 @@ __global__ void __launch_bounds__(kT) k_farfield_g(TreeView Q, TreeView R, const
   const Action a = list[w];
   const double h = hv[a.h];
   const float c2 = (float)(-kLog2e / (2.0 * h * h));
-  const float m0 = (float)R.mom[a.r];
+  const float m0 = R.mnorm[a.r];
   const int qb = Q.beg[a.q], qn = Q.cnt[a.q];
   for (int qi = lane; qi < qn; qi += 32) {
     float d2 = 0.f;
@@ -947,7 +941,7 @@ cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuff
   if (n <= 0) return cudaSuccess;
   const int g = warp_grid(n);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_farfield<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.spow, b.gacc));
+    DISPATCH_D(Q.d, k_farfield<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.sf, b.gacc));
   } else {
     k_farfield_g<<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc);
   }
@@ -965,7 +959,7 @@ cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers
     if (e != cudaSuccess) return e;
     const long warps = (n + kBaseChunk - 1) / kBaseChunk;
     const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, vsorted, ksorted, n, b.h, b.L, b.pused));
+    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, vsorted, ksorted, n, b.sf, b.L, b.pused));
   } else {
     k_local_g<<<warp_grid(n), kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
   }
@@ -978,7 +972,7 @@ cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& 
   if (n <= 0) return cudaSuccess;
   if (Q.d <= 5) {
     const int g = warp_grid(n);
-    DISPATCH_D(Q.d, k_f2l<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.spow, b.L, b.pused));
+    DISPATCH_D(Q.d, k_f2l<DD><<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused));
   } else {
     k_f2l_g<<<(n + kT - 1) / kT, kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
   }
@@ -1008,7 +1002,7 @@ cudaError_t launch_finalize(const TreeView& Q, const TravBuffers& b, double* G, 
   const long items = (long)b.nh * Q.n;
   const int g = (int)((items + kT - 1) / kT);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_finalize<DD><<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.h, b.nh, G));
+    DISPATCH_D(Q.d, k_finalize<DD><<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.sf, b.nh, G));
   } else {
     k_finalize_g<<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.nh, G);
   }

@@ -63,21 +63,21 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
                         const double* h_host, int nh, double eps_eff, TravBuffers* b) {
   cudaStream_t s = ctx->stream;
   const size_t nodes = (size_t)nh * qt->nn;
-  CK(ctx->hvals.ensure((4 + kPowTable) * nh * sizeof(double)));
+  CK(ctx->hvals.ensure(4 * (size_t)nh * sizeof(double)));
   CK(ctx->node_state.ensure(4 * nodes * sizeof(u64)));
   CK(ctx->lmom.ensure(nodes * qt->P * sizeof(double)));
   CK(ctx->pused.ensure(nodes * sizeof(int)));
   CK(ctx->gacc.ensure((size_t)nh * qt->n * sizeof(double)));
   CK(ctx->counters.ensure(sizeof(RoundCounters)));
   {
-    // layout: h | four float arrays packed in three double slots | power table
-    std::vector<double> hv((4 + kPowTable) * (size_t)nh);
+    // layout: h (double) | five float arrays inv_dn, inv_up, i2h_up, c2, sf
+    std::vector<double> hv(4 * (size_t)nh);
     float* fl = reinterpret_cast<float*>(hv.data() + (size_t)nh);
     float* inv_dn = fl;
     float* inv_up = fl + nh;
     float* i2h_up = fl + 2 * (size_t)nh;
     float* c2 = fl + 3 * (size_t)nh;
-    double* spow = hv.data() + 4 * (size_t)nh;
+    float* sfl = fl + 4 * (size_t)nh;
     for (int i = 0; i < nh; ++i) {
       hv[i] = h_host[i];
       const double inv = 1.0 / (2.0 * h_host[i] * h_host[i]);
@@ -85,9 +85,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
       inv_up[i] = std::nextafter((float)inv, INFINITY);
       i2h_up[i] = std::nextafter((float)(1.0 / (2.0 * h_host[i])), INFINITY);
       c2[i] = (float)(-kLog2e * inv);
-      const double sc = 1.0 / std::sqrt(2.0 * h_host[i] * h_host[i]);
-      double v = 1.0;
-      for (int k = 0; k < kPowTable; ++k, v *= sc) spow[(size_t)i * kPowTable + k] = v;
+      sfl[i] = (float)(1.0 / std::sqrt(2.0 * h_host[i] * h_host[i]));
     }
     CK(cudaMemcpyAsync(ctx->hvals.p, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));  // hv is a stack buffer
@@ -111,7 +109,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->inv2h2_up = fl + nh;
   b->inv_2h_up = fl + 2 * nh;
   b->c2 = fl + 3 * nh;
-  b->spow = ctx->hvals.as<double>() + 4 * nh;
+  b->sf = fl + 4 * nh;
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
@@ -326,6 +324,21 @@ dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream) {
     ctx->own_stream = true;
   }
   if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_counters, sizeof(RoundCounters));
+  if (e == cudaSuccess) {
+    // tree arenas: a pool of our own that keeps freed memory cached
+    ctx->tpool = std::make_shared<TreePool>();
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&ctx->tpool->pool, &props);
+    if (e == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(ctx->tpool->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    ctx->tpool->stream = ctx->stream;
+  }
   for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e != cudaSuccess) {
     dfgt_destroy(ctx);
@@ -353,8 +366,14 @@ void dfgt_destroy(dfgt_ctx* ctx) {
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,
-                    &ctx->bf_partials};
+                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes};
   for (DevBuf* b : bufs) b->release();
+  if (ctx->tpool) {
+    // trees that outlive the context return their arenas in default-stream order
+    std::lock_guard<std::mutex> g(ctx->tpool->m);
+    ctx->tpool->stream = nullptr;
+  }
+  ctx->tpool.reset();
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
   for (int i = 0; i < 16; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);

@@ -19,10 +19,6 @@ __host__ __device__ constexpr int pmax_of(int D) {
 }
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e <= 0 ? 1 : b * ipow_c(b, e - 1); }
 
-// Entries per bandwidth of the moment-scale table (2h^2)^(-k/2), k < 16;
-// the largest |alpha| is D (p_max - 1) <= 10.
-constexpr int kPowTable = 16;
-
 // Row stride of the permuted point copy: float2 rows for D<=2, float4-aligned otherwise.
 inline int padded_dim(int d) { return d <= 2 ? d : ((d + 3) & ~3); }
 
@@ -38,6 +34,10 @@ struct TreeView {
   const int* parent;   // [nn] parent node, -1 for the root
   const int* leaf_of;  // [n] leaf owning each permuted point
   const double* mom;   // [nn][P] raw moments sum (r-c)^alpha/alpha! about the box center
+  const float* chi;    // [nn][d] box center as a float pair chi + clo
+  const float* clo;
+  const float* whalf;  // [nn] largest half side w of the box (1 for a point)
+  const float* mnorm;  // [nn][P] normalised moments m_alpha / w^|alpha| (|m~| <= |R|)
   int n, d, dp, nn, pm, P;
 };
 

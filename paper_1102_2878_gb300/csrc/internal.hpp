@@ -1,6 +1,8 @@
 // internal.hpp -- host-side structures of the DFGT library (not part of the ABI).
 #pragma once
 
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -30,6 +32,33 @@ struct DevBuf {
   template <class T>
   T* as() const {
     return static_cast<T*>(p);
+  }
+};
+
+// Carves 256-byte aligned sub-arrays out of one allocation; with a null
+// base it only adds up the bytes a layout needs.
+struct Carver {
+  char* base = nullptr;
+  size_t off = 0;
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Stream-ordered memory pool that tree arenas come from.  Shared by the
+// context that creates it and every tree built on that context, so it
+// lives until the last of them is gone; freed arenas stay cached in the
+// pool for the next build instead of going back to the driver.
+struct TreePool {
+  cudaMemPool_t pool = nullptr;
+  std::mutex m;
+  cudaStream_t stream = nullptr;  // the owning context's stream while it lives
+  ~TreePool() {
+    if (pool) cudaMemPoolDestroy(pool);
   }
 };
 
@@ -63,6 +92,9 @@ struct dfgt_ctx {
   DevBuf gacc;           // double [nh][nq]
   DevBuf io_q, io_r, io_g;  // dfgt_kde_host staging
   DevBuf bf_partials;       // brute-force slice partials
+  DevBuf bscratch;          // tree-build per-point scratch
+  DevBuf bnodes;            // tree-build node arrays (copied into the tree's arena)
+  std::shared_ptr<TreePool> tpool;
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned
@@ -77,6 +109,8 @@ struct dfgt_tree {
   double eps_fp = 2e-5;
   int nn = 0, nleaves = 0, depth = 0;
   std::vector<int> lvl_off;  // nodes of level k are [lvl_off[k], lvl_off[k+1])
+  std::shared_ptr<TreePool> tpool;
+  void* arena = nullptr;     // one pool allocation holding every array below
   float* pts = nullptr;
   int* perm = nullptr;
   float* lo = nullptr;
@@ -87,10 +121,15 @@ struct dfgt_tree {
   int* parent = nullptr;
   int* leaf_of = nullptr;
   double* mom = nullptr;
+  float* chi = nullptr;
+  float* clo = nullptr;
+  float* whalf = nullptr;
+  float* mnorm = nullptr;
   dfgt::TreeView view() const {
     dfgt::TreeView v;
     v.pts = pts; v.perm = perm; v.lo = lo; v.hi = hi; v.beg = beg; v.cnt = cnt;
     v.left = left; v.parent = parent; v.leaf_of = leaf_of; v.mom = mom;
+    v.chi = chi; v.clo = clo; v.whalf = whalf; v.mnorm = mnorm;
     v.n = (int)n; v.d = d; v.dp = dp; v.nn = nn; v.pm = pm; v.P = P;
     return v;
   }
@@ -132,7 +171,7 @@ struct TravBuffers {
   const float* inv2h2_up;  // [nh] 1/(2h^2) rounded up
   const float* inv_2h_up;  // [nh] 1/(2h) rounded up
   const float* c2;       // [nh] -log2(e)/(2h^2) as float, the exp2 scale of exact sums
-  const double* spow;    // [nh][kPowTable] (2h^2)^(-k/2), the moment scales
+  const float* sf;       // [nh] 1/sqrt(2h^2) as float, the expansion scale
   float* ku;        // [frontier] lower bound on K(d^u) of each pending pair
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums

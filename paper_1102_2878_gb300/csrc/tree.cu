@@ -352,6 +352,39 @@ __global__ void k_f2f_level(TreeView t, int a, int e, double* __restrict__ mom) 
   }
 }
 
+// Per-node float data for the float32 kernels: the box center as a float
+// pair (hi + lo, so that differences with points stay accurate), the
+// largest half side w and the moments normalised by w, m_alpha / w^|alpha|,
+// which are bounded by |R| (each |r_k - c_k| <= w), so the scaled moments
+// M_alpha = m~_alpha (w s)^|alpha| are formed in float32 without range
+// problems.  Computed in float64 once per tree.
+__global__ void k_node_float_data(TreeView t, int pm, float* __restrict__ chi, float* __restrict__ clo,
+                                  float* __restrict__ whalf, float* __restrict__ mnorm) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= t.nn) return;
+  const int d = t.d;
+  double w = 0.0;
+  for (int k = 0; k < d; ++k) {
+    const double lo = t.lo[(size_t)j * d + k], hi = t.hi[(size_t)j * d + k];
+    const double c = 0.5 * (lo + hi);
+    const float h = (float)c;
+    chi[(size_t)j * d + k] = h;
+    clo[(size_t)j * d + k] = (float)(c - (double)h);
+    w = fmax(w, 0.5 * (hi - lo));
+  }
+  float wf = (float)w;
+  if (!(wf > 0.f)) wf = 1.f;
+  whalf[j] = wf;
+  const double iw = 1.0 / (double)wf;
+  for (int idx = 0; idx < t.P; ++idx) {
+    int v = idx, ab = 0;
+    for (int k = 0; k < d; ++k) { ab += v % pm; v /= pm; }
+    double sc = 1.0;
+    for (int e = 0; e < ab; ++e) sc *= iw;
+    mnorm[(size_t)j * t.P + idx] = (float)(t.mom[(size_t)j * t.P + idx] * sc);
+  }
+}
+
 // D >= 6: p_max = 1, the only moment is m_0 = |R|.
 __global__ void k_count_moments(TreeView t, double* __restrict__ mom) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,30 +406,69 @@ cudaError_t moments_d(dfgt_tree* t, cudaStream_t s, long long* launches) {
   return cudaGetLastError();
 }
 
-struct Grow {
-  // grow a device array keeping its first `keep` elements
-  template <class T>
-  static cudaError_t arr(T** p, size_t keep, size_t newcap, cudaStream_t s) {
-    T* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, newcap * sizeof(T));
-    if (e != cudaSuccess) return e;
-    if (*p && keep) {
-      e = cudaMemcpyAsync(q, *p, keep * sizeof(T), cudaMemcpyDeviceToDevice, s);
-      if (e != cudaSuccess) { cudaFree(q); return e; }
-      cudaStreamSynchronize(s);
-    }
-    if (*p) cudaFree(*p);
-    *p = q;
-    return cudaSuccess;
+// Node arrays of a build in progress, carved from one buffer with room
+// for `cap` nodes.
+struct NodeArrays {
+  float *lo, *hi;
+  int *beg, *cnt, *left, *parent;
+  static size_t bytes(size_t cap, int d) {
+    Carver c;
+    NodeArrays a;
+    a.carve(c, cap, d);
+    return c.off;
+  }
+  void carve(Carver& c, size_t cap, int d) {
+    lo = c.take<float>(cap * d);
+    hi = c.take<float>(cap * d);
+    beg = c.take<int>(cap);
+    cnt = c.take<int>(cap);
+    left = c.take<int>(cap);
+    parent = c.take<int>(cap);
+  }
+  void copy_to(float* lo2, float* hi2, int* beg2, int* cnt2, int* left2, int* parent2, size_t keep,
+               int d, cudaStream_t s, cudaError_t* e) const {
+    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+    if (*e == cudaSuccess) *e = cudaMemcpyAsync(lo2, lo, keep * d * sizeof(float), k, s);
+    if (*e == cudaSuccess) *e = cudaMemcpyAsync(hi2, hi, keep * d * sizeof(float), k, s);
+    if (*e == cudaSuccess) *e = cudaMemcpyAsync(beg2, beg, keep * sizeof(int), k, s);
+    if (*e == cudaSuccess) *e = cudaMemcpyAsync(cnt2, cnt, keep * sizeof(int), k, s);
+    if (*e == cudaSuccess) *e = cudaMemcpyAsync(left2, left, keep * sizeof(int), k, s);
+    if (*e == cudaSuccess) *e = cudaMemcpyAsync(parent2, parent, keep * sizeof(int), k, s);
   }
 };
+
+// Grow the context's node buffer to `cap` nodes keeping the first `keep`.
+cudaError_t grow_nodes(DevBuf& buf, NodeArrays& na, size_t keep, size_t cap, int d, cudaStream_t s) {
+  DevBuf nb;
+  cudaError_t e = nb.ensure(NodeArrays::bytes(cap, d));
+  if (e != cudaSuccess) return e;
+  Carver c{nb.as<char>()};
+  NodeArrays nn;
+  nn.carve(c, cap, d);
+  na.copy_to(nn.lo, nn.hi, nn.beg, nn.cnt, nn.left, nn.parent, keep, d, s, &e);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    nb.release();
+    return e;
+  }
+  buf.release();
+  buf = nb;
+  na = nn;
+  return cudaSuccess;
+}
 
 }  // namespace
 
 void free_tree(dfgt_tree* t) {
-  cudaFree(t->pts); cudaFree(t->perm); cudaFree(t->lo); cudaFree(t->hi);
-  cudaFree(t->beg); cudaFree(t->cnt); cudaFree(t->left); cudaFree(t->parent);
-  cudaFree(t->leaf_of); cudaFree(t->mom);
+  if (t->arena) {
+    // every call on the tree has completed (calls return after their work),
+    // so the arena can go back to the pool in any stream's order
+    std::lock_guard<std::mutex> g(t->tpool->m);
+    cudaFreeAsync(t->arena, t->tpool->stream);
+  }
+  t->arena = nullptr;
+  t->tpool.reset();
+  t->chi = t->clo = t->whalf = t->mnorm = nullptr;
   t->pts = nullptr; t->perm = nullptr; t->lo = t->hi = nullptr;
   t->beg = t->cnt = t->left = t->parent = t->leaf_of = nullptr; t->mom = nullptr;
 }
@@ -429,55 +501,65 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   }
   t->lvl_off.assign(1, 0);
 
-  // level-build scratch: two point buffers, per-point node ids, flags,
-  // prefix sums, per-level node temporaries
-  float* pbuf[2] = {nullptr, nullptr};
-  int* perm2[2] = {nullptr, nullptr};
-  int* pnode[2] = {nullptr, nullptr};
-  int *flag = nullptr, *leftpos = nullptr, *want = nullptr, *sd = nullptr, *split = nullptr,
-      *soff = nullptr, *nleft = nullptr, *status = nullptr;
-  float* sc = nullptr;
+  // level-build scratch from the context: two point buffers, per-point node
+  // ids, flags, prefix sums, per-level node temporaries
+  float* pbuf[2];
+  int* perm2[2];
+  int* pnode[2];
+  int *flag, *leftpos, *want, *sd, *split, *soff, *nleft, *status;
+  float* sc;
+  NodeArrays na;
   size_t cap = 0;
   int cur = 0, a = 0, e = 1, level = 0;
   int h_status = 0;
   dfgt_status rc = DFGT_ECUDA;
 
   const size_t np = (size_t)n;
-  TRY(cudaMalloc(&pbuf[0], np * t->dp * sizeof(float)));
-  TRY(cudaMalloc(&pbuf[1], np * t->dp * sizeof(float)));
-  TRY(cudaMalloc(&perm2[0], np * sizeof(int)));
-  TRY(cudaMalloc(&perm2[1], np * sizeof(int)));
-  TRY(cudaMalloc(&pnode[0], np * sizeof(int)));
-  TRY(cudaMalloc(&pnode[1], np * sizeof(int)));
-  TRY(cudaMalloc(&flag, np * sizeof(int)));
-  TRY(cudaMalloc(&leftpos, (np + 1) * sizeof(int)));
-  TRY(cudaMalloc(&want, (np + 1) * sizeof(int)));
-  TRY(cudaMalloc(&sd, (np + 1) * sizeof(int)));
-  TRY(cudaMalloc(&sc, (np + 1) * sizeof(float)));
-  TRY(cudaMalloc(&split, (np + 1) * sizeof(int)));
-  TRY(cudaMalloc(&soff, (np + 2) * sizeof(int)));
-  TRY(cudaMalloc(&nleft, (np + 1) * sizeof(int)));
-  TRY(cudaMalloc(&status, sizeof(int)));
+  Carver cv;
+  for (int pass = 0; pass < 2; ++pass) {
+    cv.off = 0;
+    pbuf[0] = cv.take<float>(np * t->dp);
+    pbuf[1] = cv.take<float>(np * t->dp);
+    perm2[0] = cv.take<int>(np);
+    perm2[1] = cv.take<int>(np);
+    pnode[0] = cv.take<int>(np);
+    pnode[1] = cv.take<int>(np);
+    flag = cv.take<int>(np);
+    leftpos = cv.take<int>(np + 1);
+    want = cv.take<int>(np + 1);
+    sd = cv.take<int>(np + 1);
+    sc = cv.take<float>(np + 1);
+    split = cv.take<int>(np + 1);
+    soff = cv.take<int>(np + 2);
+    nleft = cv.take<int>(np + 1);
+    status = cv.take<int>(1);
+    if (pass == 0) {
+      TRY(ctx->bscratch.ensure(cv.off));
+      cv.base = ctx->bscratch.as<char>();
+    }
+  }
   TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
 
   cap = std::max<size_t>(64, 4 * np / std::max(1, t->leaf) + 16);
-  TRY(cudaMalloc(&t->lo, cap * d * sizeof(float)));
-  TRY(cudaMalloc(&t->hi, cap * d * sizeof(float)));
-  TRY(cudaMalloc(&t->beg, cap * sizeof(int)));
-  TRY(cudaMalloc(&t->cnt, cap * sizeof(int)));
-  TRY(cudaMalloc(&t->left, cap * sizeof(int)));
-  TRY(cudaMalloc(&t->parent, cap * sizeof(int)));
+  {
+    TRY(ctx->bnodes.ensure(NodeArrays::bytes(cap, d)));
+    // use all the room the buffer has
+    const size_t fit = (ctx->bnodes.bytes - 6 * 256) / (8 * (size_t)d + 16);
+    if (fit > cap && NodeArrays::bytes(fit, d) <= ctx->bnodes.bytes) cap = fit;
+    Carver c{ctx->bnodes.as<char>()};
+    na.carve(c, cap, d);
+  }
 
   k_pad_points<<<(n + kT - 1) / kT, kT, 0, s>>>(pts_dev, n, d, t->dp, pbuf[0], perm2[0], pnode[0], status);
   ++*L;
   {
     const int zero = 0, minus1 = -1;
-    TRY(cudaMemcpyAsync(t->beg, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(t->cnt, &n, sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(t->parent, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(t->left, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(na.beg, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(na.cnt, &n, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(na.parent, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaMemcpyAsync(na.left, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
   }
-  k_init_nodes<<<1, 32, 0, s>>>(0, 1, d, t->lo, t->hi);
+  k_init_nodes<<<1, 32, 0, s>>>(0, 1, d, na.lo, na.hi);
   ++*L;
   TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
   TRY(cudaStreamSynchronize(s));
@@ -490,13 +572,13 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   for (level = 0; level < 128; ++level) {
     const int nl = e - a;
     const int gp = (n + kT - 1) / kT, gn = (nl + kT - 1) / kT;
-    k_bbox<<<gp, kT, 0, s>>>(pbuf[cur], n, d, t->dp, pnode[cur], t->lo, t->hi);
-    k_split_decide<<<gn, kT, 0, s>>>(a, e, d, t->leaf, t->cnt, t->lo, t->hi, want, sd, sc);
+    k_bbox<<<gp, kT, 0, s>>>(pbuf[cur], n, d, t->dp, pnode[cur], na.lo, na.hi);
+    k_split_decide<<<gn, kT, 0, s>>>(a, e, d, t->leaf, na.cnt, na.lo, na.hi, want, sd, sc);
     k_flag_left<<<gp, kT, 0, s>>>(pbuf[cur], n, t->dp, a, pnode[cur], want, sd, sc, flag);
     *L += 3;
     TRY(cudaGetLastError());
     TRY(scan_exclusive(flag, leftpos, n, ctx->scan_tmp, s, L));
-    k_node_finalize<<<gn, kT, 0, s>>>(a, e, t->beg, t->cnt, want, leftpos, split, nleft);
+    k_node_finalize<<<gn, kT, 0, s>>>(a, e, na.beg, na.cnt, want, leftpos, split, nleft);
     ++*L;
     TRY(cudaGetLastError());
     TRY(scan_exclusive(split, soff, nl, ctx->scan_tmp, s, L));
@@ -505,19 +587,14 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
     TRY(cudaStreamSynchronize(s));
     const size_t need = (size_t)e + 2 * (size_t)nsplit;
     if (need > cap) {
-      size_t nc = std::max(need, cap * 2);
-      TRY(Grow::arr(&t->lo, (size_t)e * d, nc * d, s));
-      TRY(Grow::arr(&t->hi, (size_t)e * d, nc * d, s));
-      TRY(Grow::arr(&t->beg, (size_t)e, nc, s));
-      TRY(Grow::arr(&t->cnt, (size_t)e, nc, s));
-      TRY(Grow::arr(&t->left, (size_t)e, nc, s));
-      TRY(Grow::arr(&t->parent, (size_t)e, nc, s));
+      const size_t nc = std::max(need, cap * 2);
+      TRY(grow_nodes(ctx->bnodes, na, (size_t)e, nc, d, s));
       cap = nc;
     }
-    k_make_children<<<gn, kT, 0, s>>>(a, e, level, d, split, soff, nleft, t->beg, t->cnt,
-                                      t->left, t->parent, t->lo, t->hi);
+    k_make_children<<<gn, kT, 0, s>>>(a, e, level, d, split, soff, nleft, na.beg, na.cnt,
+                                      na.left, na.parent, na.lo, na.hi);
     k_scatter<<<gp, kT, 0, s>>>(n, t->dp, a, pbuf[cur], perm2[cur], pnode[cur], flag, leftpos,
-                                t->beg, t->left, nleft, pbuf[cur ^ 1], perm2[cur ^ 1], pnode[cur ^ 1]);
+                                na.beg, na.left, nleft, pbuf[cur ^ 1], perm2[cur ^ 1], pnode[cur ^ 1]);
     *L += 2;
     TRY(cudaGetLastError());
     cur ^= 1;
@@ -538,12 +615,37 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
     rc = DFGT_ECAPACITY;
     goto fail;
   }
-  t->pts = pbuf[cur];
-  pbuf[cur] = nullptr;
-  t->perm = perm2[cur];
-  perm2[cur] = nullptr;
-  TRY(cudaMalloc(&t->leaf_of, np * sizeof(int)));
-  TRY(cudaMalloc(&t->mom, (size_t)t->nn * t->P * sizeof(double)));
+  {
+    // the tree's arena: one allocation from the context's pool
+    const size_t nn = (size_t)t->nn, P = (size_t)t->P;
+    Carver ca;
+    for (int pass = 0; pass < 2; ++pass) {
+      ca.off = 0;
+      t->pts = ca.take<float>(np * t->dp);
+      t->perm = ca.take<int>(np);
+      t->leaf_of = ca.take<int>(np);
+      t->lo = ca.take<float>(nn * d);
+      t->hi = ca.take<float>(nn * d);
+      t->beg = ca.take<int>(nn);
+      t->cnt = ca.take<int>(nn);
+      t->left = ca.take<int>(nn);
+      t->parent = ca.take<int>(nn);
+      t->mom = ca.take<double>(nn * P);
+      t->chi = ca.take<float>(nn * d);
+      t->clo = ca.take<float>(nn * d);
+      t->whalf = ca.take<float>(nn);
+      t->mnorm = ca.take<float>(nn * P);
+      if (pass == 0) {
+        t->tpool = ctx->tpool;
+        TRY(cudaMallocFromPoolAsync(&t->arena, ca.off, ctx->tpool->pool, s));
+        ca.base = static_cast<char*>(t->arena);
+      }
+    }
+    cudaError_t ce = cudaMemcpyAsync(t->pts, pbuf[cur], np * t->dp * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->perm, perm2[cur], np * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    na.copy_to(t->lo, t->hi, t->beg, t->cnt, t->left, t->parent, nn, d, s, &ce);
+    TRY(ce);
+  }
   k_leaf_of<<<(int)(((size_t)t->nn * 32 + kT - 1) / kT), kT, 0, s>>>(t->nn, t->beg, t->cnt, t->left, t->leaf_of);
   ++*L;
   switch (d) {
@@ -557,6 +659,9 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       ++*L;
       TRY(cudaGetLastError());
   }
+  k_node_float_data<<<(t->nn + kT - 1) / kT, kT, 0, s>>>(t->view(), t->pm, t->chi, t->clo, t->whalf, t->mnorm);
+  ++*L;
+  TRY(cudaGetLastError());
   {
     // count leaves on the host side from the level structure
     std::vector<int> left_h(t->nn);
@@ -566,10 +671,10 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   }
   rc = DFGT_OK;
 fail:
-  cudaFree(pbuf[0]); cudaFree(pbuf[1]); cudaFree(perm2[0]); cudaFree(perm2[1]);
-  cudaFree(pnode[0]); cudaFree(pnode[1]); cudaFree(flag); cudaFree(leftpos); cudaFree(want);
-  cudaFree(sd); cudaFree(sc); cudaFree(split); cudaFree(soff); cudaFree(nleft); cudaFree(status);
-  if (rc != DFGT_OK) free_tree(t);
+  if (rc != DFGT_OK) {
+    cudaStreamSynchronize(s);
+    free_tree(t);
+  }
   return rc;
 }
 

@@ -82,3 +82,48 @@ def test_raw_moments_match_oracle(dev, orc, D):
         want = orc.farfield_moments(pts, c, h, pm)
         scale = orc.farfield_moments(np.abs(pts - c) + c, c, h, pm)
         assert np.all(np.abs(t["moments"][j] - want) <= 1e-10 * scale + 1e-300), j
+
+
+def test_node_buffer_growth(orc):
+    # points 1.5^-k: every midpoint split peels off one or two points, so the
+    # tree has far more nodes than the 4n/leaf + 16 first reserved and the
+    # build's node buffer grows (a fresh context starts with none)
+    ctx = dfgt.Context(0)
+    x = (1.5 ** -np.arange(200, dtype=np.float64)).astype(np.float32)[:, None]
+    tree = dfgt.Tree(ctx, to_cuda(x), leaf_size=8)
+    t = tree.export()
+    assert t["info"]["n_nodes"] > 4 * 200 // 8 + 16
+    check_tree(x, t, 8)
+    hs = np.array([0.01, 0.3])
+    G, _ = dfgt.kde_sum(ctx, tree, tree, hs, 1e-3)
+    G = G.cpu().numpy()
+    for i, h in enumerate(hs):
+        ref = orc.naive_kde(x.astype(np.float64), x.astype(np.float64), h)
+        assert np.all(np.abs(G[i] - ref) <= 1e-3 * ref)
+
+
+def test_tree_arenas_reused():
+    # trees come from one pool per context: a freed tree's memory serves the
+    # next build, and live trees are never disturbed by it
+    ctx = dfgt.Context(0)
+    xa = datagen.isotropic_mixture(5000, 3, 5, 0.05, seed=1)
+    a = dfgt.Tree(ctx, to_cuda(xa), leaf_size=16)
+    ea = a.export()
+    for k, n in enumerate([3000, 7000, 1000, 7000]):
+        x = datagen.isotropic_mixture(n, 3, 5, 0.05, seed=10 + k)
+        b = dfgt.Tree(ctx, to_cuda(x), leaf_size=16)
+        check_tree(x, b.export(), 16)
+        b.close()
+    ea2 = a.export()
+    for key in ("perm", "lo", "hi", "begin", "count", "left", "moments"):
+        assert np.array_equal(ea[key], ea2[key]), key
+
+
+def test_tree_outlives_context():
+    ctx = dfgt.Context(0)
+    x = datagen.isotropic_mixture(2000, 2, 3, 0.1, seed=5)
+    t = dfgt.Tree(ctx, to_cuda(x), leaf_size=16)
+    ctx.close()
+    t.close()  # the arena goes back to the pool, which then goes away
+    ctx2 = dfgt.Context(0)
+    check_tree(x, dfgt.Tree(ctx2, to_cuda(x), leaf_size=16).export(), 16)
