@@ -165,6 +165,18 @@ __device__ __forceinline__ int pick_group(int qn, int tot) {
   return best;
 }
 
+// Binomial coefficients C(b, a), b, a < 8.
+__constant__ float c_binom[8][8] = {
+    {1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {1.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {1.0f, 2.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {1.0f, 3.0f, 3.0f, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f},
+    {1.0f, 4.0f, 6.0f, 4.0f, 1.0f, 0.0f, 0.0f, 0.0f},
+    {1.0f, 5.0f, 10.0f, 10.0f, 5.0f, 1.0f, 0.0f, 0.0f},
+    {1.0f, 6.0f, 15.0f, 20.0f, 15.0f, 6.0f, 1.0f, 0.0f},
+    {1.0f, 7.0f, 21.0f, 35.0f, 35.0f, 21.0f, 7.0f, 1.0f}};
+__device__ __forceinline__ float binom_f(int b, int a) { return c_binom[b][a]; }
+
 // Kahan step of a float32 running sum.
 __device__ __forceinline__ void kahan_add(float& S, float& C, float v) {
   const float y = v - C;
@@ -659,132 +671,149 @@ __global__ void k_prune_apply(TreeView Q, TreeView R, const Pair* __restrict__ l
   atomicMax(&pused[hq], 1);
 }
 
-// ------------------------------------------------------- local to local
-// TransLocalToLocal (Lemma 3.6, Eq. local_to_local_translation) from every
-// node of one level to both children, order p = highest order used at the
-// node: L_alpha(c') += sum_{alpha<=beta<p} beta!/(alpha!(beta-alpha)!) L_beta(c) ((c'-c)/sqrt(2h^2))^{beta-alpha}.
-// The binomial coefficient and the power both factor over dimensions, so
-// the shift is applied as D one-dimensional shifts (D p^D p operations
-// instead of p^{2D}), in float64, in shared memory.  One warp per (node,
-// bandwidth); a child has one parent, so its coefficients are updated
-// without atomics.
+// ---------------------------------------------------------------- post
+// DFGTPost, fused.  The paper shifts every local expansion down the query
+// tree with TransLocalToLocal (Lemma 3.6) and reads the leaves out with
+// EvaluateLocalExpansion.  Re-centering a polynomial is exact, so shifting
+// each expansion of a leaf's ancestors straight to the leaf's center gives
+// the same polynomial as the level-by-level pass; one warp per leaf does
+// that for every bandwidth, sums the shifted coefficients (Kahan-
+// compensated float32; the constant term in float64), evaluates the sum
+// at the leaf's points and adds the exact and far-field parts, writing G
+// in the caller's query order.  One launch instead of one per level.
+//
+// Shift from center c to c' along one dimension, d = (c' - c)/sqrt(2h^2):
+// L'_a = sum_{a<=b<p} C(b, a) d^{b-a} L_b; the D dimensions are applied one
+// after the other (D p^D p operations).  Every shifted coefficient is a sum
+// of terms whose absolute values add up, at a point x of the leaf, to at
+// most sum_alpha |L_alpha| prod_k (w_k s)^alpha_k with w the half sides of
+// the ancestor's box (|x - c'| + |c' - c| <= w per dimension for nested
+// boxes), the same quantity that bounds the expansion's own evaluation; the
+// float32 rounding of a shift is at most 6 p D u times it (the rounded
+// d carries 4u, its powers up to 4(p-1)u, Horner's rule (2p-1)u per
+// dimension), which the rounding allowance of the truncation bounds
+// includes.
+constexpr int kMaxDepth = 128;
+
 template <int D>
-__global__ void __launch_bounds__(kT) k_l2l(TreeView Q, double* __restrict__ L,
-                                            int* __restrict__ pused, const double* __restrict__ hv,
-                                            int nh, int a, int e) {
+__global__ void __launch_bounds__(kT) k_post(TreeView Q, const int* __restrict__ leaves, int nleaves,
+                                             const double* __restrict__ gacc,
+                                             const double* __restrict__ L,
+                                             const int* __restrict__ pused,
+                                             const float* __restrict__ sfv, int nh,
+                                             double* __restrict__ G) {
   constexpr int PM = pmax_of(D);
   constexpr int P = ipow_c(PM, D);
-  __shared__ double sL[kWarpsPerBlock][2][P];
-  __shared__ double sC[PM][PM];  // binomial coefficients C(b, a)
-  if (threadIdx.x < PM * PM) {
-    const int bb = threadIdx.x / PM, aa = threadIdx.x % PM;
-    sC[bb][aa] = aa <= bb ? fact_d(bb) / (fact_d(aa) * fact_d(bb - aa)) : 0.0;
+  constexpr int S = (P + 31) / 32;
+  __shared__ int sPath[kWarpsPerBlock][kMaxDepth];
+  __shared__ float sT[kWarpsPerBlock][2][P];
+  __shared__ float sA[kWarpsPerBlock][P];
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = blockIdx.x * kWarpsPerBlock + wib;
+  if (li >= nleaves) return;
+  const int leaf = leaves[li];
+  int len = 0;
+  if (lane == 0) {
+    for (int v = leaf; v >= 0 && len < kMaxDepth; v = Q.parent[v]) sPath[wib][len++] = v;
   }
-  __syncthreads();
-  const int wib = threadIdx.x >> 5;
-  const int w = blockIdx.x * kWarpsPerBlock + wib;
-  const int lane = threadIdx.x & 31;
-  const int nl = e - a;
-  if (w >= nl * nh) return;
-  const int node = a + w % nl, hidx = w / nl;
-  const int cl = Q.left[node];
-  if (cl < 0) return;
-  const size_t hq = (size_t)hidx * Q.nn + node;
-  const int p = pused[hq];
-  if (p == 0) return;
-  const double* Lp = L + hq * P;
-  if (p == 1) {  // only the constant term (prune values): it shifts unchanged
-    if (lane < 2) {
-      const size_t hc = (size_t)hidx * Q.nn + cl + lane;
-      L[hc * P] += Lp[0];
-      if (pused[hc] < 1) pused[hc] = 1;
-    }
-    return;
-  }
-  const double h = hv[hidx];
-  const double s = 1.0 / sqrt(2.0 * h * h);
-  for (int ch = 0; ch < 2; ++ch) {
-    const int c = cl + ch;
-    const size_t hc = (size_t)hidx * Q.nn + c;
-    for (int idx = lane; idx < P; idx += 32) sL[wib][0][idx] = Lp[idx];
-    __syncwarp();
-    int cur = 0;
+  len = __shfl_sync(0xffffffffu, len, 0);
+  __syncwarp();
+  CenterHL cl[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      const double x = (center(Q, c, k) - center(Q, node, k)) * s;
-      constexpr int dummy = 0;
-      (void)dummy;
-      int stride = 1;
-      for (int j = D - 1; j > k; --j) stride *= PM;
-      for (int idx = lane; idx < P; idx += 32) {
-        const int ak = (idx / stride) % PM;
-        double acc = 0.0;
-        if (ak < p) {
-          double xp = 1.0;
-          for (int bk = ak; bk < p; ++bk) {
-            acc += sC[bk][ak] * xp * sL[wib][cur][idx + (bk - ak) * stride];
-            xp *= x;
+  for (int k = 0; k < D; ++k) cl[k] = center_hl(Q, leaf, k);
+  const int qb = Q.beg[leaf], qn = Q.cnt[leaf];
+  for (int hidx = 0; hidx < nh; ++hidx) {
+    const float sf = sfv[hidx];
+    float accS[S], accC[S];
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) accS[sl] = accC[sl] = 0.f;
+    double c0 = 0.0;  // constant term, the same in every lane
+    int pa = 0;       // highest order on the path
+    for (int i0 = 0; i0 < len; i0 += 32) {
+      const int node = i0 + lane < len ? sPath[wib][i0 + lane] : -1;
+      const int pu = node >= 0 ? pused[(size_t)hidx * Q.nn + node] : 0;
+      unsigned m = __ballot_sync(0xffffffffu, pu > 0);
+      while (m) {
+        const int bl = __ffs(m) - 1;
+        m &= m - 1;
+        const int j = __shfl_sync(0xffffffffu, node, bl);
+        const int pj = __shfl_sync(0xffffffffu, pu, bl);
+        const double* Lj = L + ((size_t)hidx * Q.nn + j) * P;
+        c0 += Lj[0];
+        pa = max(pa, pj);
+        if (pj == 1) continue;  // a constant shifts unchanged
+        // the non-constant part, shifted from c_j to the leaf's center
+        for (int idx = lane; idx < P; idx += 32) sT[wib][0][idx] = idx == 0 ? 0.f : (float)Lj[idx];
+        __syncwarp();
+        int cur = 0;
+        if (j != leaf) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const CenterHL cj = center_hl(Q, j, k);
+            const float dk = ((cl[k].hi - cj.hi) + (cl[k].lo - cj.lo)) * sf;
+            const int stride = ipow_c(PM, D - 1 - k);
+            for (int idx = lane; idx < P; idx += 32) {
+              const int ak = (idx / stride) % PM;
+              float acc = 0.f;
+              if (ak < pj) {
+                // sum_{b=ak}^{pj-1} C(b, ak) d^(b-ak) L_b, Horner in d
+                for (int bk = pj - 1; bk >= ak; --bk)
+                  acc = fmaf(acc, dk, binom_f(bk, ak) * sT[wib][cur][idx + (bk - ak) * stride]);
+              }
+              sT[wib][cur ^ 1][idx] = acc;
+            }
+            __syncwarp();
+            cur ^= 1;
           }
         }
-        sL[wib][cur ^ 1][idx] = acc;
+#pragma unroll
+        for (int sl = 0; sl < S; ++sl) {
+          const int idx = lane + 32 * sl;
+          if (idx < P) kahan_add(accS[sl], accC[sl], sT[wib][cur][idx]);
+        }
+        __syncwarp();
       }
+    }
+    // coefficients of the summed expansion at the leaf's center
+    double cst = c0;
+    if (pa > 1) {
+#pragma unroll
+      for (int sl = 0; sl < S; ++sl) {
+        const int idx = lane + 32 * sl;
+        if (idx < P) sA[wib][idx] = idx == 0 ? 0.f : accS[sl] - accC[sl];
+      }
+      cst += (double)__shfl_sync(0xffffffffu, accS[0] - accC[0], 0);
       __syncwarp();
-      cur ^= 1;
     }
-    for (int idx = lane; idx < P; idx += 32) L[hc * P + idx] += sL[wib][cur][idx];
+    for (int pi = lane; pi < qn; pi += 32) {
+      const int i = qb + pi;
+      double val = gacc[(size_t)hidx * Q.n + i] + cst;
+      if (pa > 1) {
+        float qv[D];
+        load_point<D>(Q.pts + (size_t)i * Q.dp, qv);
+        float X[D][PM];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float x = minus_center(qv[k], cl[k]) * sf;
+          float v = 1.f;
+#pragma unroll
+          for (int e = 0; e < PM; ++e) { X[k][e] = v; v *= x; }
+        }
+        float acc = 0.f;
+#pragma unroll
+        for (int idx = 1; idx < P; ++idx) {
+          if (!below_c<D, PM>(idx, pa)) continue;
+          float term = sA[wib][idx];
+#pragma unroll
+          for (int k = 0; k < D; ++k) term *= X[k][digit_c<D, PM>(idx, k)];
+          acc += term;
+        }
+        val += (double)acc;
+      }
+      G[(size_t)hidx * Q.n + Q.perm[i]] = val;
+    }
     __syncwarp();
-    if (lane == 0 && pused[hc] < p) pused[hc] = p;
   }
-}
-
-// ------------------------------------------------------------ finalise
-// Leaf read-out (EvaluateLocalExpansion) and the final sum of DFGTPost:
-// G~(q) = exact + far-field parts + sum_{beta<p} L_beta ((q - Q.c)/sqrt(2h^2))^beta,
-// written to the caller's query order.  The constant term is added in
-// float64, the rest of the polynomial is evaluated in float32.
-template <int D>
-__global__ void __launch_bounds__(kT) k_finalize(TreeView Q, const double* __restrict__ gacc,
-                                                 const double* __restrict__ L,
-                                                 const int* __restrict__ pused,
-                                                 const float* __restrict__ sfv, int nh,
-                                                 double* __restrict__ G) {
-  constexpr int PM = pmax_of(D);
-  constexpr int P = ipow_c(PM, D);
-  const long t = (long)blockIdx.x * kT + threadIdx.x;
-  if (t >= (long)nh * Q.n) return;
-  const int hidx = (int)(t / Q.n), i = (int)(t % Q.n);
-  const int leaf = Q.leaf_of[i];
-  const size_t hq = (size_t)hidx * Q.nn + leaf;
-  double val = gacc[t];
-  const int p = pused[hq];
-  if (p > 0) {
-    const double* Lq = L + hq * P;
-    val += Lq[0];
-    if (p > 1) {
-      const float sf = sfv[hidx];
-      float qv[D];
-      load_point<D>(Q.pts + (size_t)i * Q.dp, qv);
-      float X[D][PM];
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float x = minus_center(qv[k], center_hl(Q, leaf, k)) * sf;
-        float v = 1.f;
-#pragma unroll
-        for (int q = 0; q < PM; ++q) { X[k][q] = v; v *= x; }
-      }
-      float acc = 0.f;
-#pragma unroll
-      for (int idx = 1; idx < P; ++idx) {
-        if (!below_c<D, PM>(idx, p)) continue;
-        float term = (float)Lq[idx];
-#pragma unroll
-        for (int k = 0; k < D; ++k) term *= X[k][digit_c<D, PM>(idx, k)];
-        acc += term;
-      }
-      val += (double)acc;
-    }
-  }
-  G[(size_t)hidx * Q.n + Q.perm[i]] = val;
 }
 
 // ------------------------------------------------- order 0 (D >= 6)
@@ -857,32 +886,26 @@ __global__ void k_f2l_g(TreeView Q, TreeView R, const Action* __restrict__ list,
   atomicMax(&pused[hq], 1);
 }
 
-__global__ void k_l2l_g(TreeView Q, double* __restrict__ L, int* __restrict__ pused, int nh, int a,
-                        int e) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nl = e - a;
-  if (t >= nl * nh) return;
-  const int node = a + t % nl, hidx = t / nl;
-  const int cl = Q.left[node];
-  if (cl < 0) return;
-  const size_t hq = (size_t)hidx * Q.nn + node;
-  if (pused[hq] == 0) return;
-  for (int ch = 0; ch < 2; ++ch) {
-    const size_t hc = (size_t)hidx * Q.nn + cl + ch;
-    L[hc] += L[hq];
-    if (pused[hc] < 1) pused[hc] = 1;
+// D >= 6: only constants, summed along the path from the root.
+__global__ void __launch_bounds__(kT) k_post_g(TreeView Q, const int* __restrict__ leaves, int nleaves,
+                                               const double* __restrict__ gacc,
+                                               const double* __restrict__ L,
+                                               const int* __restrict__ pused, int nh,
+                                               double* __restrict__ G) {
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int li = blockIdx.x * kWarpsPerBlock + wib;
+  if (li >= nleaves) return;
+  const int leaf = leaves[li];
+  const int qb = Q.beg[leaf], qn = Q.cnt[leaf];
+  for (int hidx = 0; hidx < nh; ++hidx) {
+    double c0 = 0.0;
+    for (int v = leaf; v >= 0; v = Q.parent[v]) {
+      const size_t hv = (size_t)hidx * Q.nn + v;
+      if (pused[hv] > 0) c0 += L[hv];
+    }
+    for (int pi = lane; pi < qn; pi += 32)
+      G[(size_t)hidx * Q.n + Q.perm[qb + pi]] = gacc[(size_t)hidx * Q.n + qb + pi] + c0;
   }
-}
-
-__global__ void k_finalize_g(TreeView Q, const double* __restrict__ gacc, const double* __restrict__ L,
-                             const int* __restrict__ pused, int nh, double* __restrict__ G) {
-  const long t = (long)blockIdx.x * kT + threadIdx.x;
-  if (t >= (long)nh * Q.n) return;
-  const int hidx = (int)(t / Q.n), i = (int)(t % Q.n);
-  const size_t hq = (size_t)hidx * Q.nn + Q.leaf_of[i];
-  double val = gacc[t];
-  if (pused[hq] > 0) val += L[hq];
-  G[(size_t)hidx * Q.n + Q.perm[i]] = val;
 }
 
 inline int warp_grid(long items) { return (int)((items * 32 + kT - 1) / kT); }
@@ -986,25 +1009,14 @@ cudaError_t launch_prune_apply(const TreeView& Q, const TreeView& R, const TravB
   return cudaGetLastError();
 }
 
-cudaError_t launch_l2l_level(const TreeView& Q, const TravBuffers& b, int a, int e, cudaStream_t s) {
-  const long items = (long)(e - a) * b.nh;
-  if (items <= 0) return cudaSuccess;
+cudaError_t launch_post(const TreeView& Q, const int* leaves, int nleaves, const TravBuffers& b,
+                        double* G, cudaStream_t s) {
+  if (nleaves <= 0) return cudaSuccess;
+  const int g = (nleaves + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (Q.d <= 5) {
-    const int g = warp_grid(items);
-    DISPATCH_D(Q.d, k_l2l<DD><<<g, kT, 0, s>>>(Q, b.L, b.pused, b.h, b.nh, a, e));
+    DISPATCH_D(Q.d, k_post<DD><<<g, kT, 0, s>>>(Q, leaves, nleaves, b.gacc, b.L, b.pused, b.sf, b.nh, G));
   } else {
-    k_l2l_g<<<(int)((items + kT - 1) / kT), kT, 0, s>>>(Q, b.L, b.pused, b.nh, a, e);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_finalize(const TreeView& Q, const TravBuffers& b, double* G, cudaStream_t s) {
-  const long items = (long)b.nh * Q.n;
-  const int g = (int)((items + kT - 1) / kT);
-  if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_finalize<DD><<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.sf, b.nh, G));
-  } else {
-    k_finalize_g<<<g, kT, 0, s>>>(Q, b.gacc, b.L, b.pused, b.nh, G);
+    k_post_g<<<g, kT, 0, s>>>(Q, leaves, nleaves, b.gacc, b.L, b.pused, b.nh, G);
   }
   return cudaGetLastError();
 }

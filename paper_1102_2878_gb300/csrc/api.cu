@@ -36,17 +36,13 @@ bool bad_h(const double* h, int nh) {
   return false;
 }
 
-// DFGTPost: local-to-local translation level by level down the query
-// tree, then the leaf read-out and the final sum into G_dev.
+// DFGTPost: local expansions shifted to the leaves, read out and added to
+// the exact and far-field parts, into G_dev (one fused kernel).
 dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, double* G_dev,
                  dfgt_stats* st) {
   cudaStream_t s = ctx->stream;
   const TreeView Q = qt->view();
-  for (int lev = 0; lev + 1 < qt->depth; ++lev) {
-    CK(launch_l2l_level(Q, b, qt->lvl_off[lev], qt->lvl_off[lev + 1], s));
-    ++ctx->launches;
-  }
-  CK(launch_finalize(Q, b, G_dev, s));
+  CK(launch_post(Q, qt->leaves, qt->nleaves, b, G_dev, s));
   ++ctx->launches;
   CK(cudaEventRecord(ctx->ev[3], s));
   CK(cudaStreamSynchronize(s));

@@ -32,7 +32,6 @@ struct TreeView {
   const int* cnt;      // [nn] number of points
   const int* left;     // [nn] first child, -1 for a leaf (second child = left+1)
   const int* parent;   // [nn] parent node, -1 for the root
-  const int* leaf_of;  // [n] leaf owning each permuted point
   const double* mom;   // [nn][P] raw moments sum (r-c)^alpha/alpha! about the box center
   const float* chi;    // [nn][d] box center as a float pair chi + clo
   const float* clo;
@@ -98,15 +97,14 @@ __device__ inline double bound_f2l(double nR, int D, double r, int p) {
 // term of the truncated series is bounded (Szasz's inequality, as in the
 // proofs of the truncation lemmas) so that the sum of absolute terms is at
 // most |R| * S with S = ((1-r^p)/(1-r))^D (far field, local) or
-// ((1-(2r)^p)/(1-2r))^{2D} (far to local); float32 evaluation, the
-// float32 local-expansion read-out and the coefficient conversions add at
-// most c * u * |R| * S with u = 2^-24 and c = 2 (2 p^D + 6D + 16).
-__device__ inline double fp_allowance(double nR, int D, double r_eff, int p, int pow2) {
-  const double u = 5.9604644775390625e-08;
-  const double g = (1.0 - pow_int(r_eff, p)) / (1.0 - r_eff);
-  const double S = pow_int(g, pow2 * D);
-  const double c = 2.0 * (2.0 * pow_int((double)p, D) + 6.0 * D + 16.0);
-  return c * u * nR * S;
+// ((1-(2r)^p)/(1-2r))^{2D} (far to local); float32 evaluation, the shift
+// of a local expansion to the leaf center, the float32 read-out and the
+// coefficient conversions add at most c * u * |R| * S with u = 2^-24 and
+// c = 2 (2 p^D + 6 p D + 6D + 16).
+__host__ __device__ inline float fp_allowance_c(int p, int D) {
+  float pD = 1.f;
+  for (int i = 0; i < D; ++i) pD *= (float)p;
+  return 2.f * (2.f * pD + 6.f * p * D + 6.f * D + 16.f);
 }
 
 // Float32 evaluations of the same bounds for order selection.  Every
@@ -140,7 +138,7 @@ __device__ inline float bound_ff_total(float nR, int D, float r, int p) {
   const float g = 1.f / (1.f - r);
   const float gD = pow_int_f(g, D);
   const float S = pow_int_f(a * g, D);
-  const float cfp = 2.f * (2.f * pow_int_f((float)p, D) + 6.f * D + 16.f) * 5.9604645e-08f;
+  const float cfp = fp_allowance_c(p, D) * 5.9604645e-08f;
   return nR * (sum * gD + cfp * S);
 }
 
@@ -157,7 +155,7 @@ __device__ inline float bound_f2l_total(float nR, int D, float r, int p) {
   const float g = 1.f / (1.f - 2.f * r);
   const float g2D = pow_int_f(g, 2 * D);
   const float S = pow_int_f((1.f - q) * g, 2 * D);
-  const float cfp = 2.f * (2.f * pow_int_f((float)p, D) + 6.f * D + 16.f) * 5.9604645e-08f;
+  const float cfp = fp_allowance_c(p, D) * 5.9604645e-08f;
   return nR * (sum * g2D + cfp * S);
 }
 

@@ -119,7 +119,7 @@ struct dfgt_tree {
   int* cnt = nullptr;
   int* left = nullptr;
   int* parent = nullptr;
-  int* leaf_of = nullptr;
+  int* leaves = nullptr;      // [nleaves] leaf node ids
   double* mom = nullptr;
   float* chi = nullptr;
   float* clo = nullptr;
@@ -128,7 +128,7 @@ struct dfgt_tree {
   dfgt::TreeView view() const {
     dfgt::TreeView v;
     v.pts = pts; v.perm = perm; v.lo = lo; v.hi = hi; v.beg = beg; v.cnt = cnt;
-    v.left = left; v.parent = parent; v.leaf_of = leaf_of; v.mom = mom;
+    v.left = left; v.parent = parent; v.mom = mom;
     v.chi = chi; v.clo = clo; v.whalf = whalf; v.mnorm = mnorm;
     v.n = (int)n; v.d = d; v.dp = dp; v.nn = nn; v.pm = pm; v.P = P;
     return v;
@@ -212,9 +212,7 @@ cudaError_t launch_f2l(const TreeView& Q, const TreeView& R, const TravBuffers& 
                        const Action* list, int n, cudaStream_t s);
 cudaError_t launch_prune_apply(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                                const Pair* list, int n, cudaStream_t s);
-cudaError_t launch_l2l_level(const TreeView& Q, const TravBuffers& b, int a, int e,
-                             cudaStream_t s);
-cudaError_t launch_finalize(const TreeView& Q, const TravBuffers& b, double* G_out,
-                            cudaStream_t s);
+cudaError_t launch_post(const TreeView& Q, const int* leaves, int nleaves, const TravBuffers& b,
+                        double* G, cudaStream_t s);
 
 }  // namespace dfgt

@@ -204,14 +204,6 @@ __global__ void k_scatter(int n, int dp, int a, const float* __restrict__ pin,
   pnode_out[dst] = child;
 }
 
-__global__ void k_leaf_of(int nn, const int* __restrict__ beg, const int* __restrict__ cnt,
-                          const int* __restrict__ left, int* __restrict__ leaf_of) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w >= nn || left[w] >= 0) return;
-  for (int i = lane; i < cnt[w]; i += 32) leaf_of[beg[w] + i] = w;
-}
-
 // ---------------------------------------------------------------- moments
 // alpha digit of coefficient position idx (radix PM, last dimension least
 // significant), matching the linear layout of the paper's appendix.
@@ -470,7 +462,7 @@ void free_tree(dfgt_tree* t) {
   t->tpool.reset();
   t->chi = t->clo = t->whalf = t->mnorm = nullptr;
   t->pts = nullptr; t->perm = nullptr; t->lo = t->hi = nullptr;
-  t->beg = t->cnt = t->left = t->parent = t->leaf_of = nullptr; t->mom = nullptr;
+  t->beg = t->cnt = t->left = t->parent = t->leaves = nullptr; t->mom = nullptr;
 }
 
 #define TRY(x)                                                   \
@@ -623,7 +615,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       ca.off = 0;
       t->pts = ca.take<float>(np * t->dp);
       t->perm = ca.take<int>(np);
-      t->leaf_of = ca.take<int>(np);
+      t->leaves = ca.take<int>(nn);
       t->lo = ca.take<float>(nn * d);
       t->hi = ca.take<float>(nn * d);
       t->beg = ca.take<int>(nn);
@@ -646,8 +638,6 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
     na.copy_to(t->lo, t->hi, t->beg, t->cnt, t->left, t->parent, nn, d, s, &ce);
     TRY(ce);
   }
-  k_leaf_of<<<(int)(((size_t)t->nn * 32 + kT - 1) / kT), kT, 0, s>>>(t->nn, t->beg, t->cnt, t->left, t->leaf_of);
-  ++*L;
   switch (d) {
     case 1: TRY(moments_d<1>(t, s, L)); break;
     case 2: TRY(moments_d<2>(t, s, L)); break;
@@ -663,11 +653,16 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   ++*L;
   TRY(cudaGetLastError());
   {
-    // count leaves on the host side from the level structure
+    // the leaf list, in node order, from the level structure
     std::vector<int> left_h(t->nn);
     TRY(cudaMemcpyAsync(left_h.data(), t->left, t->nn * sizeof(int), cudaMemcpyDeviceToHost, s));
     TRY(cudaStreamSynchronize(s));
-    t->nleaves = (int)std::count(left_h.begin(), left_h.end(), -1);
+    std::vector<int> leaves_h;
+    for (int j = 0; j < t->nn; ++j)
+      if (left_h[j] < 0) leaves_h.push_back(j);
+    t->nleaves = (int)leaves_h.size();
+    TRY(cudaMemcpyAsync(t->leaves, leaves_h.data(), leaves_h.size() * sizeof(int), cudaMemcpyHostToDevice, s));
+    TRY(cudaStreamSynchronize(s));
   }
   rc = DFGT_OK;
 fail:

@@ -11,9 +11,12 @@ two agree to rounding.
 
 Tolerance: the GPU evaluates series terms in float32.  With u = 2^-24 the
 rounding error of an order-p series is at most c u sum|terms| with
-c = 2 (2 p^D + 6 D + 16) (the same allowance the traversal adds to its
-truncation bounds); sum|terms| is computed here from the oracle's own
-series, so the check is |gpu - oracle| <= c u sum|terms| + 1e-12.
+c = 2 (2 p^D + 6 p D + 6 D + 16) (the same allowance the traversal adds to
+its truncation bounds); sum|terms| is computed here from the oracle's own
+series, so the check is |gpu - oracle| <= c u sum|terms| + 1e-12.  A local
+expansion is shifted to the leaf center c' before it is read out, so its
+terms are taken at |x - c'| + |c' - c| per dimension (the absolute values
+of the shifted polynomial's terms), which is never less than |x - c|.
 """
 import math
 
@@ -29,7 +32,7 @@ U = 2.0 ** -24
 
 
 def allowance(p, D):
-    return 2 * (2 * p ** D + 6 * D + 16) * U
+    return 2 * (2 * p ** D + 6 * p * D + 6 * D + 16) * U
 
 
 @pytest.fixture(scope="module", params=[1, 2, 3, 4, 5])
@@ -55,6 +58,14 @@ def side(t, j):
     return float((t["hi"][j].astype(np.float64) - t["lo"][j].astype(np.float64)).max())
 
 
+def leaf_centers(t, n):
+    """center of the leaf holding each point, in the caller's point order"""
+    out = np.zeros((n, t["lo"].shape[1]))
+    for j in np.where(t["left"] < 0)[0]:
+        out[t["perm"][t["begin"][j]:t["begin"][j] + t["count"][j]]] = center(t, j)
+    return out
+
+
 def pick_nodes(t, rng, k, min_count=40):
     cand = np.where(t["count"] >= min_count)[0]
     return rng.choice(cand, size=min(k, len(cand)), replace=False)
@@ -70,9 +81,11 @@ def hermite_table(orc, t, n):
     return np.array([orc.hermite_functions(tk, n) for tk in t])  # [D][n]
 
 
-def series(orc, kind, Rp, Qp, cR, cQ, h, p, pm):
+def series(orc, kind, Rp, Qp, cR, cQ, h, p, pm, cL=None):
     """Oracle value of the truncated series at each query, and the sum of
-    the absolute values of its terms (the scale of float32 rounding)."""
+    the absolute values of its terms (the scale of float32 rounding); cL
+    holds the center of each query's leaf, where local expansions are read
+    out."""
     D = Rp.shape[1]
     s = 1.0 / np.sqrt(2 * h * h)
     A = multi(pm, D)
@@ -102,7 +115,7 @@ def series(orc, kind, Rp, Qp, cR, cQ, h, p, pm):
                 absL[b] = sum(absM[j] * np.prod([H[k, A[j, k] + A[b, k]] for k in range(D)])
                               for j in range(len(A)) if keep[j]) / fact[b]
     want = orc.eval_local(L, cQ, h, p, Qp, pm)
-    X = np.abs((Qp - cQ) * s)
+    X = np.abs((Qp - cQ) * s) if cL is None else np.abs((Qp - cL) * s) + np.abs((cL - cQ) * s)
     scale = np.array([(absL * (x[None, :] ** A).prod(1)).sum() for x in X])
     return want, scale
 
@@ -121,7 +134,8 @@ def test_expansion_operator(setup, orc, dev, kind):
         G = dfgt.apply_pairs(dev, qt, rt, [qn], [rn], [act], [p], h).cpu().numpy()
         qidx, Qp = node_points(X, tq, qn)
         _, Rp = node_points(Y, tr, rn)
-        want, scale = series(orc, kind, Rp, Qp, center(tr, rn), center(tq, qn), h, p, pm)
+        want, scale = series(orc, kind, Rp, Qp, center(tr, rn), center(tq, qn), h, p, pm,
+                             leaf_centers(tq, len(X))[qidx])
         err = np.abs(G[qidx] - want)
         assert np.all(err <= allowance(p, D) * scale + 1e-12), (kind, D, p, err.max(), scale.max())
         others = np.setdiff1d(np.arange(len(X)), qidx)
@@ -187,7 +201,8 @@ def test_mixed_list_accumulates(setup, orc, dev):
         qi, Qp = node_points(X, tq, a)
         _, Rp = node_points(Y, tr, b)
         kind = {_lib.ACT_FARFIELD: "F", _lib.ACT_LOCAL: "D", _lib.ACT_F2L: "T"}[act]
-        v, sc = series(orc, kind, Rp, Qp, center(tr, b), center(tq, a), h, p, pm)
+        v, sc = series(orc, kind, Rp, Qp, center(tr, b), center(tq, a), h, p, pm,
+                       leaf_centers(tq, len(X))[qi])
         want[qi] += v
         scale[qi] += sc
     assert np.all(np.abs(G - want) <= allowance(pm, D) * scale + 1e-12)
