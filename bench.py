@@ -308,7 +308,8 @@ def run_dfgt(args, rank, world, local):
                          "f2l": mean("ms_f2l"), "post": mean("ms_post")},
         "work": {"pairs_visited": mean("pairs_visited"), "prune": mean("n_prune"),
                  "farfield": mean("n_farfield"), "local": mean("n_local"), "f2l": mean("n_f2l"),
-                 "base_pairs": mean("n_base"), "base_interactions": inter, "rounds": mean("rounds")},
+                 "base_pairs": mean("n_base"), "base_interactions": inter,
+                 "base_expanded": mean("base_expanded"), "rounds": mean("rounds")},
         "roofline": roof,
         "cpu_baseline": None if cpu_rate is None else
         {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cpu_desc},

@@ -32,7 +32,7 @@ class Stats(C.Structure):
                 ("ms_traverse", C.c_double), ("ms_classify", C.c_double), ("ms_actions", C.c_double),
                 ("ms_post", C.c_double),
                 ("ms_base", C.c_double), ("ms_farfield", C.c_double), ("ms_local", C.c_double),
-                ("ms_f2l", C.c_double)]
+                ("ms_f2l", C.c_double), ("base_expanded", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

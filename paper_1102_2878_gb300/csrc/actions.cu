@@ -104,24 +104,25 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 // DFGTBase: exact sums over the listed node pairs.
 //
 // The list is sorted by (bandwidth, query node) with a counting sort, and
-// each warp takes a chunk of kBaseChunk consecutive sorted entries, so the
-// entries of one query node mostly share a warp: the queries stay in
-// registers across them and each query receives one float64 atomic add per
-// run of entries instead of one per pair.  The chunk's descriptors are
-// loaded in one round trip (one per lane) and broadcast with shuffles.
+// each warp takes kEntryChunk = 32 consecutive sorted entries, one per lane:
+// every descriptor of the chunk (reference block, query node, its box,
+// the expansion test) is fetched in one round trip and broadcast with
+// shuffles.  Consecutive entries of one (bandwidth, query node) form a
+// run; its references are processed as one concatenated list, so each
+// query of the run receives one float64 atomic add per tile.
 //
-// Reference points are staged per warp in shared memory, negated, as
-// structure-of-arrays tiles of kTile points, so one 64-bit load yields the
-// coordinate of two consecutive references and every FP32 step works on
-// two interactions at once (packed f32x2 add / fma / mul).  Per pair of
-// interactions that is 2D+2 packed ops and two SFU ex2, so the kernel is
-// bound by the ex2 rate rather than by instruction issue.  For |Q| < 32 the
-// warp is split into 32/g lane groups (g = |Q| rounded up to a power of
-// two) that share the queries and divide the reference pairs.  A run of
-// one reference node is summed in float32; runs are added with Kahan
-// compensation and lane groups are combined in float64.
-
-constexpr int kBaseChunk = 8;
+// References are copied raw into shared memory with cp.async one tile
+// ahead (the next tile of the run, or the first tile of the next run)
+// while the current tile is summed, so global latency overlaps the SFU
+// work.  A staged tile is rewritten once per run into pair-interleaved
+// rows: for references j, j+1 the values (x_j, x_j+1, y_j, y_j+1, ...,
+// B_j, B_j+1), so two 128-bit shared loads give every operand of a packed
+// f32x2 step on two interactions.  Each lane holds two queries; for a run
+// of few queries the warp splits into lane groups that share the queries
+// and divide the references.
+constexpr int kBaseChunk = 8;     // entries per warp of the local-moment kernel
+constexpr int kEntryChunk = 32;   // entries per warp of the base case
+constexpr int kBaseWarps = 4;     // warps per block of the base case
 constexpr int kNodeBits = 27;  // node indices stay below 2^27 (checked by the tree build)
 constexpr int kNodeMask = (1 << kNodeBits) - 1;
 constexpr float kFarNeg = -1.0e18f;  // padding point: contributes exp(-huge) = 0
@@ -185,212 +186,422 @@ __device__ __forceinline__ void kahan_add(float& S, float& C, float v) {
   S = t;
 }
 
-// One lane's share of a staged tile: reference pairs jp = 2*gid, 2*gid + step, ...
-// (step = 2 * number of lane groups) against the lane's two queries a and b.
-// EXP selects the expanded form (qa/qb hold W, aa/ab hold A) or the direct
-// form (qa/qb hold the query).  Runs of 16 pairs are Kahan-compensated.
-template <int D, bool EXP, int TILE>
-__device__ __forceinline__ void base_tile_sums(const float (*sR)[TILE], int tn2, int gid, int step,
-                                               const float2* qa, const float2* qb, float2 aa, float2 ab,
-                                               float2 c2p, float& Sa, float& Ca, float& Sb, float& Cb) {
-  for (int jr = 2 * gid; jr < tn2; jr += 16 * step) {
-    const int je = min(jr + 16 * step, tn2);
+// Shapes of the base-case tiles for dimension D: RAW floats per staged
+// reference (the tree's padded row), PAIRW floats per interleaved
+// reference pair (padded to whole float4s) and TILE references per warp.
+template <int D>
+struct BaseShape {
+  static constexpr int RAW = D <= 2 ? D : ((D + 3) & ~3);
+  static constexpr int PAIRW = ((2 * (D + 1) + 3) / 4) * 4;
+  static constexpr int NV = PAIRW / 4;
+  static constexpr int TILE = D == 1 ? 512 : D <= 3 ? 256 : 128;
+};
+
+__device__ __forceinline__ void cp_async_row(float* dst, const float* src, int bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const size_t g = __cvta_generic_to_global(src);
+  if (bytes == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(g) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(g) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// One interaction pair step: reference pair at p against the lane's two
+// queries; adds 2^x of the four interactions to pa / pb.
+template <int D, bool EXP>
+__device__ __forceinline__ void base_step(const float4* __restrict__ p, const float2* wa, const float2* wb,
+                                          float2 c2p, float2& pa, float2& pb) {
+  constexpr int NV = BaseShape<D>::NV;
+  float f[4 * NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float4 t4 = p[v];
+    f[4 * v] = t4.x; f[4 * v + 1] = t4.y; f[4 * v + 2] = t4.z; f[4 * v + 3] = t4.w;
+  }
+  float2 xa, xb;
+  if constexpr (EXP) {
+    xa = make_float2(f[2 * D], f[2 * D + 1]);
+    xb = xa;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float2 rk = make_float2(f[2 * k], f[2 * k + 1]);
+      xa = __ffma2_rn(wa[k], rk, xa);
+      xb = __ffma2_rn(wb[k], rk, xb);
+    }
+  } else {
+    float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float2 rk = make_float2(f[2 * k], f[2 * k + 1]);
+      const float2 ta = __fadd2_rn(wa[k], rk);
+      const float2 tb = __fadd2_rn(wb[k], rk);
+      da = __ffma2_rn(ta, ta, da);
+      db = __ffma2_rn(tb, tb, db);
+    }
+    xa = __fmul2_rn(da, c2p);
+    xb = __fmul2_rn(db, c2p);
+  }
+  pa = __fadd2_rn(pa, make_float2(ex2_approx(xa.x), ex2_approx(xa.y)));
+  pb = __fadd2_rn(pb, make_float2(ex2_approx(xb.x), ex2_approx(xb.y)));
+}
+
+// One lane's share of an interleaved tile: reference pairs jp = gid,
+// gid + ngrp, ... against the lane's two queries a and b.  EXP selects the
+// expanded form (wa/wb hold W_q; the exponent is B_r + W_q . r~, A_q is
+// applied by the caller) or the direct form (wa/wb hold the query, rows
+// the negated reference).  Blocks of 16 steps (unrolled, no bounds tests)
+// are summed in float32 and added with Kahan compensation.
+template <int D, bool EXP>
+__device__ __forceinline__ void base_tile_sums(const float4* __restrict__ T, int np2, int gid, int ngrp,
+                                               const float2* wa, const float2* wb, float2 c2p,
+                                               float& Sa, float& Ca, float& Sb, float& Cb) {
+  constexpr int NV = BaseShape<D>::NV;
+  int left = np2 / ngrp;  // np2 is padded to a multiple of ngrp: the same count in every lane
+  const float4* p = T + gid * NV;
+  const int stride = ngrp * NV;
+  for (; left >= 16; left -= 16) {
     float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
-#pragma unroll 2
-    for (int jp = jr; jp < je; jp += step) {
-      float2 rr[D + 1];
 #pragma unroll
-      for (int k = 0; k < (EXP ? D + 1 : D); ++k) rr[k] = *reinterpret_cast<const float2*>(&sR[k][jp]);
-      float2 xa, xb;
-      if constexpr (EXP) {
-        xa = __fadd2_rn(aa, rr[D]);
-        xb = __fadd2_rn(ab, rr[D]);
+    for (int u = 0; u < 16; ++u) {
+      base_step<D, EXP>(p, wa, wb, c2p, pa, pb);
+      p += stride;
+    }
+    kahan_add(Sa, Ca, pa.x + pa.y);
+    kahan_add(Sb, Cb, pb.x + pb.y);
+  }
+  if (left > 0) {
+    float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+    for (; left >= 4; left -= 4) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) {
-          xa = __ffma2_rn(qa[k], rr[k], xa);
-          xb = __ffma2_rn(qb[k], rr[k], xb);
-        }
-      } else {
-        float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-          const float2 ta = __fadd2_rn(qa[k], rr[k]);
-          const float2 tb = __fadd2_rn(qb[k], rr[k]);
-          da = __ffma2_rn(ta, ta, da);
-          db = __ffma2_rn(tb, tb, db);
-        }
-        xa = __fmul2_rn(da, c2p);
-        xb = __fmul2_rn(db, c2p);
+      for (int u = 0; u < 4; ++u) {
+        base_step<D, EXP>(p, wa, wb, c2p, pa, pb);
+        p += stride;
       }
-      pa = __fadd2_rn(pa, make_float2(ex2_approx(xa.x), ex2_approx(xa.y)));
-      pb = __fadd2_rn(pb, make_float2(ex2_approx(xb.x), ex2_approx(xb.y)));
+    }
+    for (; left > 0; --left) {
+      base_step<D, EXP>(p, wa, wb, c2p, pa, pb);
+      p += stride;
     }
     kahan_add(Sa, Ca, pa.x + pa.y);
     kahan_add(Sb, Cb, pb.x + pb.y);
   }
 }
 
-// References staged per warp: D+1 rows of as many points as 48 KB of
-// shared memory per block allows.
+// First D coordinates of a staged raw row (RAW floats, 16-byte aligned for RAW >= 4).
 template <int D>
-constexpr int base_tile() {
-  return ((48 * 1024 / 4 / kWarpsPerBlock) / (D + 1)) & ~1;
+__device__ __forceinline__ void load_raw(const float* row, float* a) {
+  constexpr int RAW = BaseShape<D>::RAW;
+  if constexpr (RAW == 1) {
+    a[0] = row[0];
+  } else if constexpr (RAW == 2) {
+    const float2 v = *reinterpret_cast<const float2*>(row);
+    a[0] = v.x; a[1] = v.y;
+  } else {
+    const float4 v = *reinterpret_cast<const float4*>(row);
+    a[0] = v.x; a[1] = v.y; a[2] = v.z;
+    if constexpr (D >= 4) a[3] = v.w;
+    if constexpr (D == 5) a[4] = row[4];
+  }
 }
 
 // Two forms of the exponent x = c |q - r|^2, c = -log2(e)/(2h^2):
-//  * direct: differences q - r, D packed add + D packed fma per pair of
-//    references; rounding changes a term by at most (D+3) u x relative;
+//  * direct: differences q - r, D packed add + D packed fma + 1 packed mul
+//    per two interactions; rounding changes a term by at most (D+3) u x
+//    relative (x in natural units from here on);
 //  * expanded about the query node's center m, with q~ = q - m, r~ = r - m:
 //    x = A_q + B_r + sum_k W_qk r~_k, A_q = c|q~|^2, W_q = -2c q~, B_r = c|r~|^2
-//    staged with the reference; one packed add + D packed fma per pair.
-//    Its rounding error in x is at most (D+3) u |c| (|q~| + |r~|)^2, the
-//    same for every term, so a run uses it only when that bound, taken over
-//    the query box and the farthest corner of every reference box, is at
-//    most kExpandedErr relative; otherwise the direct form.
+//    staged with the reference; the sum runs over 2^(B_r + W_q . r~) with D
+//    packed fma per two interactions and is scaled by 2^A_q once per query
+//    and tile (B_r + W_q . r~ = x - A_q lies between x and |c| |q~|^2, so it
+//    cannot overflow, and it underflows only where 2^x does).  Its error in
+//    x, with the rounding of q~ and r~ taken as a perturbation of the points,
+//    is at most (D+4) u (|q~| + |r~|)^2 / 2h^2.  A run uses it when that is
+//    at most kExpandedErr for the query box and the farthest corner of every
+//    reference box, or when 8 (D+4) u rho_Q^2 / 2h^2 <= kExpandedErr for the
+//    query box radius rho_Q alone: with |r~| <= |q~| + |q - r| and
+//    (a + b)^2 <= 2a^2 + 2b^2 the error is then at most
+//    kExpandedErr + 2 (D+4) u x per term.  Otherwise the direct form.
 constexpr float kExpandedErr = 5e-6f;
 
+constexpr int kQCap = 64;  // queries of a run staged at a time
+
 template <int D>
-__global__ void __launch_bounds__(kT, 3) k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted,
-                                             const int* __restrict__ ksorted, int n,
-                                             const float* __restrict__ c2v,
-                                             const float* __restrict__ inv2h2_up,
-                                             double* __restrict__ gacc) {
-  constexpr int TILE = base_tile<D>();
-  __shared__ __align__(16) float sR[kWarpsPerBlock][D + 1][TILE];
+__global__ void __launch_bounds__(kBaseWarps * 32, 5)
+    k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted, const int* __restrict__ ksorted, int n,
+           const float* __restrict__ c2v, const float* __restrict__ inv2h2_up, double* __restrict__ gacc,
+           unsigned long long* __restrict__ exp_ctr) {
+  using SH = BaseShape<D>;
+  constexpr int TILE = SH::TILE, RAW = SH::RAW, NV = SH::NV;
+  constexpr int QV = (D + 1 + 3) / 4;  // float4 per staged query: W (or q) then A
+  __shared__ __align__(16) float sRaw[kBaseWarps][TILE * RAW];
+  __shared__ __align__(16) float4 sT[kBaseWarps][(TILE / 2) * NV];
+  __shared__ __align__(16) float4 sQ[kBaseWarps][kQCap * QV];
+  __shared__ float2 sAcc[kBaseWarps][kQCap];
+  __shared__ int sOff[kBaseWarps][2][kEntryChunk + 1];
+  __shared__ int sRb[kBaseWarps][2][kEntryChunk];
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
+  const long i0 = ((long)blockIdx.x * kBaseWarps + wib) * kEntryChunk;
   if (i0 >= n) return;
-  const int m = (int)min((long)kBaseChunk, n - i0);
-  int my_key = -1, my_r = 0, my_rb = 0, my_rn = 0;
+  const int m = (int)min((long)kEntryChunk, n - i0);
+  const unsigned FULL = 0xffffffffu;
+
+  // ---- descriptors, one entry per lane
+  int key = -1 - lane, rb = 0, rn = 0, qbeg = 0, qcnt = 0;
+  float mc[D], rho2 = 0.f, far2 = 0.f, c2 = 0.f, i2h = 0.f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) mc[k] = 0.f;
   if (lane < m) {
-    my_key = ksorted[i0 + lane];
-    my_r = rsorted[i0 + lane] & kNodeMask;
-    my_rb = R.beg[my_r];
-    my_rn = R.cnt[my_r];
-  }
-  int t = 0;
-  while (t < m) {
-    // a run: consecutive entries of the same (bandwidth, query node)
-    const int key = __shfl_sync(0xffffffffu, my_key, t);
-    int e = t + 1;
-    while (e < m && __shfl_sync(0xffffffffu, my_key, e) == key) ++e;
-    int tot = 0;
-    for (int u = t; u < e; ++u) tot += __shfl_sync(0xffffffffu, my_rn, u);
-    const int hidx = key / Q.nn, q = key % Q.nn;
-    const float c2 = c2v[hidx];
-    const int qb = Q.beg[q], qn = Q.cnt[q];
-    const int g = pick_group(qn, tot);
-    const int ngrp = 32 / g, ql = lane % g, gid = lane / g;
-    // expansion center and the error test of the expanded form
-    float mc[D];
-    float rhoQ2 = 0.f;
+    key = ksorted[i0 + lane];
+    const int r = rsorted[i0 + lane] & kNodeMask;
+    const int hidx = key / Q.nn, q = key - hidx * Q.nn;
+    rb = R.beg[r];
+    rn = R.cnt[r];
+    qbeg = Q.beg[q];
+    qcnt = Q.cnt[q];
+    c2 = c2v[hidx];
+    i2h = inv2h2_up[hidx];
 #pragma unroll
     for (int k = 0; k < D; ++k) {
       const float lo = Q.lo[(size_t)q * D + k], hi = Q.hi[(size_t)q * D + k];
       mc[k] = 0.5f * (lo + hi);
       const float w = fmaxf(__fsub_ru(hi, mc[k]), __fsub_ru(mc[k], lo));
-      rhoQ2 = __fmaf_ru(w, w, rhoQ2);
+      rho2 = __fmaf_ru(w, w, rho2);
     }
-    float far2 = 0.f;  // farthest reference-box corner from mc, squared
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float lo = R.lo[(size_t)r * D + k], hi = R.hi[(size_t)r * D + k];
+      const float w = fmaxf(fabsf(__fsub_ru(hi, mc[k])), fabsf(__fsub_rd(lo, mc[k])));
+      far2 = __fmaf_ru(w, w, far2);
+    }
+  }
+  const int keyp = __shfl_up_sync(FULL, key, 1);
+  const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
+  auto run_end = [&](int t) -> int {
+    const unsigned later = starts & ~((2u << t) - 1u);
+    return later ? __ffs(later) - 1 : m;
+  };
+  // offset table of run [t, e) in slot sl; returns the run's reference count
+  auto build_table = [&](int t, int e, int sl) -> int {
+    const int in_run = (lane >= t && lane < e) ? rn : 0;
+    int incl = in_run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int tot = __shfl_sync(FULL, incl, 31);
     if (lane >= t && lane < e) {
+      sOff[wib][sl][lane - t] = incl - in_run;
+      sRb[wib][sl][lane - t] = rb;
+    }
+    if (lane == 0) sOff[wib][sl][e - t] = tot;
+    __syncwarp();
+    return tot;
+  };
+  // raw rows [j0, j0 + tn) of the run in table slot sl (ne entries) -> sRaw, asynchronously
+  auto issue = [&](int sl, int ne, int j0, int tn) {
+    int u = -1;
+    for (int j = lane; j < tn; j += 32) {
+      const int J = j0 + j;
+      if (u < 0) {
+        int lo = 0, hi = ne;  // sOff[lo] <= J < sOff[hi]
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (sOff[wib][sl][mid] <= J) lo = mid; else hi = mid;
+        }
+        u = lo;
+      } else {
+        while (sOff[wib][sl][u + 1] <= J) ++u;
+      }
+      const float* src = R.pts + (size_t)(sRb[wib][sl][u] + J - sOff[wib][sl][u]) * RAW;
+      float* dst = &sRaw[wib][j * RAW];
+      if constexpr (RAW * 4 <= 16) {
+        cp_async_row(dst, src, RAW * 4);
+      } else {
 #pragma unroll
-      for (int k = 0; k < D; ++k) {
-        const float lo = R.lo[(size_t)my_r * D + k], hi = R.hi[(size_t)my_r * D + k];
-        const float w = fmaxf(fabsf(__fsub_ru(hi, mc[k])), fabsf(__fsub_rd(lo, mc[k])));
-        far2 = __fmaf_ru(w, w, far2);
+        for (int c = 0; c < RAW * 4 / 16; ++c) cp_async_row(dst + 4 * c, src + 4 * c, 16);
       }
     }
-    for (int o = 16; o > 0; o >>= 1) far2 = fmaxf(far2, __shfl_xor_sync(0xffffffffu, far2, o));
-    const float span = __fadd_ru(__fsqrt_ru(rhoQ2), __fsqrt_ru(far2));
-    const bool expanded =
-        (float)(D + 3) * 5.9604645e-08f * span * span * inv2h2_up[hidx] <= kExpandedErr;
-    // Stage references [j0, j0 + tn) of the run's concatenated point list,
-    // padded with a far point to an even count; entry by entry.
-    auto stage = [&](int j0, int tn) {
-      const int tn2 = (tn + 1) & ~1;
-      __syncwarp();
-      int base = 0;
-      for (int u = t; u < e; ++u) {
-        const int rn_u = __shfl_sync(0xffffffffu, my_rn, u);
-        const int rb_u = __shfl_sync(0xffffffffu, my_rb, u);
-        const int lo = max(j0 - base, 0), hi = min(j0 + tn - base, rn_u);
-        for (int jj = lo + lane; jj < hi; jj += 32) {
-          float rv[D];
-          load_point<D>(R.pts + (size_t)(rb_u + jj) * R.dp, rv);
-          const int j = base + jj - j0;
-          if (expanded) {
-            float b2 = 0.f;
+    cp_async_commit();
+  };
+
+  // current segment: run [t, e) (table slot ts), query block qs, tile j0
+  int t = 0, e = run_end(0), ts = 0, qs = 0, j0 = 0;
+  int tot = build_table(t, e, ts);
+  issue(ts, e - t, 0, min(TILE, tot));
+  // run parameters (warp-uniform), refreshed when the run changes
+  float c2r = 0.f, m_[D];
+  int qb = 0, qn = 0, hidx = 0;
+  bool expanded = false;
+  bool new_run = true;
+  int g = 32, ngrp = 1, ql = 0, gid = 0, qcnt_blk = 0;
+  while (true) {
+    if (new_run) {
+      c2r = __shfl_sync(FULL, c2, t);
+      qb = __shfl_sync(FULL, qbeg, t);
+      qn = __shfl_sync(FULL, qcnt, t);
+      hidx = __shfl_sync(FULL, key, t) / Q.nn;
 #pragma unroll
-            for (int k = 0; k < D; ++k) {
-              const float rt = rv[k] - mc[k];
-              sR[wib][k][j] = rt;
-              b2 = fmaf(rt, rt, b2);
-            }
-            sR[wib][D][j] = c2 * b2;
-          } else {
+      for (int k = 0; k < D; ++k) m_[k] = __shfl_sync(FULL, mc[k], t);
+      const float rq2 = __shfl_sync(FULL, rho2, t);
+      const float f2 = __uint_as_float(
+          __reduce_max_sync(FULL, (lane >= t && lane < e) ? __float_as_uint(far2) : 0u));
+      const float span = __fadd_ru(__fsqrt_ru(rq2), __fsqrt_ru(f2));
+      const float ui = (float)(D + 4) * 5.9604645e-08f * __shfl_sync(FULL, i2h, t);
+      expanded = ui * span * span <= kExpandedErr || 8.f * ui * rq2 <= kExpandedErr;
+      if (expanded && lane == 0) atomicAdd(exp_ctr, (unsigned long long)qn * tot);
+      new_run = false;
+    }
+    if (j0 == 0) {
+      // a new query block: stage its queries (W and A, or the point) and clear its sums
+      qcnt_blk = min(kQCap, qn - qs);
+      g = pick_group(qcnt_blk, tot);
+      ngrp = 32 / g;
+      ql = lane % g;
+      gid = lane / g;
+      for (int qi = lane; qi < qcnt_blk; qi += 32) {
+        float v[D];
+        load_point<D>(Q.pts + (size_t)(qb + qs + qi) * Q.dp, v);
+        float f[4 * QV];
 #pragma unroll
-            for (int k = 0; k < D; ++k) sR[wib][k][j] = -rv[k];
-          }
-        }
-        base += rn_u;
-      }
-      if (lane == 0 && tn2 > tn) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) sR[wib][k][tn] = expanded ? 0.f : kFarNeg;
-        sR[wib][D][tn] = -1.0e30f;
-      }
-      __syncwarp();
-      return tn2;
-    };
-    const bool one_tile = tot <= TILE;
-    const int staged2 = one_tile ? stage(0, tot) : 0;
-    const float2 c2p = make_float2(c2, c2);
-    // every lane holds queries q0 + ql and q0 + g + ql
-    for (int q0 = 0; q0 < qn; q0 += 2 * g) {
-      const int qia = q0 + ql, qib = q0 + g + ql;
-      const bool oka = qia < qn, okb = qib < qn;
-      float2 wqa[D], wqb[D], aa, ab;
-      {
-        float va[D], vb[D];
-        if (oka) load_point<D>(Q.pts + (size_t)(qb + qia) * Q.dp, va);
-        else
-#pragma unroll
-          for (int k = 0; k < D; ++k) va[k] = mc[k];
-        if (okb) load_point<D>(Q.pts + (size_t)(qb + qib) * Q.dp, vb);
-        else
-#pragma unroll
-          for (int k = 0; k < D; ++k) vb[k] = mc[k];
-        float a2 = 0.f, b2 = 0.f;
+        for (int i = 0; i < 4 * QV; ++i) f[i] = 0.f;
+        float a2 = 0.f;
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-          const float ta = va[k] - mc[k], tb = vb[k] - mc[k];
-          a2 = fmaf(ta, ta, a2);
-          b2 = fmaf(tb, tb, b2);
-          const float wa = expanded ? -2.f * c2 * ta : va[k];
-          const float wb = expanded ? -2.f * c2 * tb : vb[k];
-          wqa[k] = make_float2(wa, wa);
-          wqb[k] = make_float2(wb, wb);
+          const float tq = v[k] - m_[k];
+          a2 = fmaf(tq, tq, a2);
+          f[k] = expanded ? -2.f * c2r * tq : v[k];
         }
-        aa = make_float2(c2 * a2, c2 * a2);
-        ab = make_float2(c2 * b2, c2 * b2);
+        f[D] = c2r * a2;
+#pragma unroll
+        for (int i = 0; i < QV; ++i) sQ[wib][qi * QV + i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+        sAcc[wib][qi] = make_float2(0.f, 0.f);
+      }
+    }
+    const int tn = min(TILE, tot - j0);
+    // reference pairs, padded with zero-weight pairs to a multiple of the
+    // lane groups so that every lane runs the same number of steps
+    const int np2 = (((tn + 1) >> 1) + ngrp - 1) / ngrp * ngrp;
+    cp_async_wait_all();
+    __syncwarp();
+    // interleave: lane per reference pair
+    for (int jp = lane; jp < np2; jp += 32) {
+      const bool has_a = 2 * jp < tn, has_b = 2 * jp + 1 < tn;
+      float a[D], b[D];
+#pragma unroll
+      for (int k = 0; k < D; ++k) a[k] = b[k] = 0.f;
+      if (has_a) load_raw<D>(&sRaw[wib][(2 * jp) * RAW], a);
+      if (has_b) load_raw<D>(&sRaw[wib][(2 * jp + 1) * RAW], b);
+      float f[4 * NV];
+#pragma unroll
+      for (int i = 0; i < 4 * NV; ++i) f[i] = 0.f;
+      if (expanded) {
+        float ba = 0.f, bb = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          const float ra = has_a ? a[k] - m_[k] : 0.f, rbv = has_b ? b[k] - m_[k] : 0.f;
+          f[2 * k] = ra;
+          f[2 * k + 1] = rbv;
+          ba = fmaf(ra, ra, ba);
+          bb = fmaf(rbv, rbv, bb);
+        }
+        f[2 * D] = has_a ? c2r * ba : -1.0e30f;
+        f[2 * D + 1] = has_b ? c2r * bb : -1.0e30f;
+      } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          f[2 * k] = has_a ? -a[k] : kFarNeg;
+          f[2 * k + 1] = has_b ? -b[k] : kFarNeg;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+        sT[wib][jp * NV + v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+    }
+    __syncwarp();
+    // prefetch the next segment: next tile, else next query block, else next run
+    int nt = t, ne = e, nts = ts, nqs = qs, nj0 = j0 + TILE, ntot = tot;
+    const bool last_tile = nj0 >= tot;
+    if (last_tile) {
+      nj0 = 0;
+      nqs = qs + kQCap;
+      if (nqs >= qn) {
+        nqs = 0;
+        nt = e;
+        if (nt < m) {
+          ne = run_end(nt);
+          nts = ts ^ 1;
+          ntot = build_table(nt, ne, nts);
+        }
+      }
+    }
+    if (nt < m) issue(nts, ne - nt, nj0, min(TILE, ntot - nj0));
+
+    // sum this tile for every query of the block, into the block's sums
+    const float2 c2p = make_float2(c2r, c2r);
+    for (int q0 = 0; q0 < qcnt_blk; q0 += 2 * g) {
+      const int qia = q0 + ql, qib = q0 + g + ql;
+      const bool oka = qia < qcnt_blk, okb = qib < qcnt_blk;
+      float2 wqa[D], wqb[D];
+      {
+        float fa[4 * QV], fb[4 * QV];
+#pragma unroll
+        for (int i = 0; i < QV; ++i) {
+          const float4 va = sQ[wib][(oka ? qia : 0) * QV + i];
+          const float4 vb = sQ[wib][(okb ? qib : 0) * QV + i];
+          fa[4 * i] = va.x; fa[4 * i + 1] = va.y; fa[4 * i + 2] = va.z; fa[4 * i + 3] = va.w;
+          fb[4 * i] = vb.x; fb[4 * i + 1] = vb.y; fb[4 * i + 2] = vb.z; fb[4 * i + 3] = vb.w;
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          wqa[k] = make_float2(fa[k], fa[k]);
+          wqb[k] = make_float2(fb[k], fb[k]);
+        }
       }
       float Sa = 0.f, Ca = 0.f, Sb = 0.f, Cb = 0.f;
-      for (int j0 = 0; j0 < tot; j0 += TILE) {
-        const int tn2 = one_tile ? staged2 : stage(j0, min(TILE, tot - j0));
-        if (expanded)
-          base_tile_sums<D, true, TILE>(sR[wib], tn2, gid, 2 * ngrp, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
-        else
-          base_tile_sums<D, false, TILE>(sR[wib], tn2, gid, 2 * ngrp, wqa, wqb, aa, ab, c2p, Sa, Ca, Sb, Cb);
-      }
+      if (expanded)
+        base_tile_sums<D, true>(sT[wib], np2, gid, ngrp, wqa, wqb, c2p, Sa, Ca, Sb, Cb);
+      else
+        base_tile_sums<D, false>(sT[wib], np2, gid, ngrp, wqa, wqb, c2p, Sa, Ca, Sb, Cb);
       float va = Sa - Ca, vb = Sb - Cb;
       for (int o = g; o < 32; o <<= 1) {
-        va += __shfl_xor_sync(0xffffffffu, va, o);
-        vb += __shfl_xor_sync(0xffffffffu, vb, o);
+        va += __shfl_xor_sync(FULL, va, o);
+        vb += __shfl_xor_sync(FULL, vb, o);
       }
-      if (gid == 0 && oka) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qia], (double)va);
-      if (gid == 0 && okb) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qib], (double)vb);
+      if (gid == 0 && oka) {
+        float2 acc = sAcc[wib][qia];
+        kahan_add(acc.x, acc.y, va);
+        sAcc[wib][qia] = acc;
+      }
+      if (gid == 0 && okb) {
+        float2 acc = sAcc[wib][qib];
+        kahan_add(acc.x, acc.y, vb);
+        sAcc[wib][qib] = acc;
+      }
     }
-    t = e;
+    if (last_tile) {
+      // the block's sums, scaled by 2^A_q in the expanded form, one atomic per query
+      __syncwarp();
+      for (int qi = lane; qi < qcnt_blk; qi += 32) {
+        const float2 acc = sAcc[wib][qi];
+        float v = acc.x - acc.y;
+        if (expanded) v *= exp2f(reinterpret_cast<const float*>(&sQ[wib][qi * QV])[D]);
+        atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qs + qi], (double)v);
+      }
+    }
+    __syncwarp();
+    if (nt >= m) break;
+    if (nt != t) new_run = true;
+    t = nt;
+    e = ne;
+    ts = nts;
+    qs = nqs;
+    j0 = nj0;
+    tot = ntot;
   }
 }
 
@@ -494,104 +705,197 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
 // AccumulateDirectLocalMoment:
 // L_beta(Q) += ((-1)^{|beta|}/beta!) sum_{r in R} h_beta((Q.c - r)/sqrt(2h^2)).
 // The list is sorted by (bandwidth, query node) like the base case, and a
-// warp takes kBaseChunk consecutive sorted entries: every run of one query
-// node accumulates its coefficients in registers (lane per coefficient
-// position) and adds them to L once.  For each batch of 32 reference points
-// each lane tabulates the 1-D Hermite functions of one point in shared
-// memory, then every lane sums its coefficient over the batch; batches are
-// summed in float32 and added in float64.  An entry of order p contributes
-// only to beta < p.
+// warp takes kEntryChunk consecutive sorted entries, one per lane; a run of
+// one query node is one concatenated list of references, taken in batches
+// of 32 (one per lane, the next batch's point loaded while the current one
+// is summed).  The coefficient sum_r prod_k h_{beta_k}(t_rk) factors over
+// dimensions, so a lane owns the coefficients of one prefix (beta_0 ..
+// beta_{D-B-1}) and all PM^B values of the last B digits: per reference it
+// forms the prefix product once and multiplies it out over the block, with
+// the 1-D Hermite rows tabulated in shared memory by the reference's lane.
+// Lanes of one prefix split the batch into streams, reduced at the end of
+// the run; each lane's batch sums are Kahan-compensated.  An entry of order
+// p contributes only to beta < p: its rows are zero past p.
 template <int D>
-__global__ void __launch_bounds__(kT) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
-                                              const int* __restrict__ ksorted, int n,
-                                              const float* __restrict__ sfv,
-                                              double* __restrict__ L, int* __restrict__ pused) {
-  constexpr int PM = pmax_of(D);
-  constexpr int P = ipow_c(PM, D);
+struct LocalShape {
+  static constexpr int PM = pmax_of(D);
+  static constexpr int P = ipow_c(PM, D);
+  static constexpr int B = D <= 2 ? 1 : 2;             // block digits
+  static constexpr int NB = ipow_c(PM, B);             // coefficients per lane
+  static constexpr int NPRE = ipow_c(PM, D - B);       // prefixes
+  static constexpr int NSTR = 32 / NPRE;               // streams per prefix
+};
+
+template <int D>
+__global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
+                                                 const int* __restrict__ ksorted, int n,
+                                                 const float* __restrict__ sfv,
+                                                 double* __restrict__ L, int* __restrict__ pused) {
+  using LS = LocalShape<D>;
+  constexpr int PM = LS::PM, P = LS::P, B = LS::B, NB = LS::NB, NPRE = LS::NPRE, NSTR = LS::NSTR;
+  constexpr int NB2 = NB / 2;
   constexpr int S = (P + 31) / 32;
-  __shared__ float sH[kWarpsPerBlock][32][D][PM];
+  constexpr int kFlush = 8;  // batches between compensated additions
+  __shared__ __align__(16) float sH[kWarpsPerBlock][32][D][PM];
+  __shared__ float sRed[kWarpsPerBlock][NSTR][P];
+  __shared__ int sOff[kWarpsPerBlock][33], sRb[kWarpsPerBlock][32], sRp[kWarpsPerBlock][32];
+  const unsigned FULL = 0xffffffffu;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
+  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kEntryChunk;
   if (i0 >= n) return;
-  const int m = (int)min((long)kBaseChunk, n - i0);
-  int my_key = -1, my_r = 0, my_p = 0;
+  const int m = (int)min((long)kEntryChunk, n - i0);
+  int key = -1 - lane, rb = 0, rn = 0, rp = 0;
   if (lane < m) {
-    my_key = ksorted[i0 + lane];
+    key = ksorted[i0 + lane];
     const int v = rsorted[i0 + lane];
-    my_r = v & kNodeMask;
-    my_p = v >> kNodeBits;
+    const int r = v & kNodeMask;
+    rp = v >> kNodeBits;
+    rb = R.beg[r];
+    rn = R.cnt[r];
   }
-  int al[S][D];
-  double fsign[S];
+  const int keyp = __shfl_up_sync(FULL, key, 1);
+  const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
+  // this lane's prefix, stream and prefix digits
+  const int pre = lane % NPRE, str = lane / NPRE;
+  int pd[D - B > 0 ? D - B : 1];
+  {
+    int v = pre;
 #pragma unroll
-  for (int sl = 0; sl < S; ++sl) {
-    int v = lane + 32 * sl, ab = 0;
-    double f = 1.0;
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) { al[sl][k] = v % PM; v /= PM; ab += al[sl][k]; f *= fact_d(al[sl][k]); }
-    fsign[sl] = ((ab & 1) ? -1.0 : 1.0) / f;
+    for (int k = D - B - 1; k >= 0; --k) { pd[k] = v % PM; v /= PM; }
   }
   int t = 0;
   while (t < m) {
-    const int key = __shfl_sync(0xffffffffu, my_key, t);
-    int e = t + 1;
-    while (e < m && __shfl_sync(0xffffffffu, my_key, e) == key) ++e;
-    const int hidx = key / Q.nn, q = key % Q.nn;
+    const unsigned later = starts & ~((2u << t) - 1u);
+    const int e = later ? __ffs(later) - 1 : m;
+    const int key_t = __shfl_sync(FULL, key, t);
+    const int hidx = key_t / Q.nn, q = key_t - hidx * Q.nn;
     const float sf = sfv[hidx];
     CenterHL cQ[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, q, k);
-    float accS[S], accC[S];
+    // the run's entries t..e-1 as a table: offset in the concatenated list,
+    // first point, order
+    const int in_run = (lane >= t && lane < e) ? rn : 0;
+    int incl = in_run;
 #pragma unroll
-    for (int sl = 0; sl < S; ++sl) accS[sl] = accC[sl] = 0.f;
-    int prun = 0;
-    for (int u = t; u < e; ++u) {
-      const int r = __shfl_sync(0xffffffffu, my_r, u);
-      const int p = __shfl_sync(0xffffffffu, my_p, u);
-      prun = max(prun, p);
-      const int rb = R.beg[r], rn = R.cnt[r];
-      for (int j0 = 0; j0 < rn; j0 += 32) {
-        const int j = j0 + lane;
-        if (j < rn) {
-          float rv[D];
-          load_point<D>(R.pts + (size_t)(rb + j) * R.dp, rv);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int tot = __shfl_sync(FULL, incl, 31);
+    const int prun = __reduce_max_sync(FULL, (lane >= t && lane < e) ? rp : 0);
+    if (lane >= t && lane < e) {
+      sOff[wib][lane - t] = incl - in_run;
+      sRb[wib][lane - t] = rb;
+      sRp[wib][lane - t] = rp;
+    }
+    if (lane == 0) sOff[wib][e - t] = tot;
+    __syncwarp();
+    // reference J of the run (J advances by 32 per batch, so a cursor over
+    // the table moves forward only)
+    int cur = 0;
+    auto fetch = [&](int J, float* pv, int& pp) {
+      if (J < tot) {
+        while (sOff[wib][cur + 1] <= J) ++cur;
+        pp = sRp[wib][cur];
+        load_point<D>(R.pts + (size_t)(sRb[wib][cur] + J - sOff[wib][cur]) * R.dp, pv);
+      } else {
+        pp = 0;
 #pragma unroll
-          for (int k = 0; k < D; ++k) hermite_f32<PM>(-minus_center(rv[k], cQ[k]) * sf, sH[wib][lane][k]);
-        } else {
+        for (int k = 0; k < D; ++k) pv[k] = 0.f;
+      }
+    };
+    float2 accS[NB2], accC[NB2], blk[NB2];
 #pragma unroll
-          for (int k = 0; k < D; ++k)
+    for (int i = 0; i < NB2; ++i) accS[i] = accC[i] = blk[i] = make_float2(0.f, 0.f);
+    float pv[D];
+    int pp = 0;
+    fetch(lane, pv, pp);
+    int nb = 0;
+    for (int j0 = 0; j0 < tot; j0 += 32) {
+      // tabulate this lane's reference: h_e((Q.c - r) s) for e < p, 0 beyond
 #pragma unroll
-            for (int e2 = 0; e2 < PM; ++e2) sH[wib][lane][k][e2] = 0.f;
-        }
-        __syncwarp();
+      for (int k = 0; k < D; ++k) {
+        float H[PM];
+        hermite_f32<PM>(-minus_center(pv[k], cQ[k]) * sf, H);
 #pragma unroll
-        for (int sl = 0; sl < S; ++sl) {
-          const int idx = lane + 32 * sl;
-          bool ok = idx < P;
+        for (int e2 = 0; e2 < PM; e2 += 2)
+          *reinterpret_cast<float2*>(&sH[wib][lane][k][e2]) =
+              make_float2(e2 < pp ? H[e2] : 0.f, e2 + 1 < pp ? H[e2 + 1] : 0.f);
+      }
+      __syncwarp();
+      float nv[D];
+      int np = 0;
+      if (j0 + 32 < tot) fetch(j0 + 32 + lane, nv, np);
+      // this lane's stream: references str, str + NSTR, ...
+      if (str < NSTR) {
+        for (int j = str; j < 32; j += NSTR) {
+          float pr = 1.f;
 #pragma unroll
-          for (int k = 0; k < D; ++k) ok = ok && al[sl][k] < p;
-          if (ok) {
-            float part = 0.f;
-            for (int jj = 0; jj < 32; ++jj) {
-              float tt = sH[wib][jj][0][al[sl][0]];
+          for (int k = 0; k < D - B; ++k) pr *= sH[wib][j][k][pd[k]];
+          const float2* hl = reinterpret_cast<const float2*>(&sH[wib][j][D - 1][0]);
+          if constexpr (B == 1) {
+            const float2 p2 = make_float2(pr, pr);
 #pragma unroll
-              for (int k = 1; k < D; ++k) tt *= sH[wib][jj][k][al[sl][k]];
-              part += tt;
+            for (int i = 0; i < NB2; ++i) blk[i] = __ffma2_rn(p2, hl[i], blk[i]);
+          } else {
+#pragma unroll
+            for (int e1 = 0; e1 < PM; ++e1) {
+              const float t1 = pr * sH[wib][j][D - 2][e1];
+              const float2 t2 = make_float2(t1, t1);
+#pragma unroll
+              for (int i = 0; i < PM / 2; ++i)
+                blk[e1 * (PM / 2) + i] = __ffma2_rn(t2, hl[i], blk[e1 * (PM / 2) + i]);
             }
-            kahan_add(accS[sl], accC[sl], part);
           }
         }
-        __syncwarp();
+      }
+      if (++nb == kFlush || j0 + 32 >= tot) {
+        nb = 0;
+#pragma unroll
+        for (int i = 0; i < NB2; ++i) {
+          kahan_add(accS[i].x, accC[i].x, blk[i].x);
+          kahan_add(accS[i].y, accC[i].y, blk[i].y);
+          blk[i] = make_float2(0.f, 0.f);
+        }
+      }
+      __syncwarp();
+      if (j0 + 32 < tot) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) pv[k] = nv[k];
+        pp = np;
       }
     }
+    // streams -> coefficients
+    if (str < NSTR) {
+#pragma unroll
+      for (int i = 0; i < NB2; ++i) {
+        sRed[wib][str][pre * NB + 2 * i] = accS[i].x - accC[i].x;
+        sRed[wib][str][pre * NB + 2 * i + 1] = accS[i].y - accC[i].y;
+      }
+    }
+    __syncwarp();
     const size_t hq = (size_t)hidx * Q.nn + q;
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
       const int idx = lane + 32 * sl;
-      const double v = (double)accS[sl] - (double)accC[sl];
-      if (idx < P && v != 0.0) atomicAdd(&L[hq * P + idx], v * fsign[sl]);
+      if (idx < P) {
+        float cs = 0.f, cc = 0.f;
+#pragma unroll
+        for (int st = 0; st < NSTR; ++st) kahan_add(cs, cc, sRed[wib][st][idx]);
+        const double v = (double)cs - (double)cc;
+        if (v != 0.0) {
+          int ab = 0;
+          double f = 1.0;
+          int w = idx;
+#pragma unroll
+          for (int k = D - 1; k >= 0; --k) { const int a = w % PM; w /= PM; ab += a; f *= fact_d(a); }
+          atomicAdd(&L[hq * P + idx], ((ab & 1) ? -v : v) / f);
+        }
+      }
     }
     if (lane == 0) atomicMax(&pused[hq], prun);
+    __syncwarp();
     t = e;
   }
 }
@@ -948,11 +1252,14 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
   int *rsorted, *ksorted;
   cudaError_t e = sort_by_query(list, n, Q.nn, b.nh, sc, s, launches, &rsorted, &ksorted);
   if (e != cudaSuccess) return e;
-  const long warps = (n + kBaseChunk - 1) / kBaseChunk;
-  const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
   if (Q.d <= 5) {
-    DISPATCH_D(Q.d, k_base<DD><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc));
+    const long warps = (n + kEntryChunk - 1) / kEntryChunk;
+    const int g = (int)((warps + kBaseWarps - 1) / kBaseWarps);
+    DISPATCH_D(Q.d, k_base<DD><<<g, kBaseWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up,
+                                                              b.gacc, b.base_exp));
   } else {
+    const long warps = (n + kBaseChunk - 1) / kBaseChunk;
+    const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
     k_base_g<<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc);
   }
   ++*launches;
@@ -980,7 +1287,7 @@ cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers
     cudaError_t e = sort_by_query(reinterpret_cast<const Pair*>(list), n, Q.nn, b.nh, sc, s, launches,
                                   &vsorted, &ksorted);
     if (e != cudaSuccess) return e;
-    const long warps = (n + kBaseChunk - 1) / kBaseChunk;
+    const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
     DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, vsorted, ksorted, n, b.sf, b.L, b.pused));
   } else {

@@ -44,6 +44,7 @@ dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, doubl
   const TreeView Q = qt->view();
   CK(launch_post(Q, qt->leaves, qt->nleaves, b, G_dev, s));
   ++ctx->launches;
+  CK(cudaMemcpyAsync(ctx->h_counters, ctx->counters.p, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
   CK(cudaEventRecord(ctx->ev[3], s));
   CK(cudaStreamSynchronize(s));
   if (st) {
@@ -106,6 +107,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->inv_2h_up = fl + 2 * nh;
   b->c2 = fl + 3 * nh;
   b->sf = fl + 4 * nh;
+  b->base_exp = &ctx->counters.as<RoundCounters>()->base_exp;
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
@@ -113,6 +115,8 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->inv_fix = 1.0 / b->fix_scale;
   b->fix_scale_dn = std::nextafter((float)b->fix_scale, 0.f);
   b->inv_nr = 1.0 / (double)rt->n;
+  // tau = eps_eff |R| G^l / |R_total| with G^l = lb |R_total| 2^-62
+  b->tau_scale_dn = std::nextafter((float)std::ldexp(eps_eff, -62), 0.f);
   b->p_limit = std::min(qt->p_limit, rt->p_limit);
   return DFGT_OK;
 }
@@ -282,6 +286,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     st->n_local = lists[2].total;
     st->n_f2l = lists[3].total;
     st->base_interactions = (long long)hc->base_inter;
+    st->base_expanded = (long long)hc->base_exp;
     st->rounds = rounds;
     st->list_flushes = flushes;
     float ms = 0.f;

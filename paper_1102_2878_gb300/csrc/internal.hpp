@@ -69,6 +69,7 @@ struct RoundCounters {
   int n_far, n_loc, n_f2l, n_base;   // cumulative list lengths
   unsigned long long n_prune;        // cumulative prune count
   unsigned long long base_inter;     // cumulative sum |Q||R| over base pairs
+  unsigned long long base_exp;       // base interactions summed in the expanded form
 };
 
 struct dfgt_ctx {
@@ -172,6 +173,8 @@ struct TravBuffers {
   const float* inv_2h_up;  // [nh] 1/(2h) rounded up
   const float* c2;       // [nh] -log2(e)/(2h^2) as float, the exp2 scale of exact sums
   const float* sf;       // [nh] 1/sqrt(2h^2) as float, the expansion scale
+  unsigned long long* base_exp;  // device counter of expanded-form base interactions
+  float tau_scale_dn;    // eps_eff / (fix_scale |R_total|) as float, rounded down
   float* ku;        // [frontier] lower bound on K(d^u) of each pending pair
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums

@@ -36,9 +36,24 @@ constexpr float kMaxSummaryPoints = 4096.f;
 constexpr int kSlotBits = 28;  // frontier slots stay below 2^28 (checked by the host)
 constexpr int kSplitROnly = 1, kSplitQOnly = 2;
 
+// Truncation of a non-negative float below 2^64 to an integer, by shifting
+// its significand (integer instructions only).
+__device__ __forceinline__ u64 f2u64_rz(float x) {
+  const unsigned bits = __float_as_uint(x);
+  const int e = (int)(bits >> 23) - 127;  // x = 1.m 2^e
+  if (e < 0) return 0;
+  const u64 m = (u64)((bits & 0x7fffffu) | 0x800000u);
+  return e >= 23 ? m << (e - 23) : m >> (23 - e);
+}
+
+// A u64 as a float, rounded down.
+__device__ __forceinline__ float u64_to_f_rd(u64 v) {
+  return __fmaf_rd(__uint2float_rd((unsigned)(v >> 32)), 4294967296.f, __uint2float_rd((unsigned)v));
+}
+
 // Fixed-point units of a lower bound (rounded down).
 __device__ __forceinline__ u64 to_fix_f(float nR, float K, float scale_dn) {
-  return __float2ull_rz(__fmul_rd(__fmul_rd(nR, K), scale_dn));
+  return f2u64_rz(__fmul_rd(__fmul_rd(nR, K), scale_dn));
 }
 
 // FarFieldOrder / LocalAccumulationOrder: least p <= plim whose truncation
@@ -65,26 +80,21 @@ __device__ int order_t(float r, float nR, int D, float tau, int plim) {
   return plim;
 }
 
-// All 32 lanes call this; returns the first slot of this lane's n items.
-__device__ __forceinline__ int warp_alloc(int* counter, int n) {
-  const int lane = threadIdx.x & 31;
-  int incl = n;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const int total = __shfl_sync(0xffffffffu, incl, 31);
-  int base = 0;
-  if (lane == 31 && total > 0) base = atomicAdd(counter, total);
-  base = __shfl_sync(0xffffffffu, base, 31);
-  return base + incl - n;
-}
-
-__device__ __forceinline__ void warp_add_u64(unsigned long long* counter, unsigned long long v) {
+// Block-wide sum added with one atomic (every thread of the block calls it;
+// scratch holds one word per warp).
+__device__ __forceinline__ void warp_add_u64_block(unsigned long long* counter, unsigned long long v,
+                                                   u64* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0 && v) atomicAdd(counter, v);
+  __syncthreads();
+  if (lane == 0) scratch[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    u64 t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += scratch[w];
+    if (t) atomicAdd(counter, t);
+  }
 }
 
 __global__ void k_fold(u64* __restrict__ decided, u64* __restrict__ incr, u64* __restrict__ lbsum,
@@ -132,6 +142,10 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
   const int d = D > 0 ? D : Q.d;
   const int P = Q.P;
   const int stride = gridDim.x * kT;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ u64 sWarp[kT / 32];
+  __shared__ int sBase[5];
+  unsigned long long my_prune = 0, my_inter = 0;
   for (int i0 = blockIdx.x * kT; i0 < nF; i0 += stride) {
     const int i = i0 + threadIdx.x;
     // kind: -1 none, 0 prune, 1 F, 2 D, 3 T, 4 base, 5 recurse
@@ -141,20 +155,25 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
     if (i < nF) {
       pr = F[i];
       const size_t hq = (size_t)pr.h * Q.nn + pr.q;
-      const float nQ = (float)Q.cnt[pr.q], nR = (float)R.cnt[pr.r];
+      const int cQ = Q.cnt[pr.q], cR = R.cnt[pr.r];
+      const float nQ = (float)cQ, nR = (float)cR;
       float dl2, du2, sideQ, sideR;
       box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
       const float Kl = kernel_upper(dl2, b.inv2h2_dn[pr.h]);
       const float Ku = b.ku[i];
       const u64 lbf = b.inherited[hq] + b.decided[hq] + b.lbsum[hq];
       // tau = eps |R| G^l(Q) / |R_total| (CanSummarize), rounded down
-      const float tau = __double2float_rd(b.eps_eff * (double)nR * ((double)lbf * b.inv_fix) * b.inv_nr);
+      const float tau = __fmul_rd(__fmul_rd(b.tau_scale_dn, nR), u64_to_f_rd(lbf));
       // prune: the kernel over the pair lies in [Ku, Kl]; the midpoint is off by
-      // at most half the width
-      const float err_prune = __fmul_ru(0.5f * nR, __fsub_ru(Kl, Ku));
+      // at most half the width, plus the float32 rounding of the midpoint
+      // value itself (two roundings, covered by 4u of it)
+      const float halfR = 0.5f * nR;
+      const float value = halfR * (Kl + Ku);
+      const float err_prune = __fadd_ru(__fmul_ru(halfR, __fsub_ru(Kl, Ku)),
+                                        __fmul_ru(__fmul_ru(halfR, __fadd_ru(Kl, Ku)), 2.4e-7f));
       if (err_prune <= tau) {
         kind = 0;
-        atomicAdd(&b.L[hq * P], (double)(0.5f * nR) * ((double)Kl + (double)Ku));
+        atomicAdd(&b.L[hq * P], (double)value);
         atomicMax(&b.pused[hq], 1);
       } else {
         int pF = 0, pD = 0, pT = 0;
@@ -178,9 +197,9 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
           // exact sum: at a leaf pair (DFGTBase), or for any pair small
           // enough that recursing further cannot pay (|Q||R| <= base_block)
           const int ql = Q.left[pr.q], rl = R.left[pr.r];
-          if ((ql < 0 && rl < 0) || (double)nQ * nR <= (double)b.base_block) {
+          if ((ql < 0 && rl < 0) || (long long)cQ * cR <= b.base_block) {
             kind = 4;
-            inter = (unsigned long long)(nQ * nR);
+            inter = (unsigned long long)cQ * (unsigned long long)cR;
           } else {
             kind = 5;
             nchild = (ql >= 0 && rl >= 0) ? 4 : 2;
@@ -204,26 +223,54 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
         if (f) atomicAdd(&b.incr[hq], f);
       }
     }
-    // warp-aggregated appends (all lanes take part); child pairs only get
+    // Block-aggregated appends: the five counts of each pair (children,
+    // F, D, T, base) packed in 12-bit fields of one word, one block-wide
+    // exclusive scan, one atomic per list and block step (atomics on the
+    // shared counters would otherwise serialise).  Child pairs only get
     // their slots here and are written by k_emit once the host has sized
-    // the next frontier
-    {
-      const int s0 = warp_alloc(&ctr->n_next, nchild);
-      if (i < nF) slot[i] = nchild ? (s0 | (split << kSlotBits)) : -1;
+    // the next frontier.
+    const u64 mine = (u64)nchild | ((u64)(kind == 1) << 12) | ((u64)(kind == 2) << 24) |
+                     ((u64)(kind == 3) << 36) | ((u64)(kind == 4) << 48);
+    u64 incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    {
-      const int s1 = warp_alloc(&ctr->n_far, kind == 1);
-      if (kind == 1) { if (s1 < cap_lists) far[s1] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
-      const int s2 = warp_alloc(&ctr->n_loc, kind == 2);
-      if (kind == 2) { if (s2 < cap_lists) loc[s2] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
-      const int s3 = warp_alloc(&ctr->n_f2l, kind == 3);
-      if (kind == 3) { if (s3 < cap_lists) f2l[s3] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
-      const int s4 = warp_alloc(&ctr->n_base, kind == 4);
-      if (kind == 4) { if (s4 < cap_lists) base[s4] = Pair{pr.q, pr.r, pr.h, 0}; else atomicOr(&ctr->status, kStOverflow); }
+    if (lane == 31) sWarp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      const u64 w = lane < kT / 32 ? sWarp[lane] : 0;
+      u64 ws = w;
+#pragma unroll
+      for (int o = 1; o < kT / 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws += y;
+      }
+      if (lane < kT / 32) sWarp[lane] = ws - w;
+      const u64 tot = __shfl_sync(0xffffffffu, ws, kT / 32 - 1);
+      if (lane < 5) {
+        int* const c = lane == 0 ? &ctr->n_next : lane == 1 ? &ctr->n_far : lane == 2 ? &ctr->n_loc
+                     : lane == 3 ? &ctr->n_f2l : &ctr->n_base;
+        const int n = (int)((tot >> (12 * lane)) & 0xfffu);
+        sBase[lane] = n ? atomicAdd(c, n) : 0;
+      }
     }
-    warp_add_u64(&ctr->n_prune, kind == 0 ? 1ull : 0ull);
-    warp_add_u64(&ctr->base_inter, inter);
+    __syncthreads();
+    const u64 ex = sWarp[wid] + incl - mine;
+    auto field = [&](int k) { return sBase[k] + (int)((ex >> (12 * k)) & 0xfffu); };
+    if (i < nF) slot[i] = nchild ? (field(0) | (split << kSlotBits)) : -1;
+    if (kind == 1) { const int s1 = field(1); if (s1 < cap_lists) far[s1] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
+    if (kind == 2) { const int s2 = field(2); if (s2 < cap_lists) loc[s2] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
+    if (kind == 3) { const int s3 = field(3); if (s3 < cap_lists) f2l[s3] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
+    if (kind == 4) { const int s4 = field(4); if (s4 < cap_lists) base[s4] = Pair{pr.q, pr.r, pr.h, 0}; else atomicOr(&ctr->status, kStOverflow); }
+    my_prune += kind == 0 ? 1ull : 0ull;
+    my_inter += inter;
+    __syncthreads();  // sWarp / sBase are reused by the next step
   }
+  // totals: one atomic per block
+  warp_add_u64_block(&ctr->n_prune, my_prune, sWarp);
+  warp_add_u64_block(&ctr->base_inter, my_inter, sWarp);
 }
 
 // Write the child pairs of every recursing pair at the slot reserved by
