@@ -157,9 +157,10 @@ constexpr int kPassCost = 16;
 __device__ __forceinline__ int pick_group(int qn, int tot) {
   const int pairs = (tot + 1) / 2;
   int best = 32, cost = 1 << 30;
-  for (int g = 32; g >= 1; g >>= 1) {
-    const int passes = (qn + 2 * g - 1) / (2 * g);
-    const int iters = (pairs + (32 / g) - 1) / (32 / g);
+  for (int lg = 5; lg >= 0; --lg) {  // g = 2^lg
+    const int g = 1 << lg;
+    const int passes = (qn + 2 * g - 1) >> (lg + 1);
+    const int iters = (pairs + (32 >> lg) - 1) >> (5 - lg);
     const int c = passes * (iters + kPassCost);
     if (c < cost) { cost = c; best = g; }
   }
@@ -188,13 +189,16 @@ __device__ __forceinline__ void kahan_add(float& S, float& C, float v) {
 
 // Shapes of the base-case tiles for dimension D: RAW floats per staged
 // reference (the tree's padded row), PAIRW floats per interleaved
-// reference pair (padded to whole float4s) and TILE references per warp.
+// reference pair (padded to whole float4s), SV float4 per pair slot (room
+// for both the two raw rows and the interleaved pair, so a pair is
+// rewritten in place) and TILE references per warp.
 template <int D>
 struct BaseShape {
   static constexpr int RAW = D <= 2 ? D : ((D + 3) & ~3);
   static constexpr int PAIRW = ((2 * (D + 1) + 3) / 4) * 4;
   static constexpr int NV = PAIRW / 4;
-  static constexpr int TILE = D == 1 ? 512 : D <= 3 ? 256 : 128;
+  static constexpr int SV = (2 * RAW > PAIRW ? 2 * RAW : PAIRW) / 4;
+  static constexpr int TILE = D == 1 ? 1024 : D <= 3 ? 512 : 256;
 };
 
 __device__ __forceinline__ void cp_async_row(float* dst, const float* src, int bytes) {
@@ -260,9 +264,11 @@ __device__ __forceinline__ void base_tile_sums(const float4* __restrict__ T, int
                                                const float2* wa, const float2* wb, float2 c2p,
                                                float& Sa, float& Ca, float& Sb, float& Cb) {
   constexpr int NV = BaseShape<D>::NV;
-  int left = np2 / ngrp;  // np2 is padded to a multiple of ngrp: the same count in every lane
-  const float4* p = T + gid * NV;
-  const int stride = ngrp * NV;
+  // np2 is padded to a multiple of ngrp (a power of two): the same count in every lane
+  int left = np2 >> (31 - __clz(ngrp));
+  constexpr int SV = BaseShape<D>::SV;
+  const float4* p = T + gid * SV;
+  const int stride = ngrp * SV;
   for (; left >= 16; left -= 16) {
     float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
 #pragma unroll
@@ -335,10 +341,11 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
            const float* __restrict__ c2v, const float* __restrict__ inv2h2_up, double* __restrict__ gacc,
            unsigned long long* __restrict__ exp_ctr) {
   using SH = BaseShape<D>;
-  constexpr int TILE = SH::TILE, RAW = SH::RAW, NV = SH::NV;
+  constexpr int TILE = SH::TILE, RAW = SH::RAW, NV = SH::NV, SV = SH::SV;
   constexpr int QV = (D + 1 + 3) / 4;  // float4 per staged query: W (or q) then A
-  __shared__ __align__(16) float sRaw[kBaseWarps][TILE * RAW];
-  __shared__ __align__(16) float4 sT[kBaseWarps][(TILE / 2) * NV];
+  // one tile per warp: raw rows land at the start of their pair slot and
+  // each pair is rewritten in place into the interleaved form
+  __shared__ __align__(16) float4 sT[kBaseWarps][(TILE / 2) * SV];
   __shared__ __align__(16) float4 sQ[kBaseWarps][kQCap * QV];
   __shared__ float2 sAcc[kBaseWarps][kQCap];
   __shared__ int sOff[kBaseWarps][2][kEntryChunk + 1];
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
         while (sOff[wib][sl][u + 1] <= J) ++u;
       }
       const float* src = R.pts + (size_t)(sRb[wib][sl][u] + J - sOff[wib][sl][u]) * RAW;
-      float* dst = &sRaw[wib][j * RAW];
+      float* dst = reinterpret_cast<float*>(&sT[wib][(j >> 1) * SV]) + (j & 1) * RAW;
       if constexpr (RAW * 4 <= 16) {
         cp_async_row(dst, src, RAW * 4);
       } else {
@@ -432,13 +439,12 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
   // current segment: run [t, e) (table slot ts), query block qs, tile j0
   int t = 0, e = run_end(0), ts = 0, qs = 0, j0 = 0;
   int tot = build_table(t, e, ts);
-  issue(ts, e - t, 0, min(TILE, tot));
   // run parameters (warp-uniform), refreshed when the run changes
   float c2r = 0.f, m_[D];
   int qb = 0, qn = 0, hidx = 0;
   bool expanded = false;
   bool new_run = true;
-  int g = 32, ngrp = 1, ql = 0, gid = 0, qcnt_blk = 0;
+  int g = 32, lgg = 5, ngrp = 1, ql = 0, gid = 0, qcnt_blk = 0;
   while (true) {
     if (new_run) {
       c2r = __shfl_sync(FULL, c2, t);
@@ -460,9 +466,10 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
       // a new query block: stage its queries (W and A, or the point) and clear its sums
       qcnt_blk = min(kQCap, qn - qs);
       g = pick_group(qcnt_blk, tot);
-      ngrp = 32 / g;
-      ql = lane % g;
-      gid = lane / g;
+      lgg = 31 - __clz(g);
+      ngrp = 32 >> lgg;
+      ql = lane & (g - 1);
+      gid = lane >> lgg;
       for (int qi = lane; qi < qcnt_blk; qi += 32) {
         float v[D];
         load_point<D>(Q.pts + (size_t)(qb + qs + qi) * Q.dp, v);
@@ -485,7 +492,8 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
     const int tn = min(TILE, tot - j0);
     // reference pairs, padded with zero-weight pairs to a multiple of the
     // lane groups so that every lane runs the same number of steps
-    const int np2 = (((tn + 1) >> 1) + ngrp - 1) / ngrp * ngrp;
+    const int np2 = (((tn + 1) >> 1) + ngrp - 1) & ~(ngrp - 1);
+    issue(ts, e - t, j0, tn);
     cp_async_wait_all();
     __syncwarp();
     // interleave: lane per reference pair
@@ -494,8 +502,9 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
       float a[D], b[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) a[k] = b[k] = 0.f;
-      if (has_a) load_raw<D>(&sRaw[wib][(2 * jp) * RAW], a);
-      if (has_b) load_raw<D>(&sRaw[wib][(2 * jp + 1) * RAW], b);
+      const float* slot = reinterpret_cast<const float*>(&sT[wib][jp * SV]);
+      if (has_a) load_raw<D>(slot, a);
+      if (has_b) load_raw<D>(slot + RAW, b);
       float f[4 * NV];
 #pragma unroll
       for (int i = 0; i < 4 * NV; ++i) f[i] = 0.f;
@@ -520,10 +529,10 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v)
-        sT[wib][jp * NV + v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
+        sT[wib][jp * SV + v] = make_float4(f[4 * v], f[4 * v + 1], f[4 * v + 2], f[4 * v + 3]);
     }
     __syncwarp();
-    // prefetch the next segment: next tile, else next query block, else next run
+    // the next segment: next tile, else next query block, else next run
     int nt = t, ne = e, nts = ts, nqs = qs, nj0 = j0 + TILE, ntot = tot;
     const bool last_tile = nj0 >= tot;
     if (last_tile) {
@@ -539,7 +548,6 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
         }
       }
     }
-    if (nt < m) issue(nts, ne - nt, nj0, min(TILE, ntot - nj0));
 
     // sum this tile for every query of the block, into the block's sums
     const float2 c2p = make_float2(c2r, c2r);
