@@ -198,7 +198,7 @@ struct BaseShape {
   static constexpr int PAIRW = ((2 * (D + 1) + 3) / 4) * 4;
   static constexpr int NV = PAIRW / 4;
   static constexpr int SV = (2 * RAW > PAIRW ? 2 * RAW : PAIRW) / 4;
-  static constexpr int TILE = D == 1 ? 1024 : D <= 3 ? 512 : 256;
+  static constexpr int TILE = D == 1 ? 1024 : D == 2 ? 512 : D == 3 ? 448 : 192;
 };
 
 __device__ __forceinline__ void cp_async_row(float* dst, const float* src, int bytes) {
@@ -333,7 +333,7 @@ __device__ __forceinline__ void load_raw(const float* row, float* a) {
 //    kExpandedErr + 2 (D+4) u x per term.  Otherwise the direct form.
 constexpr float kExpandedErr = 5e-6f;
 
-constexpr int kQCap = 64;  // queries of a run staged at a time
+constexpr int kQCap = 128;  // queries of a run staged at a time
 
 template <int D>
 __global__ void __launch_bounds__(kBaseWarps * 32, 5)
@@ -670,6 +670,58 @@ __device__ __forceinline__ void stage_moments(const float* __restrict__ mn, floa
 
 // ------------------------------------------------------------- far field
 // EvaluateFarFieldExpansion: sum_{alpha<p} M_alpha h_alpha((q - R.c)/sqrt(2h^2)).
+// sum over the multi-indices of M[alpha] prod_k H[j][k][alpha_k] for NQ
+// points j, nested one dimension at a time (radix PM, dimension K upward,
+// the last dimension contiguous in M): P + P/PM + ... fma per point.
+template <int D, int PM, int K, int NQ>
+__device__ __forceinline__ void eval_nested(const float* __restrict__ M, const float (*H)[D][PM], float* out) {
+  constexpr int STRIDE = ipow_c(PM, D - 1 - K);
+  float acc[NQ];
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) acc[j] = 0.f;
+#pragma unroll
+  for (int e = 0; e < PM; ++e) {
+    if constexpr (K == D - 1) {
+      const float m = M[e];
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) acc[j] = fmaf(H[j][K][e], m, acc[j]);
+    } else {
+      float in[NQ];
+      eval_nested<D, PM, K + 1, NQ>(M + e * STRIDE, H, in);
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) acc[j] = fmaf(H[j][K][e], in[j], acc[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) out[j] = acc[j];
+}
+
+// Far-field value at NQ queries of this lane (q0 + lane + 32 j).
+template <int D, int NQ>
+__device__ __forceinline__ void farfield_points(const TreeView& Q, const float* Ms, const CenterHL* cR,
+                                                float sf, int qb, int qn, int q0, int lane,
+                                                double* __restrict__ gout) {
+  constexpr int PM = pmax_of(D);
+  float H[NQ][D][PM];
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const int qi = q0 + lane + 32 * j;
+    float v[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = cR[k].hi;
+    if (qi < qn) load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, v);
+#pragma unroll
+    for (int k = 0; k < D; ++k) hermite_f32<PM>(minus_center(v[k], cR[k]) * sf, H[j][k]);
+  }
+  float acc[NQ];
+  eval_nested<D, PM, 0, NQ>(Ms, H, acc);
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    const int qi = q0 + lane + 32 * j;
+    if (qi < qn) atomicAdd(&gout[qb + qi], (double)acc[j]);
+  }
+}
+
 template <int D>
 __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
                                                  const Action* __restrict__ list, int n,
@@ -691,21 +743,16 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
 #pragma unroll
   for (int k = 0; k < D; ++k) cR[k] = center_hl(R, a.r, k);
   const int qb = Q.beg[a.q], qn = Q.cnt[a.q];
-  for (int qi = lane; qi < qn; qi += 32) {
-    float qv[D];
-    load_point<D>(Q.pts + (size_t)(qb + qi) * Q.dp, qv);
-    float H[D][PM];
-#pragma unroll
-    for (int k = 0; k < D; ++k) hermite_f32<PM>(minus_center(qv[k], cR[k]) * sf, H[k]);
-    float acc = 0.f;
-#pragma unroll
-    for (int idx = 0; idx < P; ++idx) {
-      float t = Ms[idx];
-#pragma unroll
-      for (int k = 0; k < D; ++k) t *= H[k][digit_c<D, PM>(idx, k)];
-      acc += t;
+  // two queries per lane share every moment load while more than 32 remain
+  double* gout = gacc + (size_t)a.h * Q.n;
+  for (int q0 = 0; q0 < qn;) {
+    if (qn - q0 > 32) {
+      farfield_points<D, 2>(Q, Ms, cR, sf, qb, qn, q0, lane, gout);
+      q0 += 64;
+    } else {
+      farfield_points<D, 1>(Q, Ms, cR, sf, qb, qn, q0, lane, gout);
+      q0 += 32;
     }
-    atomicAdd(&gacc[(size_t)a.h * Q.n + qb + qi], (double)acc);
   }
 }
 
