@@ -25,6 +25,7 @@ namespace dfgt {
 namespace {
 
 constexpr int kT = 256;
+constexpr int kMaxLevels = 128;
 
 __global__ void k_pad_points(const float* __restrict__ in, int n, int d, int dp,
                              float* __restrict__ out, int* __restrict__ perm,
@@ -42,12 +43,20 @@ __global__ void k_pad_points(const float* __restrict__ in, int n, int d, int dp,
   if (bad) atomicOr(status, kStNonFinite);
 }
 
-__global__ void k_init_nodes(int a, int e, int d, float* lo, float* hi) {
-  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= e) return;
-  for (int k = 0; k < d; ++k) {
-    lo[(size_t)j * d + k] = INFINITY;
-    hi[(size_t)j * d + k] = -INFINITY;
+// The root: all points, an empty box to be filled by k_bbox; level 0 = [0, 1).
+__global__ void k_init_root(int n, int d, int* beg, int* cnt, int* left, int* parent, float* lo, float* hi,
+                            int* lv) {
+  if (threadIdx.x == 0) {
+    beg[0] = 0;
+    cnt[0] = n;
+    left[0] = -1;
+    parent[0] = -1;
+    lv[0] = 0;
+    lv[1] = 1;
+  }
+  for (int k = threadIdx.x; k < d; k += blockDim.x) {
+    lo[k] = INFINITY;
+    hi[k] = -INFINITY;
   }
 }
 
@@ -107,63 +116,87 @@ __global__ void __launch_bounds__(kT) k_bbox(const float* __restrict__ pts, int 
   }
 }
 
-// Split decision of each node of the level: widest side sd and its box
-// midpoint sc; a node splits only if it holds more than `leaf` points and
-// its box has positive extent.
-__global__ void k_split_decide(int a, int e, int d, int leaf, const int* __restrict__ cnt,
-                               const float* __restrict__ lo, const float* __restrict__ hi,
-                               int* __restrict__ want, int* __restrict__ sd_out,
-                               float* __restrict__ sc_out) {
-  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= e) return;
-  int sd = 0;
+// Split rule of a node: it splits only if it holds more than `leaf` points
+// and its box has positive extent, along its widest side sd at the box
+// midpoint sc (Algorithm 2).
+__device__ __forceinline__ bool split_rule(int j, int d, int leaf, const int* __restrict__ cnt,
+                                           const float* __restrict__ lo, const float* __restrict__ hi,
+                                           int& sd, float& sc) {
+  sd = 0;
   float ext = hi[(size_t)j * d] - lo[(size_t)j * d];
   for (int k = 1; k < d; ++k) {
-    float x = hi[(size_t)j * d + k] - lo[(size_t)j * d + k];
+    const float x = hi[(size_t)j * d + k] - lo[(size_t)j * d + k];
     if (x > ext) { ext = x; sd = k; }
   }
-  const int w = (cnt[j] > leaf && ext > 0.f) ? 1 : 0;
-  want[j - a] = w;
-  sd_out[j - a] = sd;
-  sc_out[j - a] = 0.5f * (lo[(size_t)j * d + sd] + hi[(size_t)j * d + sd]);
+  sc = 0.5f * (lo[(size_t)j * d + sd] + hi[(size_t)j * d + sd]);
+  return cnt[j] > leaf && ext > 0.f;
 }
 
-__global__ void k_flag_left(const float* __restrict__ pts, int n, int dp, int a,
-                            const int* __restrict__ pnode, const int* __restrict__ want,
-                            const int* __restrict__ sd, const float* __restrict__ sc,
+__global__ void k_flag_left(const float* __restrict__ pts, int n, int dp, int d, int leaf,
+                            const int* __restrict__ pnode, const int* __restrict__ cnt,
+                            const float* __restrict__ lo, const float* __restrict__ hi,
                             int* __restrict__ flag) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int nd = pnode[i];
   int f = 0;
-  if (nd >= 0 && want[nd - a]) f = pts[(size_t)i * dp + sd[nd - a]] <= sc[nd - a] ? 1 : 0;
+  int sd;
+  float sc;
+  if (nd >= 0 && split_rule(nd, d, leaf, cnt, lo, hi, sd, sc)) f = pts[(size_t)i * dp + sd] <= sc ? 1 : 0;
   flag[i] = f;
 }
 
-__global__ void k_node_finalize(int a, int e, const int* __restrict__ beg,
-                                const int* __restrict__ cnt, const int* __restrict__ want,
+// Level L occupies nodes [lv[3L], lv[3L+1]); lv[3L+2] is its number of
+// splits.  Node kernels of a level run over `bound` >= its node count.
+__global__ void k_node_finalize(const int* __restrict__ lv, int L, int bound, int d, int leaf,
+                                const int* __restrict__ beg, const int* __restrict__ cnt,
+                                const float* __restrict__ lo, const float* __restrict__ hi,
                                 const int* __restrict__ leftpos, int* __restrict__ split,
                                 int* __restrict__ nleft) {
-  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= e) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= bound) return;
+  const int a = lv[3 * L], e = lv[3 * L + 1];
+  const int j = a + t;
+  if (j >= e) {
+    split[t] = 0;
+    nleft[t] = 0;
+    return;
+  }
+  int sd;
+  float sc;
+  const bool want = split_rule(j, d, leaf, cnt, lo, hi, sd, sc);
   const int b = beg[j], c = cnt[j];
   const int nl = leftpos[b + c] - leftpos[b];
-  split[j - a] = (want[j - a] && nl > 0 && nl < c) ? 1 : 0;
-  nleft[j - a] = nl;
+  split[t] = (want && nl > 0 && nl < c) ? 1 : 0;
+  nleft[t] = nl;
 }
 
-__global__ void k_make_children(int a, int e, int level, int d, const int* __restrict__ split,
-                                const int* __restrict__ soff, const int* __restrict__ nleft,
-                                int* beg, int* cnt, int* left, int* parent, float* lo,
-                                float* hi) {
-  const int j = a + blockIdx.x * blockDim.x + threadIdx.x;
+// Children of the level's split nodes, numbered level by level; also
+// writes the next level's range.  The caller reserves room for every node
+// the level can create; a request beyond `cap` is refused and flagged.
+__global__ void k_make_children(int* __restrict__ lv, int L, int bound, int d, int cap,
+                                const int* __restrict__ split, const int* __restrict__ soff,
+                                const int* __restrict__ nleft, int* beg, int* cnt, int* left,
+                                int* parent, float* lo, float* hi, int* __restrict__ status) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int a = lv[3 * L], e = lv[3 * L + 1];
+  const int total = soff[bound];
+  const bool fits = (long long)e + 2LL * total <= cap;
+  if (t == 0) {
+    lv[3 * L + 2] = fits ? total : 0;
+    lv[3 * (L + 1)] = e;
+    lv[3 * (L + 1) + 1] = fits ? e + 2 * total : e;
+    if (!fits) atomicOr(status, kStOverflow);
+  }
+  if (t >= bound) return;
+  const int j = a + t;
   if (j >= e) return;
-  if (!split[j - a]) {
+  if (!fits || !split[t]) {
     left[j] = -1;
     return;
   }
-  const int c0 = e + 2 * soff[j - a];
-  const int nl = nleft[j - a];
+  const int c0 = e + 2 * soff[t];
+  const int nl = nleft[t];
   left[j] = c0;
   beg[c0] = beg[j];
   cnt[c0] = nl;
@@ -175,10 +208,9 @@ __global__ void k_make_children(int a, int e, int level, int d, const int* __res
     lo[(size_t)c0 * d + k] = lo[(size_t)(c0 + 1) * d + k] = INFINITY;
     hi[(size_t)c0 * d + k] = hi[(size_t)(c0 + 1) * d + k] = -INFINITY;
   }
-  (void)level;
 }
 
-__global__ void k_scatter(int n, int dp, int a, const float* __restrict__ pin,
+__global__ void k_scatter(int n, int dp, const int* __restrict__ lv, int L, const float* __restrict__ pin,
                           const int* __restrict__ perm_in, const int* __restrict__ pnode_in,
                           const int* __restrict__ flag, const int* __restrict__ leftpos,
                           const int* __restrict__ beg, const int* __restrict__ left,
@@ -186,6 +218,7 @@ __global__ void k_scatter(int n, int dp, int a, const float* __restrict__ pin,
                           int* __restrict__ perm_out, int* __restrict__ pnode_out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const int a = lv[3 * L];
   const int nd = pnode_in[i];
   int dst = i, child = -1;
   if (nd >= 0 && left[nd] >= 0) {
@@ -494,17 +527,17 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   t->lvl_off.assign(1, 0);
 
   // level-build scratch from the context: two point buffers, per-point node
-  // ids, flags, prefix sums, per-level node temporaries
+  // ids, flags, prefix sums, per-level node temporaries, the level table
   float* pbuf[2];
   int* perm2[2];
   int* pnode[2];
-  int *flag, *leftpos, *want, *sd, *split, *soff, *nleft, *status;
-  float* sc;
+  int *flag, *leftpos, *split, *soff, *nleft, *status, *lv;
   NodeArrays na;
   size_t cap = 0;
-  int cur = 0, a = 0, e = 1, level = 0;
+  int cur = 0, level = 0, last = -1;
   int h_status = 0;
   dfgt_status rc = DFGT_ECUDA;
+  std::vector<int> lvh;
 
   const size_t np = (size_t)n;
   Carver cv;
@@ -518,13 +551,11 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
     pnode[1] = cv.take<int>(np);
     flag = cv.take<int>(np);
     leftpos = cv.take<int>(np + 1);
-    want = cv.take<int>(np + 1);
-    sd = cv.take<int>(np + 1);
-    sc = cv.take<float>(np + 1);
     split = cv.take<int>(np + 1);
     soff = cv.take<int>(np + 2);
     nleft = cv.take<int>(np + 1);
     status = cv.take<int>(1);
+    lv = cv.take<int>(3 * (kMaxLevels + 2));
     if (pass == 0) {
       TRY(ctx->bscratch.ensure(cv.off));
       cv.base = ctx->bscratch.as<char>();
@@ -543,62 +574,91 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   }
 
   k_pad_points<<<(n + kT - 1) / kT, kT, 0, s>>>(pts_dev, n, d, t->dp, pbuf[0], perm2[0], pnode[0], status);
-  ++*L;
-  {
-    const int zero = 0, minus1 = -1;
-    TRY(cudaMemcpyAsync(na.beg, &zero, sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(na.cnt, &n, sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(na.parent, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaMemcpyAsync(na.left, &minus1, sizeof(int), cudaMemcpyHostToDevice, s));
-  }
-  k_init_nodes<<<1, 32, 0, s>>>(0, 1, d, na.lo, na.hi);
-  ++*L;
-  TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-  TRY(cudaStreamSynchronize(s));
-  if (h_status & kStNonFinite) {
-    ctx->err = "dfgt_build: non-finite coordinate";
-    rc = DFGT_EINVAL;
-    goto fail;
-  }
+  k_init_root<<<1, 32, 0, s>>>(n, d, na.beg, na.cnt, na.left, na.parent, na.lo, na.hi, lv);
+  *L += 2;
+  TRY(cudaGetLastError());
 
-  for (level = 0; level < 128; ++level) {
-    const int nl = e - a;
-    const int gp = (n + kT - 1) / kT, gn = (nl + kT - 1) / kT;
-    k_bbox<<<gp, kT, 0, s>>>(pbuf[cur], n, d, t->dp, pnode[cur], na.lo, na.hi);
-    k_split_decide<<<gn, kT, 0, s>>>(a, e, d, t->leaf, na.cnt, na.lo, na.hi, want, sd, sc);
-    k_flag_left<<<gp, kT, 0, s>>>(pbuf[cur], n, t->dp, a, pnode[cur], want, sd, sc, flag);
-    *L += 3;
-    TRY(cudaGetLastError());
-    TRY(scan_exclusive(flag, leftpos, n, ctx->scan_tmp, s, L));
-    k_node_finalize<<<gn, kT, 0, s>>>(a, e, na.beg, na.cnt, want, leftpos, split, nleft);
-    ++*L;
-    TRY(cudaGetLastError());
-    TRY(scan_exclusive(split, soff, nl, ctx->scan_tmp, s, L));
-    int nsplit = 0;
-    TRY(cudaMemcpyAsync(&nsplit, soff + nl, sizeof(int), cudaMemcpyDeviceToHost, s));
-    TRY(cudaStreamSynchronize(s));
-    const size_t need = (size_t)e + 2 * (size_t)nsplit;
-    if (need > cap) {
-      const size_t nc = std::max(need, cap * 2);
-      TRY(grow_nodes(ctx->bnodes, na, (size_t)e, nc, d, s));
-      cap = nc;
+  {
+    // Levels run in batches between host synchronisations.  A node splits
+    // only if it holds more than `leaf` points, so a level has at most
+    // 2 floor(n / (leaf + 1)) nodes below the root and at most twice the
+    // nodes of the level above: node kernels run over that bound and the
+    // node arrays hold room for every node a batch can create.  The level
+    // table records each level's range and split count; a level without
+    // splits ends the tree (levels enqueued after it are empty and leave the
+    // points in place).
+    const long long max_level_nodes = std::max<long long>(1, 2LL * (n / (t->leaf + 1)));
+    size_t known_e = 1;
+    long long known_nl = 1;
+    int batch = std::max(8, ctx->last_depth + 1);
+    const int gp = (n + kT - 1) / kT;
+    while (last < 0) {
+      if (level >= kMaxLevels) {
+        ctx->err = "dfgt_build: more than 128 tree levels";
+        rc = DFGT_ETIMEOUT;
+        goto fail;
+      }
+      const int nb = std::min(batch, kMaxLevels - level);
+      std::vector<long long> bnd(nb + 1);
+      bnd[0] = known_nl;
+      size_t need = known_e;
+      for (int k = 1; k <= nb; ++k) {
+        bnd[k] = std::min(2 * bnd[k - 1], max_level_nodes);
+        need += (size_t)bnd[k];
+      }
+      if (need > cap) {
+        const size_t nc = std::max(need, cap * 2);
+        TRY(grow_nodes(ctx->bnodes, na, known_e, nc, d, s));
+        cap = nc;
+      }
+      for (int k = 0; k < nb; ++k) {
+        const int Lk = level + k;
+        const int bk = (int)std::max<long long>(1, bnd[k]);
+        const int gn = (bk + kT - 1) / kT;
+        k_bbox<<<gp, kT, 0, s>>>(pbuf[cur], n, d, t->dp, pnode[cur], na.lo, na.hi);
+        k_flag_left<<<gp, kT, 0, s>>>(pbuf[cur], n, t->dp, d, t->leaf, pnode[cur], na.cnt, na.lo, na.hi, flag);
+        *L += 2;
+        TRY(cudaGetLastError());
+        TRY(scan_exclusive(flag, leftpos, n, ctx->scan_tmp, s, L));
+        k_node_finalize<<<gn, kT, 0, s>>>(lv, Lk, bk, d, t->leaf, na.beg, na.cnt, na.lo, na.hi, leftpos,
+                                          split, nleft);
+        ++*L;
+        TRY(cudaGetLastError());
+        TRY(scan_exclusive(split, soff, bk, ctx->scan_tmp, s, L));
+        k_make_children<<<gn, kT, 0, s>>>(lv, Lk, bk, d, (int)std::min<size_t>(cap, INT32_MAX), split, soff,
+                                          nleft, na.beg, na.cnt, na.left, na.parent, na.lo, na.hi, status);
+        k_scatter<<<gp, kT, 0, s>>>(n, t->dp, lv, Lk, pbuf[cur], perm2[cur], pnode[cur], flag, leftpos,
+                                    na.beg, na.left, nleft, pbuf[cur ^ 1], perm2[cur ^ 1], pnode[cur ^ 1]);
+        *L += 2;
+        TRY(cudaGetLastError());
+        cur ^= 1;
+      }
+      lvh.resize(3 * (level + nb + 1));
+      TRY(cudaMemcpyAsync(lvh.data(), lv, lvh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
+      TRY(cudaStreamSynchronize(s));
+      if (h_status & kStNonFinite) {
+        ctx->err = "dfgt_build: non-finite coordinate";
+        rc = DFGT_EINVAL;
+        goto fail;
+      }
+      if (h_status & kStOverflow) {
+        ctx->err = "dfgt_build: node capacity bound violated (internal error)";
+        rc = DFGT_ECAPACITY;
+        goto fail;
+      }
+      for (int k = 0; k < nb && last < 0; ++k)
+        if (lvh[3 * (level + k) + 2] == 0) last = level + k;
+      level += nb;
+      if (last < 0) {
+        known_e = (size_t)lvh[3 * level + 1];
+        known_nl = (long long)lvh[3 * level + 1] - lvh[3 * level];
+        batch = 8;
+      }
     }
-    k_make_children<<<gn, kT, 0, s>>>(a, e, level, d, split, soff, nleft, na.beg, na.cnt,
-                                      na.left, na.parent, na.lo, na.hi);
-    k_scatter<<<gp, kT, 0, s>>>(n, t->dp, a, pbuf[cur], perm2[cur], pnode[cur], flag, leftpos,
-                                na.beg, na.left, nleft, pbuf[cur ^ 1], perm2[cur ^ 1], pnode[cur ^ 1]);
-    *L += 2;
-    TRY(cudaGetLastError());
-    cur ^= 1;
-    t->lvl_off.push_back(e);
-    if (nsplit == 0) break;
-    a = e;
-    e = (int)need;
-  }
-  if (level >= 128) {
-    ctx->err = "dfgt_build: more than 128 tree levels";
-    rc = DFGT_ETIMEOUT;
-    goto fail;
+    t->lvl_off.assign(1, 0);
+    for (int Lk = 0; Lk <= last; ++Lk) t->lvl_off.push_back(lvh[3 * Lk + 1]);
+    ctx->last_depth = last + 1;
   }
   t->nn = t->lvl_off.back();
   t->depth = (int)t->lvl_off.size() - 1;
