@@ -24,6 +24,8 @@ __all__ = [
     "uneven_query_batches",
     "workload",
     "WORKLOADS",
+    "bichromatic",
+    "BICHROMATIC",
     "logspace_bandwidths",
 ]
 
@@ -33,12 +35,13 @@ def _finish(x: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.clip(x, 0.0, 1.0).astype(np.float32))
 
 
-def isotropic_mixture(n: int, d: int, k: int, sigma, seed: int) -> np.ndarray:
+def isotropic_mixture(n: int, d: int, k: int, sigma, seed: int, draw_seed: int | None = None) -> np.ndarray:
     """n points from k isotropic Gaussians with means uniform in [0,1]^d.
 
     ``sigma`` is either one standard deviation for all components or a pair
     (lo, hi) from which each component's deviation is drawn log-uniformly.
-    Components have equal weight.
+    Components have equal weight.  The mixture comes from ``seed``; with
+    ``draw_seed`` the points are an independent draw from that same mixture.
     """
     rng = np.random.default_rng(seed)
     means = rng.random((k, d))
@@ -47,6 +50,8 @@ def isotropic_mixture(n: int, d: int, k: int, sigma, seed: int) -> np.ndarray:
     else:
         lo, hi = sigma
         sig = np.exp(rng.uniform(np.log(lo), np.log(hi), size=k))
+    if draw_seed is not None:
+        rng = np.random.default_rng(draw_seed)
     comp = rng.integers(0, k, size=n)
     x = means[comp] + rng.standard_normal((n, d)) * sig[comp, None]
     return _finish(x)
@@ -128,6 +133,34 @@ WORKLOADS = {
                                h=list(logspace_bandwidths(0.01, 1.0, 8)), eps=1e-2,
                                gen=lambda: manifold_points(1_000_000, 16, 4, 0.01, seed=4)),
 }
+
+
+# Bichromatic workloads: a reference set and separately drawn query batches
+# from the same mixture.
+BICHROMATIC = {
+    # D=32, |R|=1e6 from 128 isotropic components (sigma log-uniform in
+    # [0.02, 0.1]); 64 query batches of sizes log-uniform in [1e3, 2e5] from
+    # the same mixture; 16 bandwidths in [0.01, 1]; eps 1e-2 and 1e-3.
+    "kde32d_r1e6_q64batches": dict(d=32, nr=1_000_000, k=128, sigma=(0.02, 0.1), nbatch=64,
+                                   batch_lo=1_000, batch_hi=200_000,
+                                   h=list(logspace_bandwidths(0.01, 1.0, 16)), eps=[1e-2, 1e-3], seed=5),
+}
+
+
+def bichromatic(name: str, nr: int | None = None, nbatch: int | None = None,
+                batch_hi: int | None = None):
+    """Return (references float32 [nr,D], list of query batches, bandwidths,
+    eps values) for a named bichromatic workload.  ``nr``, ``nbatch`` and
+    ``batch_hi`` give a smaller case of the same recipe."""
+    w = BICHROMATIC[name]
+    nr = w["nr"] if nr is None else nr
+    nbatch = w["nbatch"] if nbatch is None else nbatch
+    hi = w["batch_hi"] if batch_hi is None else batch_hi
+    refs = isotropic_mixture(nr, w["d"], w["k"], w["sigma"], w["seed"])
+    sizes = uneven_query_batches(nbatch, w["batch_lo"], hi, w["seed"] + 100)
+    batches = [isotropic_mixture(int(m), w["d"], w["k"], w["sigma"], w["seed"], draw_seed=1000 * w["seed"] + b)
+               for b, m in enumerate(sizes)]
+    return refs, batches, list(w["h"]), list(w["eps"])
 
 
 def workload(name: str, n: int | None = None):
