@@ -91,8 +91,8 @@ dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream);
 /* Set the capacity of the traversal's action lists (items per list) and
  * the initial capacity of its frontier (node pairs).  A list that could
  * overflow in the next round is drained first (its kernel runs early,
- * counted in dfgt_stats.list_flushes); the frontier grows to the exact
- * size each round needs.  Larger lists trade memory for fewer, larger
+ * counted in dfgt_stats.list_flushes); the frontier grows to hold the
+ * next round's child pairs (at most four per pair).  Larger lists trade memory for fewer, larger
  * launches.  Both must be >= 1. */
 dfgt_status dfgt_set_capacity(dfgt_ctx* ctx, int64_t frontier_pairs, int64_t list_items);
 

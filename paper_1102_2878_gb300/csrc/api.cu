@@ -228,14 +228,17 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       rc = ensure_lists(ctx);
       if (rc != DFGT_OK) return rc;
     }
-    CK(ctx->slots.ensure((size_t)nF * sizeof(int)));
+    // the next frontier: at most four child pairs per pair
+    CK(ctx->frontier[cur ^ 1].ensure(4 * (size_t)nF * sizeof(Pair)));
+    ctx->cap_frontier = std::max(ctx->cap_frontier, 4 * (size_t)nF);
     CK(ctx->kus.ensure((size_t)nF * sizeof(float)));
     b.ku = ctx->kus.as<float>();
     CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_fold(b, qt->nn, s));
     CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
     CK(cudaMemsetAsync(&dctr->n_next, 0, sizeof(int), s));
-    CK(launch_classify(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, ctx->slots.as<int>(),
+    CK(launch_classify(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, ctx->frontier[cur ^ 1].as<Pair>(),
+                       (int)std::min<size_t>(4 * (size_t)nF, INT32_MAX),
                        ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(),
                        ctx->list_f2l.as<Action>(), ctx->list_base.as<Pair>(), (int)ctx->cap_lists,
                        dctr, s));
@@ -248,7 +251,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       cudaEventElapsedTime(&t, ctx->ev[6], ctx->ev[7]);
       ms_classify += t;
     }
-    if (hc->status & kStOverflow) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: action list overflow");
+    if (hc->status & kStOverflow) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work list overflow");
     visited += nF;
     ++rounds;
     for (int w = 0; w < 4; ++w) lists[w].collect();
@@ -257,16 +260,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       lists[w].total += got[w] - lists[w].count;
       lists[w].count = got[w];
     }
-    const int n_next = hc->n_next;
-    if (n_next > 0) {
-      // size the next frontier exactly, then write the reserved child pairs
-      CK(ctx->frontier[cur ^ 1].ensure((size_t)n_next * sizeof(Pair)));
-      ctx->cap_frontier = std::max(ctx->cap_frontier, (size_t)n_next);
-      CK(launch_emit(Q, R, ctx->frontier[cur].as<Pair>(), nF, ctx->slots.as<int>(),
-                     ctx->frontier[cur ^ 1].as<Pair>(), s));
-      ++ctx->launches;
-    }
-    nF = n_next;
+    nF = hc->n_next;
     cur ^= 1;
   }
   CK(cudaEventRecord(ctx->ev[1], s));
@@ -363,7 +357,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1], &ctx->slots,
+  DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1],
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,

@@ -84,7 +84,6 @@ struct dfgt_ctx {
   DevBuf hvals;          // bandwidths, then 1/(2h^2)
   DevBuf kus;            // float lower bound on K(d^u) per frontier pair
   DevBuf frontier[2];    // Pair
-  DevBuf slots;          // int child slot per frontier pair
   DevBuf grp_cnt, grp_off, grp_r;  // base-case grouping scratch
   DevBuf list_far, list_loc, list_f2l, list_base;  // Action / Pair
   DevBuf node_state;     // u64 inherited/decided/incr/lbsum
@@ -191,11 +190,9 @@ cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s);
 cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
                       int nF, cudaStream_t s);
 cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Pair* F, int nF, int* slot, Action* far, Action* loc,
+                            const Pair* F, int nF, Pair* next, int cap_next, Action* far, Action* loc,
                             Action* f2l, Pair* base, int cap_lists, RoundCounters* counters,
                             cudaStream_t s);
-cudaError_t launch_emit(const TreeView& Q, const TreeView& R, const Pair* F, int nF, const int* slot,
-                        Pair* next, cudaStream_t s);
 cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s);
 
 // Scratch of the base-case grouping (counting sort by bandwidth and query node).

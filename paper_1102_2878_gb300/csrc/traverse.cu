@@ -33,7 +33,6 @@ namespace {
 
 constexpr int kT = 256;
 constexpr float kMaxSummaryPoints = 4096.f;
-constexpr int kSlotBits = 28;  // frontier slots stay below 2^28 (checked by the host)
 constexpr int kSplitROnly = 1, kSplitQOnly = 2;
 
 // Truncation of a non-negative float below 2^64 to an integer, by shifting
@@ -135,7 +134,7 @@ __global__ void __launch_bounds__(kT) k_lb(TreeView Q, TreeView R, TravBuffers b
 template <int D>
 __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuffers b,
                                                  const Pair* __restrict__ F, int nF,
-                                                 int* __restrict__ slot,
+                                                 Pair* __restrict__ next, int cap_next,
                                                  Action* __restrict__ far, Action* __restrict__ loc,
                                                  Action* __restrict__ f2l, Pair* __restrict__ base,
                                                  int cap_lists, RoundCounters* ctr) {
@@ -227,8 +226,8 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
     // F, D, T, base) packed in 12-bit fields of one word, one block-wide
     // exclusive scan, one atomic per list and block step (atomics on the
     // shared counters would otherwise serialise).  Child pairs only get
-    // their slots here and are written by k_emit once the host has sized
-    // the next frontier.
+    // their pairs written to the next frontier (room for 4 per pair is
+    // reserved by the host).
     const u64 mine = (u64)nchild | ((u64)(kind == 1) << 12) | ((u64)(kind == 2) << 24) |
                      ((u64)(kind == 3) << 36) | ((u64)(kind == 4) << 48);
     u64 incl = mine;
@@ -259,7 +258,26 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
     __syncthreads();
     const u64 ex = sWarp[wid] + incl - mine;
     auto field = [&](int k) { return sBase[k] + (int)((ex >> (12 * k)) & 0xfffu); };
-    if (i < nF) slot[i] = nchild ? (field(0) | (split << kSlotBits)) : -1;
+    if (nchild) {
+      const int s0 = field(0);
+      if (s0 + nchild <= cap_next) {
+        const int ql = Q.left[pr.q], rl = R.left[pr.r];
+        if (split == kSplitROnly || (split == 0 && ql < 0)) {
+          next[s0] = Pair{pr.q, rl, pr.h, 0};
+          next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
+        } else if (split == kSplitQOnly || rl < 0) {
+          next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
+          next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
+        } else {
+          next[s0] = Pair{ql, rl, pr.h, kFlagSplitQ};
+          next[s0 + 1] = Pair{ql, rl + 1, pr.h, kFlagSplitQ};
+          next[s0 + 2] = Pair{ql + 1, rl, pr.h, kFlagSplitQ};
+          next[s0 + 3] = Pair{ql + 1, rl + 1, pr.h, kFlagSplitQ};
+        }
+      } else {
+        atomicOr(&ctr->status, kStOverflow);
+      }
+    }
     if (kind == 1) { const int s1 = field(1); if (s1 < cap_lists) far[s1] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
     if (kind == 2) { const int s2 = field(2); if (s2 < cap_lists) loc[s2] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
     if (kind == 3) { const int s3 = field(3); if (s3 < cap_lists) f2l[s3] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
@@ -273,45 +291,13 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
   warp_add_u64_block(&ctr->base_inter, my_inter, sWarp);
 }
 
-// Write the child pairs of every recursing pair at the slot reserved by
-// k_classify (DFGT recursion: split both nodes, or the one that is not a leaf).
-__global__ void __launch_bounds__(kT) k_emit(const int* __restrict__ Qleft, const int* __restrict__ Rleft,
-                                             const Pair* __restrict__ F, int nF,
-                                             const int* __restrict__ slot, Pair* __restrict__ next) {
-  const int i = blockIdx.x * kT + threadIdx.x;
-  if (i >= nF) return;
-  const int sv = slot[i];
-  if (sv < 0) return;
-  const int s0 = sv & ((1 << kSlotBits) - 1), split = sv >> kSlotBits;
-  const Pair pr = F[i];
-  const int ql = Qleft[pr.q], rl = Rleft[pr.r];
-  if (split == kSplitROnly) {
-    next[s0] = Pair{pr.q, rl, pr.h, 0};
-    next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
-  } else if (split == kSplitQOnly) {
-    next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
-    next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
-  } else if (ql < 0) {
-    next[s0] = Pair{pr.q, rl, pr.h, 0};
-    next[s0 + 1] = Pair{pr.q, rl + 1, pr.h, 0};
-  } else if (rl < 0) {
-    next[s0] = Pair{ql, pr.r, pr.h, kFlagSplitQ};
-    next[s0 + 1] = Pair{ql + 1, pr.r, pr.h, kFlagSplitQ};
-  } else {
-    next[s0] = Pair{ql, rl, pr.h, kFlagSplitQ};
-    next[s0 + 1] = Pair{ql, rl + 1, pr.h, kFlagSplitQ};
-    next[s0 + 2] = Pair{ql + 1, rl, pr.h, kFlagSplitQ};
-    next[s0 + 3] = Pair{ql + 1, rl + 1, pr.h, kFlagSplitQ};
-  }
-}
-
 template <int D>
 cudaError_t classify_d(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
-                       int nF, int* slot, Action* far, Action* loc, Action* f2l,
+                       int nF, Pair* next, int cap_next, Action* far, Action* loc, Action* f2l,
                        Pair* base, int cap_lists, RoundCounters* ctr, cudaStream_t s) {
   int grid = (nF + kT - 1) / kT;
   if (grid > 152 * 16) grid = 152 * 16;
-  k_classify<D><<<grid, kT, 0, s>>>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr);
+  k_classify<D><<<grid, kT, 0, s>>>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr);
   return cudaGetLastError();
 }
 
@@ -343,23 +329,17 @@ cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b
 }
 
 cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Pair* F, int nF, int* slot, Action* far, Action* loc,
+                            const Pair* F, int nF, Pair* next, int cap_next, Action* far, Action* loc,
                             Action* f2l, Pair* base, int cap_lists, RoundCounters* ctr,
                             cudaStream_t s) {
   switch (Q.d) {
-    case 1: return classify_d<1>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
-    case 2: return classify_d<2>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
-    case 3: return classify_d<3>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
-    case 4: return classify_d<4>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
-    case 5: return classify_d<5>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
-    default: return classify_d<0>(Q, R, b, F, nF, slot, far, loc, f2l, base, cap_lists, ctr, s);
+    case 1: return classify_d<1>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 2: return classify_d<2>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 3: return classify_d<3>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 4: return classify_d<4>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    case 5: return classify_d<5>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+    default: return classify_d<0>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
   }
-}
-
-cudaError_t launch_emit(const TreeView& Q, const TreeView& R, const Pair* F, int nF, const int* slot,
-                        Pair* next, cudaStream_t s) {
-  k_emit<<<(nF + kT - 1) / kT, kT, 0, s>>>(Q.left, R.left, F, nF, slot, next);
-  return cudaGetLastError();
 }
 
 }  // namespace dfgt
