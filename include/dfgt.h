@@ -49,7 +49,7 @@ typedef struct dfgt_tree dfgt_tree; /* permuted points, kd-tree nodes, raw momen
 
 /* Build and traversal options.  Zero-initialised means "defaults". */
 typedef struct {
-  int leaf_size;   /* leaf threshold of Algorithm 2 (BuildKdTree); 0 -> 32; max 256 */
+  int leaf_size;   /* leaf threshold of Algorithm 2 (BuildKdTree); 0 -> 128; max 256 */
   int p_max;       /* per-dimension expansion order limit; 0 -> the paper's table
                       (Section 3.6: 6 for D=2, 4 for D=3, 2 for D=4,5, 1 for D>=6;
                       8 for D=1); a smaller positive value lowers it */
@@ -57,7 +57,7 @@ typedef struct {
                       0 -> 2e-5; must be < eps */
   long long base_block; /* a node pair that no summary can take is summed exactly,
                       without splitting further, once |Q| |R| <= base_block;
-                      0 -> 4 leaf_size^2, -1 -> only leaf pairs (as in DFGT) */
+                      0 -> 4096, -1 -> only leaf pairs (as in DFGT) */
 } dfgt_opts;
 
 /* Work counters of one dfgt_sum call, summed over its bandwidths. */
@@ -115,6 +115,23 @@ const char* dfgt_last_error(const dfgt_ctx* ctx);
  * copy of the points.  n >= 1, 1 <= d <= 32, finite coordinates. */
 dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
                        const dfgt_opts* opts, dfgt_tree** out);
+
+/* Choose the tree options that make a dual-tree sum of these points
+ * fastest on this GPU.  No counterpart in the paper (its leaf size is
+ * unstated): the leaf size and the exact-sum threshold base_block trade
+ * traversal work against exact-sum work, and the best pair depends on the
+ * data, the bandwidths and eps.  Builds a tree over points_dev (float32
+ * [n][d], device, caller-owned, not modified) for each candidate
+ * (leaf_size 32, 64, 96, 128, 160, 192; base_block 2048, 4096, 8192), runs
+ * dfgt_sum(tree, tree, h_host[0..nh), eps) trials + 1 times and keeps the
+ * fastest of the last `trials` runs (build and sum, CUDA events on the
+ * context's stream).  `best` is read for p_max and eps_fp, which are kept,
+ * and receives the chosen options; best_ms (may be NULL) the time of one
+ * build and sum with them.  1 <= trials <= 16.  Results of the trial sums
+ * are discarded.  Errors as for dfgt_build and dfgt_sum. */
+dfgt_status dfgt_autotune(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
+                          const double* h_host, int nh, double eps, int trials,
+                          dfgt_opts* best, double* best_ms);
 
 /* Free a tree.  NULL is ignored. */
 void dfgt_tree_destroy(dfgt_tree* tree);

@@ -157,6 +157,40 @@ def kde_sum(ctx: Context, qtree: Tree, rtree: Tree, hs, eps: float, out=None):
     return out, stats.as_dict()
 
 
+def kde_sum_batches(ctx: Context, query_batches, rtree: Tree, hs, eps: float, leaf_size: int = 0,
+                    base_block: int = 0, eps_fp: float = 0.0):
+    """Sums for several query batches against one reference tree.  A query's
+    sum does not depend on the other queries, so the batches are
+    concatenated into one query tree and summed in one call; returns one
+    [nh, n_b] float64 tensor per batch and the call's statistics."""
+    torch = _torch()
+    sizes = [int(b.shape[0]) for b in query_batches]
+    q = torch.cat([b.contiguous() for b in query_batches], dim=0)
+    qt = Tree(ctx, q, leaf_size=leaf_size, base_block=base_block, eps_fp=eps_fp)
+    G, st = kde_sum(ctx, qt, rtree, hs, eps)
+    qt.close()
+    return list(torch.split(G, sizes, dim=1)), st
+
+
+def autotune(ctx: Context, points, hs, eps: float, trials: int = 2, p_max: int = 0, eps_fp: float = 0.0):
+    """dfgt_autotune: the leaf size and exact-sum threshold that make a
+    build + sum of these points fastest; returns (options dict, ms)."""
+    torch = _torch()
+    if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
+            and points.dim() == 2):
+        raise TypeError("points must be a float32 CUDA tensor [n, d]")
+    p = points.contiguous()
+    ha, hp = _hs(hs)
+    opts = _opts(0, p_max, eps_fp, 0)
+    ms = C.c_double(0.0)
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_autotune(ctx.h, C.c_void_p(p.data_ptr()), p.shape[0], p.shape[1], hp, len(ha),
+                               float(eps), int(trials), C.byref(opts), C.byref(ms))
+    ctx.check(st, "dfgt_autotune")
+    return {"leaf_size": opts.leaf_size, "base_block": opts.base_block, "p_max": opts.p_max,
+            "eps_fp": opts.eps_fp}, ms.value
+
+
 def kde_sum_bruteforce(ctx: Context, q, r, hs, out=None):
     """Exact G [nh, nq] float64 (CUDA) by the all-pairs sum."""
     torch = _torch()

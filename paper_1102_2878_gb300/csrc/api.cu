@@ -426,6 +426,54 @@ dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtr
   return run_sum(ctx, qtree, rtree, h_host, nh, eps, G_dev, stats);
 }
 
+dfgt_status dfgt_autotune(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d, const double* h_host,
+                          int nh, double eps, int trials, dfgt_opts* best, double* best_ms) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!points_dev || !best || n < 1 || n > (int64_t)std::numeric_limits<int>::max() / 4 || d < 1 || d > kMaxD ||
+      trials < 1 || trials > 16)
+    return fail(ctx, DFGT_EINVAL, "dfgt_autotune: need points, 1 <= n < 2^29, 1 <= d <= 32, 1 <= trials <= 16");
+  if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_autotune: need 1..1024 finite bandwidths > 0");
+  if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, DFGT_EINVAL, "dfgt_autotune: need 0 < eps < 1");
+  CK(cudaSetDevice(ctx->device));
+  CK(ctx->io_g.ensure((size_t)nh * n * sizeof(double)));
+  // candidates: leaf sizes and exact-sum thresholds
+  const int leaves[] = {32, 64, 96, 128, 160, 192};
+  const long long blocks[] = {2048, 4096, 8192};
+  dfgt_opts start = *best;
+  double best_t = 1e300;
+  dfgt_opts chosen = start;
+  for (int leaf : leaves) {
+    if (leaf > kMaxLeaf) continue;
+    for (long long bb : blocks) {
+      dfgt_opts o = start;
+      o.leaf_size = leaf;
+      o.base_block = bb;
+      double tmin = 1e300;
+      for (int rep = 0; rep <= trials; ++rep) {  // the first run warms up and is not counted
+        CK(cudaEventRecord(ctx->ev[4], ctx->stream));
+        dfgt_tree* t = nullptr;
+        dfgt_status rc = dfgt_build(ctx, points_dev, n, d, &o, &t);
+        if (rc != DFGT_OK) return rc;
+        rc = dfgt_sum(ctx, t, t, h_host, nh, eps, ctx->io_g.as<double>(), nullptr);
+        dfgt_tree_destroy(t);
+        if (rc != DFGT_OK) return rc;
+        CK(cudaEventRecord(ctx->ev[5], ctx->stream));
+        CK(cudaEventSynchronize(ctx->ev[5]));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]));
+        if (rep > 0) tmin = std::min(tmin, (double)ms);
+      }
+      if (tmin < best_t) {
+        best_t = tmin;
+        chosen = o;
+      }
+    }
+  }
+  *best = chosen;
+  if (best_ms) *best_ms = best_t;
+  return DFGT_OK;
+}
+
 dfgt_status dfgt_sum_bruteforce(dfgt_ctx* ctx, const float* q_dev, int64_t nq, const float* r_dev,
                                 int64_t nr, int d, const double* h_host, int nh, double* G_dev) {
   if (!ctx) return DFGT_EINVAL;

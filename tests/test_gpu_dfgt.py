@@ -141,3 +141,34 @@ def test_dfgt_against_gpu_bruteforce(dev):
     Gb = dfgt.kde_sum_bruteforce(dev, to_cuda(x), to_cuda(x), hs)
     rel = ((G - Gb).abs() / Gb).max().item()
     assert rel <= 1e-2 + 1e-5
+
+
+def test_autotune_picks_a_candidate_and_stays_exact(dev, orc):
+    # the autotuner returns one of its candidates, and a tree built with the
+    # chosen options gives sums within eps
+    x, hs, eps = datagen.workload("kde2d_n1e4")
+    pts = to_cuda(x)
+    opts, ms = dfgt.autotune(dev, pts, hs, eps, trials=1)
+    assert opts["leaf_size"] in (32, 64, 96, 128, 160, 192)
+    assert opts["base_block"] in (2048, 4096, 8192)
+    assert ms > 0
+    t = dfgt.Tree(dev, pts, leaf_size=opts["leaf_size"], base_block=opts["base_block"])
+    G, _ = dfgt.kde_sum(dev, t, t, hs, eps)
+    ref = orc.naive_kde(x.astype(np.float64), x.astype(np.float64), hs[0])
+    assert np.all(np.abs(G.cpu().numpy()[0] - ref) <= eps * ref)
+
+
+def test_query_batches_match_single_calls(dev):
+    # batches concatenated into one query tree give the same sums as each
+    # batch summed on its own (both within eps of the brute force)
+    refs, batches, hs, _ = datagen.bichromatic("kde32d_r1e6_q64batches", nr=20_000, nbatch=4, batch_hi=4_000)
+    rt = dfgt.Tree(dev, to_cuda(refs), eps_fp=5e-4)
+    eps = 1e-2
+    outs, st = dfgt.kde_sum_batches(dev, [to_cuda(b) for b in batches], rt, hs[::4], eps, eps_fp=5e-4)
+    assert len(outs) == len(batches)
+    for b, Gb in zip(batches, outs):
+        ref = dfgt.kde_sum_bruteforce(dev, to_cuda(b), to_cuda(refs), hs[::4]).cpu().numpy()
+        Gb = Gb.cpu().numpy()
+        assert Gb.shape == ref.shape
+        big = ref >= 1e-30
+        assert np.all(np.abs(Gb[big] - ref[big]) <= (eps + 5e-4) * ref[big])
