@@ -131,6 +131,12 @@ def measured_peaks():
         return {}
 
 
+# DRAM bytes read + written by one k_base launch (one launch per step at the
+# default options) of a workload, from an ncu capture of
+# `bench.py --steps 1 --warmup 1 --only-dfgt` with the current kernel.
+K_BASE_TRAFFIC = {"kde3d_n2e5_sweep10": 40034304 + 256}
+
+
 def cpu_oracle_rate(x, hs, target_s, seed=0):
     """Time the FP64 oracle's exact sums on a bounded query sample (all
     references, all bandwidths), in batches grown until about target_s of
@@ -287,7 +293,7 @@ def run_dfgt(args, rank, world, local):
     achieved = inter / (base_ms / 1e3) if base_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_base (DFGTBase exact sums)", "achieved": achieved,
             "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
-            "traffic": None,
+            "traffic": K_BASE_TRAFFIC.get(args.workload),
             "peak_source": f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz (unit counts)"}
     cpu_rate, cpu_desc, cores = (None, None, None)
     if not args.no_cpu_baseline:
