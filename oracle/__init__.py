@@ -46,6 +46,13 @@ def _load():
     i64 = C.c_int64
     lib.orc_naive_kde.argtypes = [dp, i64, dp, i64, C.c_int, C.c_double, dp]
     lib.orc_hermite_functions.argtypes = [C.c_double, C.c_int, dp]
+    lib.orc_gauss_volume.argtypes = [C.c_int, C.c_double]
+    lib.orc_gauss_volume.restype = C.c_double
+    lib.orc_loo_sums.argtypes = [dp, i64, C.c_int, C.c_double, dp]
+    lib.orc_cv_lk.argtypes = [dp, i64, C.c_int, C.c_double]
+    lib.orc_cv_lk.restype = C.c_double
+    lib.orc_cv_ls.argtypes = [dp, i64, C.c_int, C.c_double]
+    lib.orc_cv_ls.restype = C.c_double
     lib.orc_pmax.argtypes = [C.c_int]
     lib.orc_pmax.restype = C.c_int
     lib.orc_multi_to_pos.argtypes = [ip, C.c_int, C.c_int]
@@ -110,6 +117,32 @@ def naive_kde(Q, R, h):
 
 
 # ---------------------------------------------------------- multi-indices
+def gauss_volume(D, h):
+    """V_{D,h} of Eq. 1 for the Gaussian kernel."""
+    return _load().orc_gauss_volume(int(D), float(h))
+
+
+def loo_sums(X, h):
+    """Leave-one-out sums S_j = sum_{i != j} exp(-|x_j - x_i|^2 / 2h^2)."""
+    X, xp = _d(X)
+    n, D = X.shape
+    S, sp = _d(np.empty(n))
+    _load().orc_loo_sums(xp, n, D, float(h), sp)
+    return S
+
+
+def cv_lk(X, h):
+    """Likelihood cross-validation score CV_LK(h) of the introduction."""
+    X, xp = _d(X)
+    return _load().orc_cv_lk(xp, X.shape[0], X.shape[1], float(h))
+
+
+def cv_ls(X, h):
+    """Least-squares cross-validation score CV_LS(h) of the introduction."""
+    X, xp = _d(X)
+    return _load().orc_cv_ls(xp, X.shape[0], X.shape[1], float(h))
+
+
 def pmax(D: int) -> int:
     return _load().orc_pmax(D)
 

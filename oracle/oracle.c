@@ -180,6 +180,77 @@ void orc_naive_kde(const double* Q, int64_t nq, const double* R, int64_t nr, int
 }
 
 /* ------------------------------------------------------------------ */
+/* Density estimate (Eq. 1) and the cross-validation scores of the      */
+/* introduction (CV_LK, CV_LS), with the Gaussian kernel                */
+/* ------------------------------------------------------------------ */
+
+/* V_{D,h} = integral over R^D of exp(-||z||^2 / 2h^2) dz = (2 pi h^2)^{D/2},
+ * the normalising constant of Eq. 1. */
+double orc_gauss_volume(int D, double h) {
+  const double pi = 3.14159265358979323846;
+  return pow(2.0 * pi * h * h, 0.5 * D);
+}
+
+/* Leave-one-out sums over one point set (Q = R):
+ * S_j = sum_{i != j} exp(-||x_j - x_i||^2 / 2h^2), Neumaier-compensated. */
+void orc_loo_sums(const double* X, int64_t n, int D, double h, double* S) {
+  const double inv = 1.0 / (2.0 * h * h);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t j = 0; j < n; ++j) {
+    double s = 0.0, comp = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (i == j) continue;
+      double d2 = 0.0;
+      for (int d = 0; d < D; ++d) {
+        const double t = X[j * D + d] - X[i * D + d];
+        d2 += t * t;
+      }
+      const double v = exp(-d2 * inv);
+      const double t = s + v;
+      if (fabs(s) >= fabs(v))
+        comp += (s - t) + v;
+      else
+        comp += (v - t) + s;
+      s = t;
+    }
+    S[j] = s + comp;
+  }
+}
+
+/* CV_LK(h) = (1/N) sum_j log p_{h,-j}(x_j) with the leave-one-out density
+ * p_{h,-j}(x_j) = S_j / ((N - 1) V_{D,h}) (Eq. 1 over the N - 1 other
+ * points); -inf when some S_j is 0. */
+double orc_cv_lk(const double* X, int64_t n, int D, double h) {
+  double* S = (double*)malloc(sizeof(double) * (size_t)n);
+  orc_loo_sums(X, n, D, h, S);
+  const double norm = (double)(n - 1) * orc_gauss_volume(D, h);
+  double acc = 0.0;
+  for (int64_t j = 0; j < n; ++j) acc += log(S[j] / norm);
+  free(S);
+  return acc / (double)n;
+}
+
+/* CV_LS(h) = (1/N) sum_j (p*_{-j}(x_j) - 2 p_{-j}(x_j)), p* the
+ * leave-one-out estimate with the convolution kernel K_h * K_h.
+ * Reading: the convolution of two Gaussians of standard deviation h is a
+ * Gaussian of standard deviation sqrt(2) h (variance 2h^2, the "2h" of
+ * the text), normalised by V_{D, sqrt(2) h}. */
+double orc_cv_ls(const double* X, int64_t n, int D, double h) {
+  double* S = (double*)malloc(sizeof(double) * (size_t)n);
+  double* Ss = (double*)malloc(sizeof(double) * (size_t)n);
+  const double hs = sqrt(2.0) * h;
+  orc_loo_sums(X, n, D, h, S);
+  orc_loo_sums(X, n, D, hs, Ss);
+  const double norm = (double)(n - 1) * orc_gauss_volume(D, h);
+  const double norm_s = (double)(n - 1) * orc_gauss_volume(D, hs);
+  double acc = 0.0;
+  for (int64_t j = 0; j < n; ++j) acc += Ss[j] / norm_s - 2.0 * S[j] / norm;
+  free(S);
+  free(Ss);
+  return acc / (double)n;
+}
+
+/* ------------------------------------------------------------------ */
 /* Expansions (Section 3.3) and translations (Section 3.5)             */
 /* All tables have radix pm; only multi-indices below p are written.   */
 /* ------------------------------------------------------------------ */
