@@ -116,6 +116,27 @@ const char* dfgt_last_error(const dfgt_ctx* ctx);
 dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
                        const dfgt_opts* opts, dfgt_tree** out);
 
+/* Cross-validation scores of a bandwidth sweep over one point set (the
+ * introduction's CV_LK and CV_LS, with the density estimate of Eq. 1 for
+ * the Gaussian kernel, V_{D,h} = (2 pi h^2)^{D/2}).  `tree` holds the
+ * reference set, which is also the query set; for each h_host[k]
+ *   cv_lk[k] = (1/N) sum_j log( S_j / ((N-1) V_{D,h}) ),
+ *   cv_ls[k] = (1/N) sum_j ( S*_j / ((N-1) V_{D,sqrt2 h}) - 2 S_j / ((N-1) V_{D,h}) ),
+ * S_j the leave-one-out sum at h and S*_j at sqrt(2) h (the convolution
+ * kernel K_h * K_h; the text's "bandwidth 2h" is read as variance 2h^2).
+ * Runs dfgt_sum(tree, tree) over the 2 nh bandwidths {h, sqrt(2) h} with
+ * the relative error eps of Definition 1.2 (S_j = G_j - 1, the self term
+ * being exact), then reduces on the device in float64.  lk_bound[k] and
+ * ls_bound[k] (may be NULL) bound |score - exact score| from that
+ * guarantee: (1/N) sum_j -log(1 - eps' G~_j / S~_j) and
+ * (1/N) sum_j eps' (G~*_j / ((N-1) V*) + 2 G~_j / ((N-1) V)),
+ * eps' = eps / (1 - eps); a leave-one-out sum that may be 0 gives an
+ * infinite lk bound, and an estimate S~_j <= 0 a score of -inf.
+ * Host outputs have nh entries; 1 <= nh <= 512; N >= 2. */
+dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh,
+                           double eps, double* cv_lk_host, double* cv_ls_host,
+                           double* lk_bound_host, double* ls_bound_host, dfgt_stats* stats);
+
 /* Choose the tree options that make a dual-tree sum of these points
  * fastest on this GPU.  No counterpart in the paper (its leaf size is
  * unstated): the leaf size and the exact-sum threshold base_block trade

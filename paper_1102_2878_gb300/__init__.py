@@ -172,6 +172,22 @@ def kde_sum_batches(ctx: Context, query_batches, rtree: Tree, hs, eps: float, le
     return list(torch.split(G, sizes, dim=1)), st
 
 
+def cv_scores(ctx: Context, tree: Tree, hs, eps: float):
+    """dfgt_cv_scores: CV_LK and CV_LS for each bandwidth over the tree's
+    point set, with bounds on their error; returns a dict of numpy arrays."""
+    ha, hp = _hs(hs)
+    nh = len(ha)
+    outs = {k: np.empty(nh) for k in ("cv_lk", "cv_ls", "lk_bound", "ls_bound")}
+    ptr = {k: v.ctypes.data_as(C.POINTER(C.c_double)) for k, v in outs.items()}
+    stats = _lib.Stats()
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_cv_scores(ctx.h, tree.h, hp, nh, float(eps), ptr["cv_lk"], ptr["cv_ls"],
+                                ptr["lk_bound"], ptr["ls_bound"], C.byref(stats))
+    ctx.check(st, "dfgt_cv_scores")
+    outs["stats"] = stats.as_dict()
+    return outs
+
+
 def autotune(ctx: Context, points, hs, eps: float, trials: int = 2, p_max: int = 0, eps_fp: float = 0.0):
     """dfgt_autotune: the leaf size and exact-sum threshold that make a
     build + sum of these points fastest; returns (options dict, ms)."""

@@ -67,6 +67,9 @@ SIGNATURES = {
     "dfgt_tree_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
     "dfgt_apply_pairs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p] + [C.c_void_p] * 4 +
                          [C.c_int, C.c_double, C.c_void_p]),
+    "dfgt_cv_scores": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double,
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(Stats)]),
     "dfgt_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_int,
                                 C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double)]),
 }

@@ -361,7 +361,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,
-                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes};
+                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes, &ctx->cv_buf};
   for (DevBuf* b : bufs) b->release();
   if (ctx->tpool) {
     // trees that outlive the context return their arenas in default-stream order
@@ -424,6 +424,47 @@ dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtr
   ctx->err.clear();
   if (stats) std::memset(stats, 0, sizeof(*stats));
   return run_sum(ctx, qtree, rtree, h_host, nh, eps, G_dev, stats);
+}
+
+dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh, double eps,
+                           double* cv_lk, double* cv_ls, double* lk_bound, double* ls_bound,
+                           dfgt_stats* stats) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!tree || !cv_lk || !cv_ls || tree->n < 2)
+    return fail(ctx, DFGT_EINVAL, "dfgt_cv_scores: need a tree of at least 2 points and score outputs");
+  if (bad_h(h_host, nh) || nh > 512)
+    return fail(ctx, DFGT_EINVAL, "dfgt_cv_scores: need 1..512 finite bandwidths > 0");
+  const int n = (int)tree->n, d = tree->d;
+  std::vector<double> h2(2 * (size_t)nh), norm(2 * (size_t)nh);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < nh; ++k) {
+    h2[k] = h_host[k];
+    h2[nh + k] = std::sqrt(2.0) * h_host[k];
+  }
+  for (int k = 0; k < 2 * nh; ++k) norm[k] = (double)(n - 1) * std::pow(2.0 * pi * h2[k] * h2[k], 0.5 * d);
+  CK(cudaSetDevice(ctx->device));
+  CK(ctx->io_g.ensure(2 * (size_t)nh * n * sizeof(double)));
+  dfgt_status rc = dfgt_sum(ctx, tree, tree, h2.data(), 2 * nh, eps, ctx->io_g.as<double>(), stats);
+  if (rc != DFGT_OK) return rc;
+  const int nblk = std::max(1, std::min(304, (n + 1023) / 1024));
+  const size_t nnorm = 2 * (size_t)nh, npart = (size_t)nh * nblk * 4, nout = (size_t)nh * 4;
+  CK(ctx->cv_buf.ensure((nnorm + npart + nout) * sizeof(double)));
+  double* dnorm = ctx->cv_buf.as<double>();
+  double* dpart = dnorm + nnorm;
+  double* dout = dpart + npart;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(dnorm, norm.data(), nnorm * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(launch_cv_scores(ctx->io_g.as<double>(), n, nh, dnorm, eps, dpart, nblk, dout, s, &ctx->launches));
+  std::vector<double> out(nout);
+  CK(cudaMemcpyAsync(out.data(), dout, nout * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < nh; ++k) {
+    cv_lk[k] = out[4 * k];
+    cv_ls[k] = out[4 * k + 2];
+    if (lk_bound) lk_bound[k] = out[4 * k + 1];
+    if (ls_bound) ls_bound[k] = out[4 * k + 3];
+  }
+  return DFGT_OK;
 }
 
 dfgt_status dfgt_autotune(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d, const double* h_host,

@@ -92,6 +92,7 @@ struct dfgt_ctx {
   DevBuf gacc;           // double [nh][nq]
   DevBuf io_q, io_r, io_g;  // dfgt_kde_host staging
   DevBuf bf_partials;       // brute-force slice partials
+  DevBuf cv_buf;            // cross-validation normalisers, partials and scores
   DevBuf bscratch;          // tree-build per-point scratch
   DevBuf bnodes;            // tree-build node arrays (copied into the tree's arena)
   std::shared_ptr<TreePool> tpool;
@@ -152,6 +153,11 @@ cudaError_t launch_bruteforce_split(const float* q, int nq, const float* r, int 
 cudaError_t launch_bruteforce(const float* q, int nq, const float* r, int nr, int d,
                               const double* h_host, int nh, double* G, DevBuf& scratch,
                               cudaStream_t s, long long* launches);
+
+// cv.cu: cross-validation scores from the sums G [2 nh][n] at h and sqrt(2) h;
+// part holds nh * nblk * 4 doubles, out nh * 4 (CV_LK, bound, CV_LS, bound).
+cudaError_t launch_cv_scores(const double* G, int n, int nh, const double* norm, double eps, double* part,
+                             int nblk, double* out, cudaStream_t s, long long* launches);
 
 // tree.cu: build the tree (points, nodes, raw moments) on ctx's stream.
 dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n, int d,
