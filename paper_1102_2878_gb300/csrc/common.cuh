@@ -226,6 +226,7 @@ enum : int { kFlagSplitQ = 1 };
 enum : int {
   kStNonFinite = 1,   // a coordinate was NaN/Inf
   kStOverflow = 2,    // a work list ran out of room (retry with more)
+  kStTimeout = 4,     // a bounded grid-barrier wait gave up
 };
 
 }  // namespace dfgt

@@ -96,7 +96,7 @@ struct dfgt_ctx {
   DevBuf bscratch;          // tree-build per-point scratch
   DevBuf bnodes;            // tree-build node arrays (copied into the tree's arena)
   std::shared_ptr<TreePool> tpool;
-  int last_depth = 0;         // depth of the last tree built (sizes the next build's first batch)
+  int build_grid = 0;         // blocks of the cooperative level build (0: not yet chosen)
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned

@@ -2,15 +2,15 @@
 // and of the raw far-field moments of every node (Eq. far_field_moments at
 // the leaves, the far-to-far translation of Lemma 3.5 upward).
 //
-// The build is level-synchronous: every level computes the tight bounding
-// box of each of its nodes, splits the widest dimension at the box
-// midpoint when the node holds more points than the leaf threshold, and
-// stably partitions the points of every split node (x[sd] <= sc to the
-// left) with one device-wide prefix sum.  Nodes are numbered level by
-// level, so each level is a contiguous index range and the two children of
-// a node are adjacent.  A split that would leave one side empty (all
-// points equal along the widest side, or a midpoint that rounds onto the
-// upper bound) turns the node into a leaf.
+// The build is level-synchronous, all levels in one persistent cooperative
+// launch: every level has the tight bounding box of each of its nodes,
+// splits the widest dimension at the box midpoint when the node holds more
+// points than the leaf threshold, and stably partitions the points of
+// every split node (x[sd] <= sc to the left) with one device-wide prefix
+// sum.  Nodes are numbered level by level, so each level is a contiguous
+// index range and the two children of a node are adjacent.  A split that
+// would leave one side empty (all points equal along the widest side, or a
+// midpoint that rounds onto the upper bound) turns the node into a leaf.
 //
 // Moments are kept unscaled, m_alpha = sum_r (r-c)^alpha / alpha!, in
 // float64 about the box center c; the bandwidth scaling (2h^2)^(-|alpha|/2)
@@ -34,214 +34,504 @@ constexpr int kMaxLevels = 128;
 constexpr int kDefaultLeaf = 128;
 constexpr long long kDefaultBaseBlock = 4096;
 
-__global__ void k_pad_points(const float* __restrict__ in, int n, int d, int dp,
-                             float* __restrict__ out, int* __restrict__ perm,
-                             int* __restrict__ pnode, int* __restrict__ status) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  bool bad = false;
-  for (int k = 0; k < dp; ++k) {
-    float v = k < d ? in[(size_t)i * d + k] : 0.f;
-    if (!isfinite(v)) bad = true;
-    out[(size_t)i * dp + k] = v;
-  }
-  perm[i] = i;
-  pnode[i] = 0;
-  if (bad) atomicOr(status, kStNonFinite);
+// The root: all points, no children; level 0 = [0, 1).  Its box is formed
+// by the level build.
+__global__ void k_init_root(int n, int* beg, int* cnt, int* left, int* parent, int* lv) {
+  beg[0] = 0;
+  cnt[0] = n;
+  left[0] = -1;
+  parent[0] = -1;
+  lv[0] = 0;
+  lv[1] = 1;
 }
 
-// The root: all points, an empty box to be filled by k_bbox; level 0 = [0, 1).
-__global__ void k_init_root(int n, int d, int* beg, int* cnt, int* left, int* parent, float* lo, float* hi,
-                            int* lv) {
-  if (threadIdx.x == 0) {
-    beg[0] = 0;
-    cnt[0] = n;
-    left[0] = -1;
-    parent[0] = -1;
-    lv[0] = 0;
-    lv[1] = 1;
-  }
-  for (int k = threadIdx.x; k < d; k += blockDim.x) {
-    lo[k] = INFINITY;
-    hi[k] = -INFINITY;
-  }
+// ------------------------------------------------------------ level build
+// All levels run in one cooperative launch: one block per SM, all
+// co-resident, meeting at a grid barrier between the phases of a level.
+// Block b owns a fixed slice of the point positions and, at every level, a
+// slice of that level's nodes.  A level takes three phases:
+//   1. each point of a node that splits is flagged when it goes left
+//      (x[sd] <= sc); the flags are counted per block and per node;
+//   2. the flags' device-wide exclusive prefix (the stable left rank of
+//      every point) and each node's decision: it splits when the split rule
+//      holds and both sides are non-empty, else it is a leaf;
+//   3. children are numbered by the prefix of split decisions over the
+//      level (so each level is a contiguous node range and siblings are
+//      adjacent), the points are moved into their child's range in the
+//      other point buffer, and the children's tight boxes are formed from
+//      the moved points.
+// The phases are latency-bound (a few dependent L2 round trips each), so a
+// thread issues the loads of all its points before using any of them.  The
+// launch ends when a level has no split, or when the next level would not
+// fit the node arrays; then the host grows them and launches again at that
+// level.
+constexpr int kBT = 1024;       // threads per block of the level build
+constexpr int kKB = 2;          // points per thread per pass
+constexpr int kMaxGrid = 1024;  // blocks of the level build at most
+constexpr long long kSpinLimit = 1LL << 25;  // barrier polls before giving up (~1 s)
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// Tight bounding boxes of the nodes of the current level (min/max over each
-// node's points).  Points are contiguous per node, so most blocks see one
-// node and reduce in shared memory before one atomic per coordinate.
-__global__ void __launch_bounds__(kT) k_bbox(const float* __restrict__ pts, int n, int d, int dp,
-                                             const int* __restrict__ pnode, float* lo, float* hi) {
-  __shared__ int s_nd;
-  __shared__ float s_min[kT / 32], s_max[kT / 32];
-  const int i = blockIdx.x * kT + threadIdx.x;
-  const int nd = i < n ? pnode[i] : -1;
-  if (threadIdx.x == 0) s_nd = nd;
+// Grid barrier of a cooperative launch on a monotone arrival counter:
+// every block passes the same sequence of barriers, so the k-th barrier
+// opens when the counter reaches k * gridDim.x (`target`, kept by each
+// block).  The wait is bounded: a block that polls kSpinLimit times sets
+// kStTimeout and leaves; every block returns false from then on, as it does
+// once a non-finite coordinate has been seen.
+__device__ bool grid_barrier(unsigned* bar, int* status, unsigned& target) {
+  __shared__ int s_ok;
   __syncthreads();
-  const bool uniform = __syncthreads_and(nd == s_nd);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (uniform) {
-    if (nd < 0) return;
-    for (int k = 0; k < d; ++k) {
-      float v = pts[(size_t)i * dp + k];
-      float mn = v, mx = v;
-      for (int o = 16; o > 0; o >>= 1) {
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+    long long it = 0;
+    while ((int)(ld_acquire(bar) - target) < 0) {
+      if (++it > kSpinLimit) {
+        atomicOr(status, kStTimeout);
+        break;
       }
-      if (lane == 0) { s_min[wid] = mn; s_max[wid] = mx; }
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int w = 1; w < kT / 32; ++w) { mn = fminf(mn, s_min[w]); mx = fmaxf(mx, s_max[w]); }
-        atomic_min_f(&lo[(size_t)nd * d + k], mn);
-        atomic_max_f(&hi[(size_t)nd * d + k], mx);
-      }
-      __syncthreads();
     }
-    return;
+    __threadfence();
+    s_ok = (*reinterpret_cast<volatile int*>(status) & (kStTimeout | kStNonFinite)) == 0;
   }
-  // every lane of the warp is still present here (no lane has returned)
-  const unsigned peers = __match_any_sync(0xffffffffu, nd);
-  if (nd < 0) return;
-  const int leader = __ffs(peers) - 1;
-  for (int k = 0; k < d; ++k) {
-    float v = pts[(size_t)i * dp + k];
-    if (peers == 0xffffffffu) {
-      float mn = v, mx = v;
-      for (int o = 16; o > 0; o >>= 1) {
-        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      }
-      if (lane == leader) {
-        atomic_min_f(&lo[(size_t)nd * d + k], mn);
-        atomic_max_f(&hi[(size_t)nd * d + k], mx);
-      }
-    } else {
-      atomic_min_f(&lo[(size_t)nd * d + k], v);
-      atomic_max_f(&hi[(size_t)nd * d + k], v);
-    }
-  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
-// Split rule of a node: it splits only if it holds more than `leaf` points
+// Exclusive prefix of v over the block's threads; `total` gets the sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, int& total, int* sw) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sw[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = lane < kBT / 32 ? sw[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kBT / 32) sw[lane] = t;
+  }
+  __syncthreads();
+  const int before = w > 0 ? sw[w - 1] : 0;
+  total = sw[kBT / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// pre[0..G] = exclusive prefix of c[0..G) (and the total at pre[G]).
+__device__ void grid_prefix(const int* c, int G, int* pre, int* sw) {
+  int run = 0;
+  for (int base = 0; base < G; base += kBT) {
+    const int i = base + threadIdx.x;
+    const int v = i < G ? __ldcg(c + i) : 0;
+    int tot;
+    const int ex = block_exclusive_scan(v, tot, sw);
+    if (i < G) pre[i] = run + ex;
+    run += tot;
+  }
+  if (threadIdx.x == 0) pre[G] = run;
+  __syncthreads();
+}
+
+// Split rule of node j: it splits only if it holds more than `leaf` points
 // and its box has positive extent, along its widest side sd at the box
-// midpoint sc (Algorithm 2).
-__device__ __forceinline__ bool split_rule(int j, int d, int leaf, const int* __restrict__ cnt,
-                                           const float* __restrict__ lo, const float* __restrict__ hi,
-                                           int& sd, float& sc) {
+// midpoint sc (Algorithm 2).  Reads data other blocks wrote (L2 loads).
+__device__ __forceinline__ bool split_rule(int j, int d, int leaf, const int* cnt, const float* lo,
+                                           const float* hi, int& sd, float& sc) {
   sd = 0;
-  float ext = hi[(size_t)j * d] - lo[(size_t)j * d];
+  float ext = __ldcg(hi + (size_t)j * d) - __ldcg(lo + (size_t)j * d);
   for (int k = 1; k < d; ++k) {
-    const float x = hi[(size_t)j * d + k] - lo[(size_t)j * d + k];
+    const float x = __ldcg(hi + (size_t)j * d + k) - __ldcg(lo + (size_t)j * d + k);
     if (x > ext) { ext = x; sd = k; }
   }
-  sc = 0.5f * (lo[(size_t)j * d + sd] + hi[(size_t)j * d + sd]);
-  return cnt[j] > leaf && ext > 0.f;
+  sc = 0.5f * (__ldcg(lo + (size_t)j * d + sd) + __ldcg(hi + (size_t)j * d + sd));
+  return __ldcg(cnt + j) > leaf && ext > 0.f;
 }
 
-__global__ void k_flag_left(const float* __restrict__ pts, int n, int dp, int d, int leaf,
-                            const int* __restrict__ pnode, const int* __restrict__ cnt,
-                            const float* __restrict__ lo, const float* __restrict__ hi,
-                            int* __restrict__ flag) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int nd = pnode[i];
-  int f = 0;
-  int sd;
-  float sc;
-  if (nd >= 0 && split_rule(nd, d, leaf, cnt, lo, hi, sd, sc)) f = pts[(size_t)i * dp + sd] <= sc ? 1 : 0;
-  flag[i] = f;
-}
+struct LevelArgs {
+  const float* in;                  // caller's points [n][d]
+  float *pbuf0, *pbuf1;             // padded points [n][dp], ping-pong
+  int *perm0, *perm1;               // original index of each point
+  int *pnode0, *pnode1;             // node of each point at the current level (-1: in a leaf)
+  int* flag;                        // [n] goes left
+  int* leftpos;                     // [n] exclusive prefix of flag
+  int* bcnt;                        // [3 G] per block: flags, splits, leaves
+  float *lo, *hi;                   // node boxes [cap][d]
+  int *beg, *cnt, *left, *parent;   // node records [cap]
+  int* nleft;                       // [cap] points going left
+  int* lp0;                         // [cap] left prefix at the node's first point
+  int* sloc;                        // [cap] split: rank among the block's splits; leaf: -1 - rank
+  int* leaves;                      // [cap] leaf ids in node order
+  int* lv;                          // level table: [3L] first node, [3L+1] end, [3L+2] splits
+  int* ctl;                         // [0] status, [1] point buffer, [2] level, [3] leaves, [4] done, [5] nodes needed
+  unsigned* bar;                    // grid barrier counter (zero at launch)
+  int n, d, dp, leaf, cap, init_from, max_levels;
+};
 
-// Level L occupies nodes [lv[3L], lv[3L+1]); lv[3L+2] is its number of
-// splits.  Node kernels of a level run over `bound` >= its node count.
-__global__ void k_node_finalize(const int* __restrict__ lv, int L, int bound, int d, int leaf,
-                                const int* __restrict__ beg, const int* __restrict__ cnt,
-                                const float* __restrict__ lo, const float* __restrict__ hi,
-                                const int* __restrict__ leftpos, int* __restrict__ split,
-                                int* __restrict__ nleft) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= bound) return;
-  const int a = lv[3 * L], e = lv[3 * L + 1];
-  const int j = a + t;
-  if (j >= e) {
-    split[t] = 0;
-    nleft[t] = 0;
-    return;
-  }
-  int sd;
-  float sc;
-  const bool want = split_rule(j, d, leaf, cnt, lo, hi, sd, sc);
-  const int b = beg[j], c = cnt[j];
-  const int nl = leftpos[b + c] - leftpos[b];
-  split[t] = (want && nl > 0 && nl < c) ? 1 : 0;
-  nleft[t] = nl;
-}
+// Per-warp partial boxes of the children of one pass (phase 3).
+struct WarpBox {
+  int c0;         // left child of the warp's parent, or -1
+  unsigned lr;    // bit 0: has left points, bit 1: has right points
+};
 
-// Children of the level's split nodes, numbered level by level; also
-// writes the next level's range.  The caller reserves room for every node
-// the level can create; a request beyond `cap` is refused and flagged.
-__global__ void k_make_children(int* __restrict__ lv, int L, int bound, int d, int cap,
-                                const int* __restrict__ split, const int* __restrict__ soff,
-                                const int* __restrict__ nleft, int* beg, int* cnt, int* left,
-                                int* parent, float* lo, float* hi, int* __restrict__ status) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int a = lv[3 * L], e = lv[3 * L + 1];
-  const int total = soff[bound];
-  const bool fits = (long long)e + 2LL * total <= cap;
-  if (t == 0) {
-    lv[3 * L + 2] = fits ? total : 0;
-    lv[3 * (L + 1)] = e;
-    lv[3 * (L + 1) + 1] = fits ? e + 2 * total : e;
-    if (!fits) atomicOr(status, kStOverflow);
-  }
-  if (t >= bound) return;
-  const int j = a + t;
-  if (j >= e) return;
-  if (!fits || !split[t]) {
-    left[j] = -1;
-    return;
-  }
-  const int c0 = e + 2 * soff[t];
-  const int nl = nleft[t];
-  left[j] = c0;
-  beg[c0] = beg[j];
-  cnt[c0] = nl;
-  beg[c0 + 1] = beg[j] + nl;
-  cnt[c0 + 1] = cnt[j] - nl;
-  parent[c0] = parent[c0 + 1] = j;
-  left[c0] = left[c0 + 1] = -1;
-  for (int k = 0; k < d; ++k) {
-    lo[(size_t)c0 * d + k] = lo[(size_t)(c0 + 1) * d + k] = INFINITY;
-    hi[(size_t)c0 * d + k] = hi[(size_t)(c0 + 1) * d + k] = -INFINITY;
-  }
-}
+__global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
+  __shared__ int sw[kBT / 32];
+  __shared__ int sPre[2][kMaxGrid + 1];
+  __shared__ float sRed[2][kBT / 32];
+  __shared__ WarpBox sWB[kBT / 32];
+  __shared__ float sBox[kBT / 32][4][4];  // [warp][lmin, lmax, rmin, rmax][dimension, first 4]
+  const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int n = A.n, d = A.d, dp = A.dp;
+  const int PC = (n + G - 1) / G;
+  const int p0 = min(n, b * PC), p1 = min(n, p0 + PC);
+  unsigned target = 0;
+  int cur = __ldcg(A.ctl + 1), level = __ldcg(A.ctl + 2), nleaves = __ldcg(A.ctl + 3);
 
-__global__ void k_scatter(int n, int dp, const int* __restrict__ lv, int L, const float* __restrict__ pin,
-                          const int* __restrict__ perm_in, const int* __restrict__ pnode_in,
-                          const int* __restrict__ flag, const int* __restrict__ leftpos,
-                          const int* __restrict__ beg, const int* __restrict__ left,
-                          const int* __restrict__ nleft, float* __restrict__ pout,
-                          int* __restrict__ perm_out, int* __restrict__ pnode_out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int a = lv[3 * L];
-  const int nd = pnode_in[i];
-  int dst = i, child = -1;
-  if (nd >= 0 && left[nd] >= 0) {
-    const int b0 = beg[nd];
-    const int lrank = leftpos[i] - leftpos[b0];
-    if (flag[i]) {
-      dst = b0 + lrank;
-      child = left[nd];
-    } else {
-      dst = b0 + nleft[nd - a] + (i - b0 - lrank);
-      child = left[nd] + 1;
+  // boxes and left counts of the nodes this launch may create
+  for (size_t j = (size_t)A.init_from + (size_t)b * kBT + tid; j < (size_t)A.cap; j += (size_t)G * kBT) {
+    A.nleft[j] = 0;
+    for (int k = 0; k < d; ++k) {
+      A.lo[j * d + k] = INFINITY;
+      A.hi[j * d + k] = -INFINITY;
     }
   }
-  for (int k = 0; k < dp; ++k) pout[(size_t)dst * dp + k] = pin[(size_t)i * dp + k];
-  perm_out[dst] = perm_in[i];
-  pnode_out[dst] = child;
+  if (!grid_barrier(A.bar, A.ctl, target)) return;
+
+  if (A.init_from == 0) {
+    // the root: padded copies of the points and its box
+    bool bad = false;
+    for (int i = p0 + tid; i < p1; i += kBT) {
+      for (int k = 0; k < dp; ++k) {
+        const float v = k < d ? A.in[(size_t)i * d + k] : 0.f;
+        if (!isfinite(v)) bad = true;
+        A.pbuf0[(size_t)i * dp + k] = v;
+      }
+      A.perm0[i] = i;
+      A.pnode0[i] = 0;
+    }
+    if (bad) atomicOr(A.ctl, kStNonFinite);
+    for (int k = 0; k < d; ++k) {
+      float mn = INFINITY, mx = -INFINITY;
+      for (int i = p0 + tid; i < p1; i += kBT) {
+        const float v = A.in[(size_t)i * d + k];
+        mn = fminf(mn, v);
+        mx = fmaxf(mx, v);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      }
+      if (lane == 0) { sRed[0][wid] = mn; sRed[1][wid] = mx; }
+      __syncthreads();
+      if (tid == 0 && p1 > p0) {
+        for (int w = 1; w < kBT / 32; ++w) { mn = fminf(mn, sRed[0][w]); mx = fmaxf(mx, sRed[1][w]); }
+        atomic_min_f(A.lo + k, mn);
+        atomic_max_f(A.hi + k, mx);
+      }
+      __syncthreads();
+    }
+    if (!grid_barrier(A.bar, A.ctl, target)) return;
+  }
+
+  for (;;) {
+    const int a = __ldcg(A.lv + 3 * level), e = __ldcg(A.lv + 3 * level + 1);
+    const float* pin = cur ? A.pbuf1 : A.pbuf0;
+    float* pout = cur ? A.pbuf0 : A.pbuf1;
+    const int* permin = cur ? A.perm1 : A.perm0;
+    int* permout = cur ? A.perm0 : A.perm1;
+    const int* pnin = cur ? A.pnode1 : A.pnode0;
+    int* pnout = cur ? A.pnode0 : A.pnode1;
+    const int nn = e - a, NC = (nn + G - 1) / G;
+    const int j0 = a + min(nn, b * NC), j1 = a + min(nn, b * NC + NC);
+
+    // phase 1: left flags, counted per block and per node
+    int nflag = 0;
+    for (int c0 = p0; c0 < p1; c0 += kBT * kKB) {
+      int nd[kKB], sd[kKB], f[kKB];
+      float sc[kKB];
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) {
+        const int i = c0 + k * kBT + tid;
+        nd[k] = i < p1 ? __ldcg(pnin + i) : -1;
+      }
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) f[k] = nd[k] >= 0 && split_rule(nd[k], d, A.leaf, A.cnt, A.lo, A.hi, sd[k], sc[k]);
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) {
+        const int i = c0 + k * kBT + tid;
+        if (f[k]) f[k] = __ldcg(pin + (size_t)i * dp + sd[k]) <= sc[k] ? 1 : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) {
+        const int i = c0 + k * kBT + tid;
+        if (i < p1) A.flag[i] = f[k];
+        nflag += f[k];
+        const unsigned m = __ballot_sync(0xffffffffu, f[k]);
+        if (f[k]) {
+          const unsigned peers = __match_any_sync(m, nd[k]);
+          if (lane == __ffs(peers) - 1) atomicAdd(A.nleft + nd[k], __popc(peers));
+        }
+      }
+    }
+    {
+      int tot;
+      block_exclusive_scan(nflag, tot, sw);
+      if (tid == 0) A.bcnt[b] = tot;
+    }
+    if (!grid_barrier(A.bar, A.ctl, target)) return;
+
+    // phase 2: left ranks of the points (and of each node's first point),
+    // decisions of the nodes
+    {
+      int pre;
+      block_exclusive_scan(tid < b ? __ldcg(A.bcnt + tid) : 0, pre, sw);  // G <= kBT
+      int run = pre;
+      for (int c0 = p0; c0 < p1; c0 += kBT * kKB) {
+        int fk[kKB], nd[kKB], np[kKB];
+#pragma unroll
+        for (int k = 0; k < kKB; ++k) {
+          const int i = c0 + k * kBT + tid;
+          fk[k] = i < p1 ? A.flag[i] : 0;
+          nd[k] = i < p1 ? __ldcg(pnin + i) : -1;
+          np[k] = (i < p1 && i > 0) ? __ldcg(pnin + i - 1) : -2;
+        }
+#pragma unroll
+        for (int k = 0; k < kKB; ++k) {
+          const int i = c0 + k * kBT + tid;
+          int tot;
+          const int ex = block_exclusive_scan(fk[k], tot, sw);
+          if (i < p1) {
+            A.leftpos[i] = run + ex;
+            if (nd[k] >= 0 && nd[k] != np[k]) A.lp0[nd[k]] = run + ex;
+          }
+          run += tot;
+        }
+      }
+    }
+    {
+      int ns = 0, nl = 0;
+      for (int base = j0; base < j1; base += kBT) {
+        const int j = base + tid;
+        int sp = 0, lf = 0;
+        if (j < j1) {
+          int sd;
+          float sc;
+          const bool want = split_rule(j, d, A.leaf, A.cnt, A.lo, A.hi, sd, sc);
+          const int c = __ldcg(A.cnt + j), l = __ldcg(A.nleft + j);
+          sp = (want && l > 0 && l < c) ? 1 : 0;
+          lf = 1 - sp;
+        }
+        int ts, tl;
+        const int es = block_exclusive_scan(sp, ts, sw);
+        const int el = block_exclusive_scan(lf, tl, sw);
+        if (j < j1) A.sloc[j] = sp ? ns + es : -1 - (nl + el);
+        ns += ts;
+        nl += tl;
+      }
+      if (tid == 0) {
+        A.bcnt[G + b] = ns;
+        A.bcnt[2 * G + b] = nl;
+      }
+    }
+    if (!grid_barrier(A.bar, A.ctl, target)) return;
+
+    // phase 3: children, leaves, scatter
+    grid_prefix(A.bcnt + G, G, sPre[0], sw);
+    grid_prefix(A.bcnt + 2 * G, G, sPre[1], sw);
+    const int S = sPre[0][G], NL = sPre[1][G];
+    if (S == 0) {
+      // the last level: all of its nodes are leaves
+      for (int j = j0 + tid; j < j1; j += kBT) A.leaves[nleaves + sPre[1][b] + (-1 - __ldcg(A.sloc + j))] = j;
+      if (b == 0 && tid == 0) {
+        A.lv[3 * level + 2] = 0;
+        A.ctl[1] = cur;
+        A.ctl[2] = level;
+        A.ctl[3] = nleaves + NL;
+        A.ctl[4] = 1;
+        A.ctl[5] = e;
+      }
+      return;
+    }
+    const long long e2 = (long long)e + 2LL * S;
+    if (e2 > A.cap || level + 1 >= A.max_levels) {
+      // no room for the next level: undo this level's left counts and stop
+      // here; the level is redone after the host has grown the node arrays
+      for (int j = j0 + tid; j < j1; j += kBT) A.nleft[j] = 0;
+      if (b == 0 && tid == 0) {
+        A.ctl[1] = cur;
+        A.ctl[2] = level;
+        A.ctl[3] = nleaves;
+        A.ctl[4] = 0;
+        A.ctl[5] = (int)min(e2, (long long)INT32_MAX);
+      }
+      return;
+    }
+    for (int j = j0 + tid; j < j1; j += kBT) {
+      const int s = __ldcg(A.sloc + j);
+      if (s >= 0) {
+        const int c0 = e + 2 * (sPre[0][b] + s);
+        const int bg = __ldcg(A.beg + j), c = __ldcg(A.cnt + j), l = __ldcg(A.nleft + j);
+        A.left[j] = c0;
+        A.beg[c0] = bg;
+        A.cnt[c0] = l;
+        A.beg[c0 + 1] = bg + l;
+        A.cnt[c0 + 1] = c - l;
+        A.parent[c0] = A.parent[c0 + 1] = j;
+        A.left[c0] = A.left[c0 + 1] = -1;
+      } else {
+        A.leaves[nleaves + sPre[1][b] + (-1 - s)] = j;
+      }
+    }
+    if (b == 0 && tid == 0) {
+      A.lv[3 * level + 2] = S;
+      A.lv[3 * (level + 1)] = e;
+      A.lv[3 * (level + 1) + 1] = (int)e2;
+    }
+    for (int c0 = p0; c0 < p1; c0 += kBT * kKB) {
+      int nd[kKB], f[kKB], lpos[kKB], pm[kKB], s[kKB], b0[kKB], nl[kKB], l0[kKB];
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) {
+        const int i = c0 + k * kBT + tid;
+        const bool in = i < p1;
+        nd[k] = in ? __ldcg(pnin + i) : -1;
+        f[k] = in ? A.flag[i] : 0;
+        lpos[k] = in ? A.leftpos[i] : 0;
+        pm[k] = in ? __ldcg(permin + i) : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) {
+        s[k] = -1;
+        b0[k] = nl[k] = l0[k] = 0;
+        if (nd[k] >= 0) {
+          s[k] = __ldcg(A.sloc + nd[k]);
+          b0[k] = __ldcg(A.beg + nd[k]);
+          nl[k] = __ldcg(A.nleft + nd[k]);
+          l0[k] = __ldcg(A.lp0 + nd[k]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kKB; ++k) {
+        const int i = c0 + k * kBT + tid;
+        const bool in = i < p1;
+        int ch = -1, dst = i;
+        if (s[k] >= 0) {
+          const int cl = e + 2 * (sPre[0][(nd[k] - a) / NC] + s[k]);
+          const int lrank = lpos[k] - l0[k];
+          if (f[k]) {
+            dst = b0[k] + lrank;
+            ch = cl;
+          } else {
+            dst = b0[k] + nl[k] + (i - b0[k] - lrank);
+            ch = cl + 1;
+          }
+        }
+        if (in) {
+          if ((unsigned)dst < (unsigned)n) {
+            if (dp == 4) {
+              const float4 v = __ldcg(reinterpret_cast<const float4*>(pin) + i);
+              reinterpret_cast<float4*>(pout)[dst] = v;
+            } else {
+              for (int q = 0; q < dp; ++q) pout[(size_t)dst * dp + q] = __ldcg(pin + (size_t)i * dp + q);
+            }
+            permout[dst] = pm[k];
+            pnout[dst] = ch;
+          } else {
+            atomicOr(A.ctl, kStOverflow);  // inconsistent ranks: never expected
+            ch = -1;
+          }
+        }
+        // children's boxes: a warp whose points share one parent (points are
+        // contiguous per node) reduces with shuffles; the warps of the block
+        // then merge runs of equal parents, so each child gets one atomic
+        // per block and coordinate; other warps update per point
+        const bool valid = in && ch >= 0;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        const int first = vm ? __ffs(vm) - 1 : 0;
+        const int nd0 = __shfl_sync(0xffffffffu, nd[k], first);
+        const int c00 = __shfl_sync(0xffffffffu, ch - (f[k] ? 0 : 1), first);
+        const bool uni = vm != 0 && __all_sync(0xffffffffu, !valid || nd[k] == nd0);
+        const unsigned lm = __ballot_sync(0xffffffffu, valid && f[k]), rm = vm & ~lm;
+        if (lane == 0) {
+          sWB[wid].c0 = uni ? c00 : -1;
+          sWB[wid].lr = (lm ? 1u : 0u) | (rm ? 2u : 0u);
+        }
+        for (int q0 = 0; q0 < d; q0 += 4) {
+          // up to four coordinates per round through shared memory
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const int q = q0 + qq;
+            if (q >= d) break;
+            const float v = valid ? __ldcg(pin + (size_t)i * dp + q) : 0.f;
+            if (uni) {
+              float lmn = (valid && f[k]) ? v : INFINITY, lmx = (valid && f[k]) ? v : -INFINITY;
+              float rmn = (valid && !f[k]) ? v : INFINITY, rmx = (valid && !f[k]) ? v : -INFINITY;
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1) {
+                lmn = fminf(lmn, __shfl_xor_sync(0xffffffffu, lmn, o));
+                lmx = fmaxf(lmx, __shfl_xor_sync(0xffffffffu, lmx, o));
+                rmn = fminf(rmn, __shfl_xor_sync(0xffffffffu, rmn, o));
+                rmx = fmaxf(rmx, __shfl_xor_sync(0xffffffffu, rmx, o));
+              }
+              if (lane == 0) {
+                sBox[wid][0][qq] = lmn;
+                sBox[wid][1][qq] = lmx;
+                sBox[wid][2][qq] = rmn;
+                sBox[wid][3][qq] = rmx;
+              }
+            } else if (valid) {
+              atomic_min_f(A.lo + (size_t)ch * d + q, v);
+              atomic_max_f(A.hi + (size_t)ch * d + q, v);
+            }
+          }
+          __syncthreads();
+          // thread (w, qq) of warp 0 .. : one thread per warp slot and
+          // coordinate closes the run of equal parents that ends at its warp
+          if (tid < (kBT / 32) * 4) {
+            const int w = tid >> 2, qq = tid & 3, q = q0 + qq;
+            const int cw = sWB[w].c0;
+            const bool ends = cw >= 0 && q < d && (w == kBT / 32 - 1 || sWB[w + 1].c0 != cw);
+            if (ends) {
+              float lmn = INFINITY, lmx = -INFINITY, rmn = INFINITY, rmx = -INFINITY;
+              unsigned lr = 0;
+              for (int u = w; u >= 0 && sWB[u].c0 == cw; --u) {
+                lmn = fminf(lmn, sBox[u][0][qq]);
+                lmx = fmaxf(lmx, sBox[u][1][qq]);
+                rmn = fminf(rmn, sBox[u][2][qq]);
+                rmx = fmaxf(rmx, sBox[u][3][qq]);
+                lr |= sWB[u].lr;
+              }
+              if (lr & 1u) {
+                atomic_min_f(A.lo + (size_t)cw * d + q, lmn);
+                atomic_max_f(A.hi + (size_t)cw * d + q, lmx);
+              }
+              if (lr & 2u) {
+                atomic_min_f(A.lo + (size_t)(cw + 1) * d + q, rmn);
+                atomic_max_f(A.hi + (size_t)(cw + 1) * d + q, rmx);
+              }
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+    if (!grid_barrier(A.bar, A.ctl, target)) return;
+    cur ^= 1;
+    nleaves += NL;
+    ++level;
+  }
 }
 
 // ---------------------------------------------------------------- moments
@@ -442,7 +732,7 @@ cudaError_t moments_d(dfgt_tree* t, cudaStream_t s, long long* launches) {
 // for `cap` nodes.
 struct NodeArrays {
   float *lo, *hi;
-  int *beg, *cnt, *left, *parent;
+  int *beg, *cnt, *left, *parent, *nleft, *lp0, *sloc, *leaves;
   static size_t bytes(size_t cap, int d) {
     Carver c;
     NodeArrays a;
@@ -456,28 +746,36 @@ struct NodeArrays {
     cnt = c.take<int>(cap);
     left = c.take<int>(cap);
     parent = c.take<int>(cap);
-  }
-  void copy_to(float* lo2, float* hi2, int* beg2, int* cnt2, int* left2, int* parent2, size_t keep,
-               int d, cudaStream_t s, cudaError_t* e) const {
-    const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-    if (*e == cudaSuccess) *e = cudaMemcpyAsync(lo2, lo, keep * d * sizeof(float), k, s);
-    if (*e == cudaSuccess) *e = cudaMemcpyAsync(hi2, hi, keep * d * sizeof(float), k, s);
-    if (*e == cudaSuccess) *e = cudaMemcpyAsync(beg2, beg, keep * sizeof(int), k, s);
-    if (*e == cudaSuccess) *e = cudaMemcpyAsync(cnt2, cnt, keep * sizeof(int), k, s);
-    if (*e == cudaSuccess) *e = cudaMemcpyAsync(left2, left, keep * sizeof(int), k, s);
-    if (*e == cudaSuccess) *e = cudaMemcpyAsync(parent2, parent, keep * sizeof(int), k, s);
+    nleft = c.take<int>(cap);
+    lp0 = c.take<int>(cap);
+    sloc = c.take<int>(cap);
+    leaves = c.take<int>(cap);
   }
 };
 
-// Grow the context's node buffer to `cap` nodes keeping the first `keep`.
-cudaError_t grow_nodes(DevBuf& buf, NodeArrays& na, size_t keep, size_t cap, int d, cudaStream_t s) {
+cudaError_t copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s, cudaError_t e) {
+  if (e != cudaSuccess || bytes == 0) return e;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+}
+
+// Grow the context's node buffer to `cap` nodes keeping the first `keep`
+// nodes and the first `nleaves` leaf ids.
+cudaError_t grow_nodes(DevBuf& buf, NodeArrays& na, size_t keep, size_t nleaves, size_t cap, int d,
+                       cudaStream_t s) {
   DevBuf nb;
   cudaError_t e = nb.ensure(NodeArrays::bytes(cap, d));
   if (e != cudaSuccess) return e;
   Carver c{nb.as<char>()};
   NodeArrays nn;
   nn.carve(c, cap, d);
-  na.copy_to(nn.lo, nn.hi, nn.beg, nn.cnt, nn.left, nn.parent, keep, d, s, &e);
+  e = copy_d2d(nn.lo, na.lo, keep * d * sizeof(float), s, e);
+  e = copy_d2d(nn.hi, na.hi, keep * d * sizeof(float), s, e);
+  e = copy_d2d(nn.beg, na.beg, keep * sizeof(int), s, e);
+  e = copy_d2d(nn.cnt, na.cnt, keep * sizeof(int), s, e);
+  e = copy_d2d(nn.left, na.left, keep * sizeof(int), s, e);
+  e = copy_d2d(nn.parent, na.parent, keep * sizeof(int), s, e);
+  e = copy_d2d(nn.nleft, na.nleft, keep * sizeof(int), s, e);
+  e = copy_d2d(nn.leaves, na.leaves, nleaves * sizeof(int), s, e);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     nb.release();
@@ -534,17 +832,18 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   t->lvl_off.assign(1, 0);
 
   // level-build scratch from the context: two point buffers, per-point node
-  // ids, flags, prefix sums, per-level node temporaries, the level table
+  // ids, flags, left ranks, per-block counts, control words, the level table
   float* pbuf[2];
   int* perm2[2];
   int* pnode[2];
-  int *flag, *leftpos, *split, *soff, *nleft, *status, *lv;
+  int *flag, *leftpos, *bcnt, *ctl, *lv;
+  unsigned* bar;
   NodeArrays na;
   size_t cap = 0;
-  int cur = 0, level = 0, last = -1;
-  int h_status = 0;
+  int cur = 0, last = -1;
+  int h_ctl[8] = {};
   dfgt_status rc = DFGT_ECUDA;
-  std::vector<int> lvh;
+  std::vector<int> lvh(3 * (kMaxLevels + 2));
 
   const size_t np = (size_t)n;
   Carver cv;
@@ -557,115 +856,108 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
     pnode[0] = cv.take<int>(np);
     pnode[1] = cv.take<int>(np);
     flag = cv.take<int>(np);
-    leftpos = cv.take<int>(np + 1);
-    split = cv.take<int>(np + 1);
-    soff = cv.take<int>(np + 2);
-    nleft = cv.take<int>(np + 1);
-    status = cv.take<int>(1);
+    leftpos = cv.take<int>(np);
+    bcnt = cv.take<int>(3 * kMaxGrid);
+    ctl = cv.take<int>(8);
+    bar = cv.take<unsigned>(2);
     lv = cv.take<int>(3 * (kMaxLevels + 2));
     if (pass == 0) {
       TRY(ctx->bscratch.ensure(cv.off));
       cv.base = ctx->bscratch.as<char>();
     }
   }
-  TRY(cudaMemsetAsync(status, 0, sizeof(int), s));
 
   cap = std::max<size_t>(64, 4 * np / std::max(1, t->leaf) + 16);
   {
     TRY(ctx->bnodes.ensure(NodeArrays::bytes(cap, d)));
     // use all the room the buffer has
-    const size_t fit = (ctx->bnodes.bytes - 6 * 256) / (8 * (size_t)d + 16);
+    const size_t fit = (ctx->bnodes.bytes - 10 * 256) / (8 * (size_t)d + 32);
     if (fit > cap && NodeArrays::bytes(fit, d) <= ctx->bnodes.bytes) cap = fit;
     Carver c{ctx->bnodes.as<char>()};
     na.carve(c, cap, d);
   }
+  if (ctx->build_grid == 0) {
+    // co-resident blocks of the level build: one per SM
+    int coop = 0, sms = 0, occ = 0;
+    TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+    TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_build_levels, kBT, 0));
+    if (!coop || occ < 1) {
+      ctx->err = "dfgt_build: the device does not support cooperative launches";
+      goto fail;
+    }
+    ctx->build_grid = std::min(kMaxGrid, sms);
+  }
 
-  k_pad_points<<<(n + kT - 1) / kT, kT, 0, s>>>(pts_dev, n, d, t->dp, pbuf[0], perm2[0], pnode[0], status);
-  k_init_root<<<1, 32, 0, s>>>(n, d, na.beg, na.cnt, na.left, na.parent, na.lo, na.hi, lv);
-  *L += 2;
+  TRY(cudaMemsetAsync(ctl, 0, 8 * sizeof(int), s));
+  k_init_root<<<1, 1, 0, s>>>(n, na.beg, na.cnt, na.left, na.parent, lv);
+  ++*L;
   TRY(cudaGetLastError());
-
   {
-    // Levels run in batches between host synchronisations.  A node splits
-    // only if it holds more than `leaf` points, so a level has at most
-    // 2 floor(n / (leaf + 1)) nodes below the root and at most twice the
-    // nodes of the level above: node kernels run over that bound and the
-    // node arrays hold room for every node a batch can create.  The level
-    // table records each level's range and split count; a level without
-    // splits ends the tree (levels enqueued after it are empty and leave the
-    // points in place).
-    const long long max_level_nodes = std::max<long long>(1, 2LL * (n / (t->leaf + 1)));
-    size_t known_e = 1;
-    long long known_nl = 1;
-    int batch = std::max(8, ctx->last_depth + 1);
-    const int gp = (n + kT - 1) / kT;
-    while (last < 0) {
-      if (level >= kMaxLevels) {
-        ctx->err = "dfgt_build: more than 128 tree levels";
-        rc = DFGT_ETIMEOUT;
-        goto fail;
-      }
-      const int nb = std::min(batch, kMaxLevels - level);
-      std::vector<long long> bnd(nb + 1);
-      bnd[0] = known_nl;
-      size_t need = known_e;
-      for (int k = 1; k <= nb; ++k) {
-        bnd[k] = std::min(2 * bnd[k - 1], max_level_nodes);
-        need += (size_t)bnd[k];
-      }
-      if (need > cap) {
-        const size_t nc = std::max(need, cap * 2);
-        TRY(grow_nodes(ctx->bnodes, na, known_e, nc, d, s));
-        cap = nc;
-      }
-      for (int k = 0; k < nb; ++k) {
-        const int Lk = level + k;
-        const int bk = (int)std::max<long long>(1, bnd[k]);
-        const int gn = (bk + kT - 1) / kT;
-        k_bbox<<<gp, kT, 0, s>>>(pbuf[cur], n, d, t->dp, pnode[cur], na.lo, na.hi);
-        k_flag_left<<<gp, kT, 0, s>>>(pbuf[cur], n, t->dp, d, t->leaf, pnode[cur], na.cnt, na.lo, na.hi, flag);
-        *L += 2;
-        TRY(cudaGetLastError());
-        TRY(scan_exclusive(flag, leftpos, n, ctx->scan_tmp, s, L));
-        k_node_finalize<<<gn, kT, 0, s>>>(lv, Lk, bk, d, t->leaf, na.beg, na.cnt, na.lo, na.hi, leftpos,
-                                          split, nleft);
-        ++*L;
-        TRY(cudaGetLastError());
-        TRY(scan_exclusive(split, soff, bk, ctx->scan_tmp, s, L));
-        k_make_children<<<gn, kT, 0, s>>>(lv, Lk, bk, d, (int)std::min<size_t>(cap, INT32_MAX), split, soff,
-                                          nleft, na.beg, na.cnt, na.left, na.parent, na.lo, na.hi, status);
-        k_scatter<<<gp, kT, 0, s>>>(n, t->dp, lv, Lk, pbuf[cur], perm2[cur], pnode[cur], flag, leftpos,
-                                    na.beg, na.left, nleft, pbuf[cur ^ 1], perm2[cur ^ 1], pnode[cur ^ 1]);
-        *L += 2;
-        TRY(cudaGetLastError());
-        cur ^= 1;
-      }
-      lvh.resize(3 * (level + nb + 1));
+    // One launch builds every level; it stops early only when the next
+    // level would not fit the node arrays, which are then grown (each time
+    // at least doubled) before the build goes on from that level.
+    int init_from = 0;
+    for (;;) {
+      TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
+      LevelArgs A;
+      A.in = pts_dev;
+      A.pbuf0 = pbuf[0]; A.pbuf1 = pbuf[1];
+      A.perm0 = perm2[0]; A.perm1 = perm2[1];
+      A.pnode0 = pnode[0]; A.pnode1 = pnode[1];
+      A.flag = flag; A.leftpos = leftpos; A.bcnt = bcnt;
+      A.lo = na.lo; A.hi = na.hi; A.beg = na.beg; A.cnt = na.cnt; A.left = na.left; A.parent = na.parent;
+      A.nleft = na.nleft; A.lp0 = na.lp0; A.sloc = na.sloc; A.leaves = na.leaves;
+      A.lv = lv; A.ctl = ctl; A.bar = bar;
+      A.n = n; A.d = d; A.dp = t->dp; A.leaf = t->leaf;
+      A.cap = (int)std::min<size_t>(cap, INT32_MAX);
+      A.init_from = init_from;
+      A.max_levels = kMaxLevels;
+      void* args[] = {&A};
+      TRY(cudaLaunchCooperativeKernel((const void*)k_build_levels, dim3(ctx->build_grid), dim3(kBT), args, 0, s));
+      ++*L;
+      TRY(cudaMemcpyAsync(h_ctl, ctl, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaMemcpyAsync(lvh.data(), lv, lvh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
-      TRY(cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaStreamSynchronize(s));
-      if (h_status & kStNonFinite) {
+      if (h_ctl[0] & kStNonFinite) {
         ctx->err = "dfgt_build: non-finite coordinate";
         rc = DFGT_EINVAL;
         goto fail;
       }
-      if (h_status & kStOverflow) {
-        ctx->err = "dfgt_build: node capacity bound violated (internal error)";
+      if (h_ctl[0] & kStOverflow) {
+        ctx->err = "dfgt_build: point rank out of range (internal error)";
         rc = DFGT_ECAPACITY;
         goto fail;
       }
-      for (int k = 0; k < nb && last < 0; ++k)
-        if (lvh[3 * (level + k) + 2] == 0) last = level + k;
-      level += nb;
-      if (last < 0) {
-        known_e = (size_t)lvh[3 * level + 1];
-        known_nl = (long long)lvh[3 * level + 1] - lvh[3 * level];
-        batch = 8;
+      if (h_ctl[0] & kStTimeout) {
+        ctx->err = "dfgt_build: a grid barrier wait timed out";
+        rc = DFGT_ETIMEOUT;
+        goto fail;
       }
+      if (h_ctl[4]) break;
+      const int level = h_ctl[2];
+      if (level + 1 >= kMaxLevels) {
+        ctx->err = "dfgt_build: more than 128 tree levels";
+        rc = DFGT_ETIMEOUT;
+        goto fail;
+      }
+      const size_t keep = (size_t)lvh[3 * level + 1];
+      const size_t need = (size_t)h_ctl[5];
+      if (need <= cap) {
+        ctx->err = "dfgt_build: level build stopped without cause (internal error)";
+        rc = DFGT_ECAPACITY;
+        goto fail;
+      }
+      const size_t nc = std::max(need + need / 2, cap * 2);
+      TRY(grow_nodes(ctx->bnodes, na, keep, (size_t)h_ctl[3], nc, d, s));
+      cap = nc;
+      init_from = (int)keep;
     }
+    cur = h_ctl[1];
+    last = h_ctl[2];
+    t->nleaves = h_ctl[3];
     t->lvl_off.assign(1, 0);
     for (int Lk = 0; Lk <= last; ++Lk) t->lvl_off.push_back(lvh[3 * Lk + 1]);
-    ctx->last_depth = last + 1;
   }
   t->nn = t->lvl_off.back();
   t->depth = (int)t->lvl_off.size() - 1;
@@ -700,9 +992,16 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
         ca.base = static_cast<char*>(t->arena);
       }
     }
-    cudaError_t ce = cudaMemcpyAsync(t->pts, pbuf[cur], np * t->dp * sizeof(float), cudaMemcpyDeviceToDevice, s);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(t->perm, perm2[cur], np * sizeof(int), cudaMemcpyDeviceToDevice, s);
-    na.copy_to(t->lo, t->hi, t->beg, t->cnt, t->left, t->parent, nn, d, s, &ce);
+    cudaError_t ce = cudaSuccess;
+    ce = copy_d2d(t->pts, pbuf[cur], np * t->dp * sizeof(float), s, ce);
+    ce = copy_d2d(t->perm, perm2[cur], np * sizeof(int), s, ce);
+    ce = copy_d2d(t->lo, na.lo, nn * d * sizeof(float), s, ce);
+    ce = copy_d2d(t->hi, na.hi, nn * d * sizeof(float), s, ce);
+    ce = copy_d2d(t->beg, na.beg, nn * sizeof(int), s, ce);
+    ce = copy_d2d(t->cnt, na.cnt, nn * sizeof(int), s, ce);
+    ce = copy_d2d(t->left, na.left, nn * sizeof(int), s, ce);
+    ce = copy_d2d(t->parent, na.parent, nn * sizeof(int), s, ce);
+    ce = copy_d2d(t->leaves, na.leaves, (size_t)t->nleaves * sizeof(int), s, ce);
     TRY(ce);
   }
   switch (d) {
@@ -719,18 +1018,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   k_node_float_data<<<(t->nn + kT - 1) / kT, kT, 0, s>>>(t->view(), t->pm, t->chi, t->clo, t->whalf, t->mnorm);
   ++*L;
   TRY(cudaGetLastError());
-  {
-    // the leaf list, in node order, from the level structure
-    std::vector<int> left_h(t->nn);
-    TRY(cudaMemcpyAsync(left_h.data(), t->left, t->nn * sizeof(int), cudaMemcpyDeviceToHost, s));
-    TRY(cudaStreamSynchronize(s));
-    std::vector<int> leaves_h;
-    for (int j = 0; j < t->nn; ++j)
-      if (left_h[j] < 0) leaves_h.push_back(j);
-    t->nleaves = (int)leaves_h.size();
-    TRY(cudaMemcpyAsync(t->leaves, leaves_h.data(), leaves_h.size() * sizeof(int), cudaMemcpyHostToDevice, s));
-    TRY(cudaStreamSynchronize(s));
-  }
+  TRY(cudaStreamSynchronize(s));  // calls return after their work
   rc = DFGT_OK;
 fail:
   if (rc != DFGT_OK) {

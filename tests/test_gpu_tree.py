@@ -40,7 +40,7 @@ def check_tree(x, t, leaf):
 
 
 @pytest.mark.parametrize("D,n,leaf", [(1, 1000, 8), (2, 5000, 32), (3, 20011, 32), (5, 3000, 16),
-                                      (8, 2000, 32), (16, 1500, 64)])
+                                      (8, 2000, 32), (16, 1500, 64), (2, 400003, 128)])
 def test_tree_invariants(dev, D, n, leaf):
     x = datagen.isotropic_mixture(n, D, 6, 0.05, seed=D + n)
     tree = dfgt.Tree(dev, to_cuda(x), leaf_size=leaf)
