@@ -94,9 +94,10 @@ struct dfgt_ctx {
   DevBuf bf_partials;       // brute-force slice partials
   DevBuf cv_buf;            // cross-validation normalisers, partials and scores
   DevBuf bscratch;          // tree-build per-point scratch
-  DevBuf bnodes;            // tree-build node arrays (copied into the tree's arena)
+  DevBuf bnodes;            // tree-build per-node scratch (left counts, prefixes, split ranks)
   std::shared_ptr<TreePool> tpool;
   int build_grid = 0;         // blocks of the cooperative level build (0: not yet chosen)
+  int mom_grid[6] = {};       // blocks of the cooperative moment pass per dimension (0: D >= 6)
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned

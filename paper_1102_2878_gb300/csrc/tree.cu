@@ -24,7 +24,6 @@
 namespace dfgt {
 namespace {
 
-constexpr int kT = 256;
 constexpr int kMaxLevels = 128;
 // Defaults measured on a GB300 (D = 3, 2e5 clustered points, 10 bandwidths
 // in [1e-3, 1], eps = 1e-2): leaf sizes 16..256 and exact-sum thresholds
@@ -171,6 +170,7 @@ struct LevelArgs {
   float *lo, *hi;                   // node boxes [cap][d]
   int *beg, *cnt, *left, *parent;   // node records [cap]
   int* nleft;                       // [cap] points going left
+  int* arrive;                      // [cap] moment-pass child counters (zeroed here)
   int* lp0;                         // [cap] left prefix at the node's first point
   int* sloc;                        // [cap] split: rank among the block's splits; leaf: -1 - rank
   int* leaves;                      // [cap] leaf ids in node order
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
   // boxes and left counts of the nodes this launch may create
   for (size_t j = (size_t)A.init_from + (size_t)b * kBT + tid; j < (size_t)A.cap; j += (size_t)G * kBT) {
     A.nleft[j] = 0;
+    A.arrive[j] = 0;
     for (int k = 0; k < d; ++k) {
       A.lo[j * d + k] = INFINITY;
       A.hi[j * d + k] = -INFINITY;
@@ -470,11 +471,14 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
         }
         for (int q0 = 0; q0 < d; q0 += 4) {
           // up to four coordinates per round through shared memory
+          float vq[4];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) vq[qq] = (valid && q0 + qq < d) ? __ldcg(pin + (size_t)i * dp + q0 + qq) : 0.f;
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq) {
             const int q = q0 + qq;
             if (q >= d) break;
-            const float v = valid ? __ldcg(pin + (size_t)i * dp + q) : 0.f;
+            const float v = vq[qq];
             if (uni) {
               float lmn = (valid && f[k]) ? v : INFINITY, lmx = (valid && f[k]) ? v : -INFINITY;
               float rmn = (valid && !f[k]) ? v : INFINITY, rmx = (valid && !f[k]) ? v : -INFINITY;
@@ -550,241 +554,344 @@ __constant__ double c_inv_fact[16] = {
     1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
     1.0 / 87178291200.0, 1.0 / 1307674368000.0};
 
-// Leaf moments (AccumulateFarFieldMoment): for each batch of 32 points the
-// lanes tabulate the powers (r_k - c_k)^e, e < p_max, of one point each in
-// shared memory; then each lane owns coefficient positions and accumulates
-// prod_k table[j][k][alpha_k] over the batch.  Float64 throughout.
-template <int D>
-__global__ void __launch_bounds__(kT) k_leaf_moments(TreeView t, double* __restrict__ mom) {
-  constexpr int PM = pmax_of(D);
-  constexpr int P = ipow_c(PM, D);
-  constexpr int S = (P + 31) / 32;
-  constexpr int W = kT / 32;
-  __shared__ double sPow[W][32][D][PM];
-  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int w = blockIdx.x * W + wib;
-  if (w >= t.nn || t.left[w] >= 0) return;
+constexpr int kMT = 256;  // threads per block of the moment pass
+constexpr int kMW = kMT / 32;
+
+struct MomArgs {
+  const float *pbuf0, *pbuf1;  // the level build's point buffers (ctl[1] holds the final one)
+  const int *perm0, *perm1;
+  float* pts;                  // the tree's points and permutation
+  int* perm;
+  const float *lo, *hi;
+  const int *beg, *cnt, *left, *parent, *leaves;
+  double* mom;                 // [nodes][P] raw moments
+  float *chi, *clo, *whalf, *mnorm;
+  int* arrive;                 // [nodes] children finished (zero at launch)
+  const int* ctl;
+  int n, d, dp, pm, P;
+};
+
+// Shared memory of one warp: a batch of 32 points' coordinate powers
+// (leaf moments) or the moment buffers of a dimension-wise shift (F2F).
+template <int D, int PM, int P>
+union MomSmem {
+  double pw[32][D][PM];
+  double m[3][P];
+};
+
+// Leaf moments (AccumulateFarFieldMoment) of leaf w, one warp, float64:
+// the points' powers (r_k - c_k)^e, e < p_max, are tabulated 32 points at
+// a time; lane (g, pre) owns the digits alpha_0..alpha_{D-2} = pre and all
+// p_max values of the last digit, and sums over every R-th point of the
+// batch (R = 32 / p_max^{D-1} lane groups), so a term costs one multiply
+// per leading digit and one FMA per last digit.
+template <int D, int PM, int P>
+__device__ void leaf_moments(const MomArgs& M, const float* pin, int w, MomSmem<D, PM, P>& sm) {
+  constexpr int NPRE = P / PM;
+  constexpr int R = 32 / NPRE;
+  const int lane = threadIdx.x & 31, g = lane / NPRE, pre = lane % NPRE;
   double c[D];
 #pragma unroll
-  for (int k = 0; k < D; ++k) c[k] = 0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
-  int al[S][D];
+  for (int k = 0; k < D; ++k) c[k] = 0.5 * ((double)M.lo[(size_t)w * D + k] + (double)M.hi[(size_t)w * D + k]);
+  int al[D > 1 ? D - 1 : 1];
 #pragma unroll
-  for (int sl = 0; sl < S; ++sl) {
-    int v = lane + 32 * sl;
+  for (int k = D - 2, v = pre; k >= 0; --k) { al[k] = v % PM; v /= PM; }
+  double acc[PM];
 #pragma unroll
-    for (int k = D - 1; k >= 0; --k) { al[sl][k] = v % PM; v /= PM; }
-  }
-  double acc[S];
-#pragma unroll
-  for (int sl = 0; sl < S; ++sl) acc[sl] = 0.0;
-  const int b = t.beg[w], n = t.cnt[w];
+  for (int e = 0; e < PM; ++e) acc[e] = 0.0;
+  const int b = M.beg[w], n = M.cnt[w];
   for (int j0 = 0; j0 < n; j0 += 32) {
     const int j = j0 + lane;
+    float xr[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) xr[k] = j < n ? pin[(size_t)(b + j) * M.dp + k] : 0.f;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const double x = j < n ? (double)t.pts[(size_t)(b + j) * t.dp + k] - c[k] : 0.0;
-      double v = j < n ? 1.0 : 0.0;  // padding points contribute nothing
+      const double x = j < n ? (double)xr[k] - c[k] : 0.0;
+      double v = 1.0;
 #pragma unroll
-      for (int e = 0; e < PM; ++e) { sPow[wib][lane][k][e] = v; v *= x; }
+      for (int e = 0; e < PM; ++e) { sm.pw[lane][k][e] = v; v *= x; }
     }
     __syncwarp();
     const int jn = min(32, n - j0);
+    if (g < R) {
+      for (int jj = g; jj < jn; jj += R) {
+        double t = 1.0;
 #pragma unroll
-    for (int sl = 0; sl < S; ++sl) {
-      if (lane + 32 * sl >= P) break;
-      double a = 0.0;
-      for (int jj = 0; jj < jn; ++jj) {
-        double term = sPow[wib][jj][0][al[sl][0]];
+        for (int k = 0; k < D - 1; ++k) t *= sm.pw[jj][k][al[k]];
 #pragma unroll
-        for (int k = 1; k < D; ++k) term *= sPow[wib][jj][k][al[sl][k]];
-        a += term;
+        for (int e = 0; e < PM; ++e) acc[e] = fma(t, sm.pw[jj][D - 1][e], acc[e]);
       }
-      acc[sl] += a;
     }
     __syncwarp();
   }
+  // lanes of group 0 collect the other groups' sums (fixed order)
 #pragma unroll
-  for (int sl = 0; sl < S; ++sl) {
-    const int idx = lane + 32 * sl;
-    if (idx >= P) break;
+  for (int e = 0; e < PM; ++e) {
+    double s = acc[e];
+    for (int g2 = 1; g2 < R; ++g2) s += __shfl_sync(0xffffffffu, acc[e], (lane + g2 * NPRE) & 31);
+    acc[e] = s;
+  }
+  if (g == 0) {
     double f = 1.0;
 #pragma unroll
-    for (int k = 0; k < D; ++k) f *= c_inv_fact[al[sl][k]];
-    mom[(size_t)w * P + idx] = acc[sl] * f;
+    for (int k = 0; k < D - 1; ++k) f *= c_inv_fact[al[k]];
+#pragma unroll
+    for (int e = 0; e < PM; ++e) M.mom[(size_t)w * P + pre * PM + e] = acc[e] * f * c_inv_fact[e];
   }
 }
 
-// Internal moments of one level by the far-to-far translation (Lemma 3.5,
+// Moments of internal node w by the far-to-far translation (Lemma 3.5,
 // Eq. far_to_far_translation, exact for gamma < p) of both children:
 // m_gamma(c') = sum_{alpha<=gamma} m_alpha(c_child) (c_child - c')^{gamma-alpha}/(gamma-alpha)!.
 // The factor (x)^{gamma-alpha}/(gamma-alpha)! is a product over dimensions,
 // so the shift is applied one dimension at a time (D p^D p operations per
 // child instead of p^{2D}), in float64 shared memory, one warp per node.
-template <int D>
-__global__ void k_f2f_level(TreeView t, int a, int e, double* __restrict__ mom) {
-  constexpr int PM = pmax_of(D);
-  constexpr int P = ipow_c(PM, D);
-  constexpr int W = kT / 32;
-  __shared__ double sM[W][2][P];
-  const int wib = threadIdx.x >> 5;
-  const int w = a + blockIdx.x * W + wib;
+// Every global load is issued before the arithmetic.
+template <int D, int PM, int P>
+__device__ void f2f_node(const MomArgs& M, int w, MomSmem<D, PM, P>& sm) {
+  constexpr int S = (P + 31) / 32;
   const int lane = threadIdx.x & 31;
-  if (w >= e || t.left[w] < 0) return;
-  double acc[(P + 31) / 32];
+  const int c0 = M.left[w];
+  float lo3[3][D], hi3[3][D];
+  double mv[2][S];
 #pragma unroll
-  for (int sl = 0; sl < (P + 31) / 32; ++sl) acc[sl] = 0.0;
+  for (int k = 0; k < D; ++k) {
+    lo3[0][k] = M.lo[(size_t)w * D + k];
+    hi3[0][k] = M.hi[(size_t)w * D + k];
+    lo3[1][k] = M.lo[(size_t)c0 * D + k];
+    hi3[1][k] = M.hi[(size_t)c0 * D + k];
+    lo3[2][k] = M.lo[(size_t)(c0 + 1) * D + k];
+    hi3[2][k] = M.hi[(size_t)(c0 + 1) * D + k];
+  }
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+      const int idx = lane + 32 * sl;
+      mv[ch][sl] = idx < P ? __ldcg(M.mom + (size_t)(c0 + ch) * P + idx) : 0.0;
+    }
+  double acc[S];
+#pragma unroll
+  for (int sl = 0; sl < S; ++sl) acc[sl] = 0.0;
+#pragma unroll
   for (int ch = 0; ch < 2; ++ch) {
-    const int cn = t.left[w] + ch;
-    for (int idx = lane; idx < P; idx += 32) sM[wib][0][idx] = mom[(size_t)cn * P + idx];
+#pragma unroll
+    for (int sl = 0; sl < S; ++sl) {
+      const int idx = lane + 32 * sl;
+      if (idx < P) sm.m[0][idx] = mv[ch][sl];
+    }
     __syncwarp();
     int cur = 0;
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const double x = 0.5 * ((double)t.lo[(size_t)cn * D + k] + (double)t.hi[(size_t)cn * D + k]) -
-                       0.5 * ((double)t.lo[(size_t)w * D + k] + (double)t.hi[(size_t)w * D + k]);
+      const double x = 0.5 * ((double)lo3[1 + ch][k] + (double)hi3[1 + ch][k]) -
+                       0.5 * ((double)lo3[0][k] + (double)hi3[0][k]);
       int stride = 1;
+#pragma unroll
       for (int j = D - 1; j > k; --j) stride *= PM;
       double T[PM];  // x^e / e!
       T[0] = 1.0;
 #pragma unroll
       for (int e2 = 1; e2 < PM; ++e2) T[e2] = T[e2 - 1] * x * (1.0 / (double)e2);
-      for (int idx = lane; idx < P; idx += 32) {
-        const int gk = (idx / stride) % PM;
-        // sum over alpha_k <= gamma_k of m[.. alpha_k ..] x^{gamma_k - alpha_k} / (gamma_k - alpha_k)!
-        double sum = 0.0;
 #pragma unroll
-        for (int dlt = 0; dlt < PM; ++dlt)
-          if (dlt <= gk) sum += sM[wib][cur][idx - dlt * stride] * T[dlt];
-        sM[wib][cur ^ 1][idx] = sum;
+      for (int sl = 0; sl < S; ++sl) {
+        const int idx = lane + 32 * sl;
+        if (idx < P) {
+          const int gk = (idx / stride) % PM;
+          double sum = 0.0;
+#pragma unroll
+          for (int dlt = 0; dlt < PM; ++dlt)
+            if (dlt <= gk) sum += sm.m[cur][idx - dlt * stride] * T[dlt];
+          sm.m[cur ^ 1][idx] = sum;
+        }
       }
       __syncwarp();
       cur ^= 1;
     }
 #pragma unroll
-    for (int sl = 0; sl < (P + 31) / 32; ++sl) {
+    for (int sl = 0; sl < S; ++sl) {
       const int idx = lane + 32 * sl;
-      if (idx < P) acc[sl] += sM[wib][cur][idx];
+      if (idx < P) acc[sl] += sm.m[cur][idx];
     }
     __syncwarp();
   }
 #pragma unroll
-  for (int sl = 0; sl < (P + 31) / 32; ++sl) {
+  for (int sl = 0; sl < S; ++sl) {
     const int idx = lane + 32 * sl;
-    if (idx < P) mom[(size_t)w * P + idx] = acc[sl];
+    if (idx < P) M.mom[(size_t)w * P + idx] = acc[sl];
   }
 }
 
-// Per-node float data for the float32 kernels: the box center as a float
-// pair (hi + lo, so that differences with points stay accurate), the
-// largest half side w and the moments normalised by w, m_alpha / w^|alpha|,
-// which are bounded by |R| (each |r_k - c_k| <= w), so the scaled moments
-// M_alpha = m~_alpha (w s)^|alpha| are formed in float32 without range
-// problems.  Computed in float64 once per tree.
-__global__ void k_node_float_data(TreeView t, int pm, float* __restrict__ chi, float* __restrict__ clo,
-                                  float* __restrict__ whalf, float* __restrict__ mnorm) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= t.nn) return;
-  const int d = t.d;
-  double w = 0.0;
-  for (int k = 0; k < d; ++k) {
-    const double lo = t.lo[(size_t)j * d + k], hi = t.hi[(size_t)j * d + k];
+// Per-node float data for the float32 kernels, one warp: the box center as
+// a float pair (hi + lo, so that differences with points stay accurate),
+// the largest half side w and the moments normalised by w,
+// m_alpha / w^|alpha|, which are bounded by |R| (each |r_k - c_k| <= w), so
+// the scaled moments M_alpha = m~_alpha (w s)^|alpha| are formed in float32
+// without range problems.  Computed in float64 once per tree; the node's
+// moments were written by this warp or are visible to it.
+__device__ void node_float_data(const MomArgs& M, int j) {
+  const int d = M.d, lane = threadIdx.x & 31;
+  double hw = 0.0;
+  for (int k = lane; k < d; k += 32) {
+    const double lo = M.lo[(size_t)j * d + k], hi = M.hi[(size_t)j * d + k];
     const double c = 0.5 * (lo + hi);
     const float h = (float)c;
-    chi[(size_t)j * d + k] = h;
-    clo[(size_t)j * d + k] = (float)(c - (double)h);
-    w = fmax(w, 0.5 * (hi - lo));
+    M.chi[(size_t)j * d + k] = h;
+    M.clo[(size_t)j * d + k] = (float)(c - (double)h);
+    hw = fmax(hw, 0.5 * (hi - lo));
   }
-  float wf = (float)w;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) hw = fmax(hw, __shfl_xor_sync(0xffffffffu, hw, o));
+  float wf = (float)hw;
   if (!(wf > 0.f)) wf = 1.f;
-  whalf[j] = wf;
+  if (lane == 0) M.whalf[j] = wf;
   const double iw = 1.0 / (double)wf;
-  for (int idx = 0; idx < t.P; ++idx) {
+  for (int idx = lane; idx < M.P; idx += 32) {
+    const double m = __ldcg(M.mom + (size_t)j * M.P + idx);
     int v = idx, ab = 0;
-    for (int k = 0; k < d; ++k) { ab += v % pm; v /= pm; }
+    for (int k = 0; k < d; ++k) { ab += v % M.pm; v /= M.pm; }
     double sc = 1.0;
     for (int e = 0; e < ab; ++e) sc *= iw;
-    mnorm[(size_t)j * t.P + idx] = (float)(t.mom[(size_t)j * t.P + idx] * sc);
+    M.mnorm[(size_t)j * M.P + idx] = (float)(m * sc);
   }
 }
 
-// D >= 6: p_max = 1, the only moment is m_0 = |R|.
-__global__ void k_count_moments(TreeView t, double* __restrict__ mom) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < t.nn) mom[j] = (double)t.cnt[j];
-}
-
+// Every moment of the tree, after the level build has finished (it returns
+// at once otherwise): the final points are copied into the tree, each warp
+// sums the moments of its leaves, and the warp that finishes the second
+// child of a node translates both children's moments to it (Lemma 3.5) and
+// goes on up, so no warp waits for another.  Each node's float data follows
+// its moments.  D = 0 stands for D >= 6, where p_max = 1 and the only
+// moment is m_0 = |R|.
 template <int D>
-cudaError_t moments_d(dfgt_tree* t, cudaStream_t s, long long* launches) {
-  TreeView v = t->view();
-  const int blocks = (int)(((size_t)t->nn * 32 + kT - 1) / kT);
-  k_leaf_moments<D><<<blocks, kT, 0, s>>>(v, t->mom);
-  ++*launches;
-  for (int lev = t->depth - 2; lev >= 0; --lev) {
-    const int a = t->lvl_off[lev], e = t->lvl_off[lev + 1];
-    const int nb = (int)(((size_t)(e - a) * 32 + kT - 1) / kT);
-    k_f2f_level<D><<<nb, kT, 0, s>>>(v, a, e, t->mom);
-    ++*launches;
+__global__ void __launch_bounds__(kMT) k_moments(MomArgs M) {
+  constexpr int PM = D > 0 ? pmax_of(D) : 1;
+  constexpr int P = D > 0 ? ipow_c(PM, D) : 1;
+  constexpr int DD = D > 0 ? D : 1;
+  __shared__ MomSmem<DD, PM, P> sm[kMW];
+  if (__ldcg(M.ctl + 4) == 0) return;
+  const int G = gridDim.x, wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kMW + wib, nw = G * kMW;
+  const int cur = __ldcg(M.ctl + 1), nleaves = __ldcg(M.ctl + 3);
+  const float* pin = cur ? M.pbuf1 : M.pbuf0;
+  const int* permin = cur ? M.perm1 : M.perm0;
+  for (size_t i = (size_t)blockIdx.x * kMT + threadIdx.x; i < (size_t)M.n * M.dp; i += (size_t)G * kMT)
+    M.pts[i] = pin[i];
+  for (int i = blockIdx.x * kMT + threadIdx.x; i < M.n; i += G * kMT) M.perm[i] = permin[i];
+  for (int li = gw; li < nleaves; li += nw) {
+    int w = M.leaves[li];
+    if constexpr (D > 0) {
+      leaf_moments<D, PM, P>(M, pin, w, sm[wib]);
+    } else {
+      if (lane == 0) M.mom[w] = (double)M.cnt[w];
+    }
+    __syncwarp();
+    node_float_data(M, w);
+    for (;;) {
+      const int par = M.parent[w];
+      if (par < 0) break;
+      // publish this node's moments, then count it as a finished child
+      __threadfence();
+      int prev = 0;
+      if (lane == 0) prev = atomicAdd(M.arrive + par, 1);
+      prev = __shfl_sync(0xffffffffu, prev, 0);
+      if (prev == 0) break;  // the sibling's warp will do the parent
+      __threadfence();
+      if constexpr (D > 0) {
+        f2f_node<D, PM, P>(M, par, sm[wib]);
+      } else {
+        if (lane == 0) M.mom[par] = (double)M.cnt[par];
+      }
+      __syncwarp();
+      node_float_data(M, par);
+      w = par;
+    }
   }
-  return cudaGetLastError();
 }
-
-// Node arrays of a build in progress, carved from one buffer with room
-// for `cap` nodes.
-struct NodeArrays {
-  float *lo, *hi;
-  int *beg, *cnt, *left, *parent, *nleft, *lp0, *sloc, *leaves;
-  static size_t bytes(size_t cap, int d) {
-    Carver c;
-    NodeArrays a;
-    a.carve(c, cap, d);
-    return c.off;
-  }
-  void carve(Carver& c, size_t cap, int d) {
-    lo = c.take<float>(cap * d);
-    hi = c.take<float>(cap * d);
-    beg = c.take<int>(cap);
-    cnt = c.take<int>(cap);
-    left = c.take<int>(cap);
-    parent = c.take<int>(cap);
-    nleft = c.take<int>(cap);
-    lp0 = c.take<int>(cap);
-    sloc = c.take<int>(cap);
-    leaves = c.take<int>(cap);
-  }
-};
 
 cudaError_t copy_d2d(void* dst, const void* src, size_t bytes, cudaStream_t s, cudaError_t e) {
   if (e != cudaSuccess || bytes == 0) return e;
   return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
 }
 
-// Grow the context's node buffer to `cap` nodes keeping the first `keep`
-// nodes and the first `nleaves` leaf ids.
-cudaError_t grow_nodes(DevBuf& buf, NodeArrays& na, size_t keep, size_t nleaves, size_t cap, int d,
-                       cudaStream_t s) {
-  DevBuf nb;
-  cudaError_t e = nb.ensure(NodeArrays::bytes(cap, d));
+// The tree's arena: one pool allocation holding every array of the tree,
+// with room for `cap` nodes.  The level build writes the node records into
+// it directly.
+void carve_tree(Carver& ca, dfgt_tree* t, size_t np, size_t cap) {
+  const int d = t->d;
+  const size_t P = (size_t)t->P;
+  t->pts = ca.take<float>(np * t->dp);
+  t->perm = ca.take<int>(np);
+  t->leaves = ca.take<int>(cap);
+  t->lo = ca.take<float>(cap * d);
+  t->hi = ca.take<float>(cap * d);
+  t->beg = ca.take<int>(cap);
+  t->cnt = ca.take<int>(cap);
+  t->left = ca.take<int>(cap);
+  t->parent = ca.take<int>(cap);
+  t->mom = ca.take<double>(cap * P);
+  t->chi = ca.take<float>(cap * d);
+  t->clo = ca.take<float>(cap * d);
+  t->whalf = ca.take<float>(cap);
+  t->mnorm = ca.take<float>(cap * P);
+}
+
+cudaError_t alloc_tree(dfgt_ctx* ctx, dfgt_tree* t, size_t np, size_t cap) {
+  Carver ca;
+  dfgt_tree shape;  // sizes only; t keeps its arrays if the allocation fails
+  shape.d = t->d;
+  shape.dp = t->dp;
+  shape.P = t->P;
+  carve_tree(ca, &shape, np, cap);
+  void* arena = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&arena, ca.off, ctx->tpool->pool, ctx->stream);
   if (e != cudaSuccess) return e;
-  Carver c{nb.as<char>()};
-  NodeArrays nn;
-  nn.carve(c, cap, d);
-  e = copy_d2d(nn.lo, na.lo, keep * d * sizeof(float), s, e);
-  e = copy_d2d(nn.hi, na.hi, keep * d * sizeof(float), s, e);
-  e = copy_d2d(nn.beg, na.beg, keep * sizeof(int), s, e);
-  e = copy_d2d(nn.cnt, na.cnt, keep * sizeof(int), s, e);
-  e = copy_d2d(nn.left, na.left, keep * sizeof(int), s, e);
-  e = copy_d2d(nn.parent, na.parent, keep * sizeof(int), s, e);
-  e = copy_d2d(nn.nleft, na.nleft, keep * sizeof(int), s, e);
-  e = copy_d2d(nn.leaves, na.leaves, nleaves * sizeof(int), s, e);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) {
-    nb.release();
-    return e;
-  }
-  buf.release();
-  buf = nb;
-  na = nn;
+  t->tpool = ctx->tpool;
+  t->arena = arena;
+  Carver cb{static_cast<char*>(arena)};
+  carve_tree(cb, t, np, cap);
   return cudaSuccess;
+}
+
+// Per-node scratch of the level build in the context (left counts, moment
+// pass counters, left prefixes, split ranks), `cap` nodes each.
+struct NodeScratch {
+  int *nleft, *arrive, *lp0, *sloc;
+  static size_t bytes(size_t cap) { return 4 * ((cap * sizeof(int) + 255) & ~(size_t)255) + 256; }
+  void carve(char* base, size_t cap) {
+    Carver c{base};
+    nleft = c.take<int>(cap);
+    arrive = c.take<int>(cap);
+    lp0 = c.take<int>(cap);
+    sloc = c.take<int>(cap);
+  }
+};
+
+// Blocks of a cooperative launch of `fn`: `per_sm` per SM at most.
+template <class F>
+cudaError_t coop_grid(F fn, int threads, int per_sm, int device, int* grid) {
+  int coop = 0, sms = 0, occ = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0);
+  if (e != cudaSuccess) return e;
+  if (!coop || occ < 1) return cudaErrorNotSupported;
+  *grid = std::min(kMaxGrid, sms * std::min(occ, per_sm));
+  return cudaSuccess;
+}
+
+template <int D>
+cudaError_t launch_moments(dfgt_ctx* ctx, const MomArgs& M, cudaStream_t s) {
+  int& g = ctx->mom_grid[D];
+  if (g == 0) {
+    int sms = 0;
+    const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e != cudaSuccess) return e;
+    g = 4 * sms;
+  }
+  k_moments<D><<<g, kMT, 0, s>>>(M);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -838,9 +945,8 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   int* pnode[2];
   int *flag, *leftpos, *bcnt, *ctl, *lv;
   unsigned* bar;
-  NodeArrays na;
+  NodeScratch ns;
   size_t cap = 0;
-  int cur = 0, last = -1;
   int h_ctl[8] = {};
   dfgt_status rc = DFGT_ECUDA;
   std::vector<int> lvh(3 * (kMaxLevels + 2));
@@ -866,37 +972,31 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       cv.base = ctx->bscratch.as<char>();
     }
   }
-
-  cap = std::max<size_t>(64, 4 * np / std::max(1, t->leaf) + 16);
-  {
-    TRY(ctx->bnodes.ensure(NodeArrays::bytes(cap, d)));
-    // use all the room the buffer has
-    const size_t fit = (ctx->bnodes.bytes - 10 * 256) / (8 * (size_t)d + 32);
-    if (fit > cap && NodeArrays::bytes(fit, d) <= ctx->bnodes.bytes) cap = fit;
-    Carver c{ctx->bnodes.as<char>()};
-    na.carve(c, cap, d);
-  }
   if (ctx->build_grid == 0) {
-    // co-resident blocks of the level build: one per SM
-    int coop = 0, sms = 0, occ = 0;
-    TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
-    TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_build_levels, kBT, 0));
-    if (!coop || occ < 1) {
+    const cudaError_t e = coop_grid(k_build_levels, kBT, 1, ctx->device, &ctx->build_grid);
+    if (e == cudaErrorNotSupported) {
       ctx->err = "dfgt_build: the device does not support cooperative launches";
       goto fail;
     }
-    ctx->build_grid = std::min(kMaxGrid, sms);
+    TRY(e);
   }
 
+  // node capacity: a level has at most 2 floor(n / (leaf + 1)) nodes below
+  // the root; twice that covers typical trees, and the build grows it
+  cap = std::max<size_t>(64, 4 * np / std::max(1, t->leaf) + 16);
+  TRY(alloc_tree(ctx, t, np, cap));
+  TRY(ctx->bnodes.ensure(NodeScratch::bytes(cap)));
+  ns.carve(ctx->bnodes.as<char>(), cap);
+
   TRY(cudaMemsetAsync(ctl, 0, 8 * sizeof(int), s));
-  k_init_root<<<1, 1, 0, s>>>(n, na.beg, na.cnt, na.left, na.parent, lv);
+  k_init_root<<<1, 1, 0, s>>>(n, t->beg, t->cnt, t->left, t->parent, lv);
   ++*L;
   TRY(cudaGetLastError());
   {
-    // One launch builds every level; it stops early only when the next
-    // level would not fit the node arrays, which are then grown (each time
-    // at least doubled) before the build goes on from that level.
+    // One launch builds every level and one more forms every moment; the
+    // level build stops early only when the next level would not fit the
+    // node arrays, which are then grown (at least doubled) before the build
+    // goes on from that level (the moment pass waits for a finished tree).
     int init_from = 0;
     for (;;) {
       TRY(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s));
@@ -906,8 +1006,8 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       A.perm0 = perm2[0]; A.perm1 = perm2[1];
       A.pnode0 = pnode[0]; A.pnode1 = pnode[1];
       A.flag = flag; A.leftpos = leftpos; A.bcnt = bcnt;
-      A.lo = na.lo; A.hi = na.hi; A.beg = na.beg; A.cnt = na.cnt; A.left = na.left; A.parent = na.parent;
-      A.nleft = na.nleft; A.lp0 = na.lp0; A.sloc = na.sloc; A.leaves = na.leaves;
+      A.lo = t->lo; A.hi = t->hi; A.beg = t->beg; A.cnt = t->cnt; A.left = t->left; A.parent = t->parent;
+      A.nleft = ns.nleft; A.arrive = ns.arrive; A.lp0 = ns.lp0; A.sloc = ns.sloc; A.leaves = t->leaves;
       A.lv = lv; A.ctl = ctl; A.bar = bar;
       A.n = n; A.d = d; A.dp = t->dp; A.leaf = t->leaf;
       A.cap = (int)std::min<size_t>(cap, INT32_MAX);
@@ -915,6 +1015,22 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       A.max_levels = kMaxLevels;
       void* args[] = {&A};
       TRY(cudaLaunchCooperativeKernel((const void*)k_build_levels, dim3(ctx->build_grid), dim3(kBT), args, 0, s));
+      ++*L;
+      MomArgs M;
+      M.pbuf0 = pbuf[0]; M.pbuf1 = pbuf[1]; M.perm0 = perm2[0]; M.perm1 = perm2[1];
+      M.pts = t->pts; M.perm = t->perm;
+      M.lo = t->lo; M.hi = t->hi; M.beg = t->beg; M.cnt = t->cnt; M.left = t->left; M.leaves = t->leaves;
+      M.mom = t->mom; M.chi = t->chi; M.clo = t->clo; M.whalf = t->whalf; M.mnorm = t->mnorm;
+      M.parent = t->parent; M.arrive = ns.arrive; M.ctl = ctl;
+      M.n = n; M.d = d; M.dp = t->dp; M.pm = t->pm; M.P = t->P;
+      switch (d) {
+        case 1: TRY(launch_moments<1>(ctx, M, s)); break;
+        case 2: TRY(launch_moments<2>(ctx, M, s)); break;
+        case 3: TRY(launch_moments<3>(ctx, M, s)); break;
+        case 4: TRY(launch_moments<4>(ctx, M, s)); break;
+        case 5: TRY(launch_moments<5>(ctx, M, s)); break;
+        default: TRY(launch_moments<0>(ctx, M, s)); break;
+      }
       ++*L;
       TRY(cudaMemcpyAsync(h_ctl, ctl, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaMemcpyAsync(lvh.data(), lv, lvh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -948,13 +1064,45 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
         rc = DFGT_ECAPACITY;
         goto fail;
       }
+      // grow: a new arena and node scratch, the finished levels copied over
       const size_t nc = std::max(need + need / 2, cap * 2);
-      TRY(grow_nodes(ctx->bnodes, na, keep, (size_t)h_ctl[3], nc, d, s));
+      const size_t nl = (size_t)h_ctl[3];
+      dfgt_tree old = *t;
+      DevBuf nsb;
+      NodeScratch ns2;
+      cudaError_t ce = alloc_tree(ctx, t, np, nc);
+      if (ce == cudaSuccess) ce = nsb.ensure(NodeScratch::bytes(nc));
+      if (ce == cudaSuccess) {
+        ns2.carve(nsb.as<char>(), nc);
+        ce = copy_d2d(t->lo, old.lo, keep * d * sizeof(float), s, ce);
+        ce = copy_d2d(t->hi, old.hi, keep * d * sizeof(float), s, ce);
+        ce = copy_d2d(t->beg, old.beg, keep * sizeof(int), s, ce);
+        ce = copy_d2d(t->cnt, old.cnt, keep * sizeof(int), s, ce);
+        ce = copy_d2d(t->left, old.left, keep * sizeof(int), s, ce);
+        ce = copy_d2d(t->parent, old.parent, keep * sizeof(int), s, ce);
+        ce = copy_d2d(t->leaves, old.leaves, nl * sizeof(int), s, ce);
+        ce = copy_d2d(ns2.nleft, ns.nleft, keep * sizeof(int), s, ce);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(ns2.arrive, 0, keep * sizeof(int), s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+      }
+      if (old.arena != t->arena) {
+        // the arena that is not kept goes back to the pool
+        std::lock_guard<std::mutex> g(ctx->tpool->m);
+        cudaFreeAsync(ce == cudaSuccess ? old.arena : t->arena, s);
+        if (ce != cudaSuccess) *t = old;
+      }
+      if (ce != cudaSuccess) {
+        nsb.release();
+        ctx->err = std::string("dfgt_build: growing the node arrays: ") + cudaGetErrorString(ce);
+        goto fail;
+      }
+      ctx->bnodes.release();
+      ctx->bnodes = nsb;
+      ns = ns2;
       cap = nc;
       init_from = (int)keep;
     }
-    cur = h_ctl[1];
-    last = h_ctl[2];
+    const int last = h_ctl[2];
     t->nleaves = h_ctl[3];
     t->lvl_off.assign(1, 0);
     for (int Lk = 0; Lk <= last; ++Lk) t->lvl_off.push_back(lvh[3 * Lk + 1]);
@@ -966,59 +1114,6 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
     rc = DFGT_ECAPACITY;
     goto fail;
   }
-  {
-    // the tree's arena: one allocation from the context's pool
-    const size_t nn = (size_t)t->nn, P = (size_t)t->P;
-    Carver ca;
-    for (int pass = 0; pass < 2; ++pass) {
-      ca.off = 0;
-      t->pts = ca.take<float>(np * t->dp);
-      t->perm = ca.take<int>(np);
-      t->leaves = ca.take<int>(nn);
-      t->lo = ca.take<float>(nn * d);
-      t->hi = ca.take<float>(nn * d);
-      t->beg = ca.take<int>(nn);
-      t->cnt = ca.take<int>(nn);
-      t->left = ca.take<int>(nn);
-      t->parent = ca.take<int>(nn);
-      t->mom = ca.take<double>(nn * P);
-      t->chi = ca.take<float>(nn * d);
-      t->clo = ca.take<float>(nn * d);
-      t->whalf = ca.take<float>(nn);
-      t->mnorm = ca.take<float>(nn * P);
-      if (pass == 0) {
-        t->tpool = ctx->tpool;
-        TRY(cudaMallocFromPoolAsync(&t->arena, ca.off, ctx->tpool->pool, s));
-        ca.base = static_cast<char*>(t->arena);
-      }
-    }
-    cudaError_t ce = cudaSuccess;
-    ce = copy_d2d(t->pts, pbuf[cur], np * t->dp * sizeof(float), s, ce);
-    ce = copy_d2d(t->perm, perm2[cur], np * sizeof(int), s, ce);
-    ce = copy_d2d(t->lo, na.lo, nn * d * sizeof(float), s, ce);
-    ce = copy_d2d(t->hi, na.hi, nn * d * sizeof(float), s, ce);
-    ce = copy_d2d(t->beg, na.beg, nn * sizeof(int), s, ce);
-    ce = copy_d2d(t->cnt, na.cnt, nn * sizeof(int), s, ce);
-    ce = copy_d2d(t->left, na.left, nn * sizeof(int), s, ce);
-    ce = copy_d2d(t->parent, na.parent, nn * sizeof(int), s, ce);
-    ce = copy_d2d(t->leaves, na.leaves, (size_t)t->nleaves * sizeof(int), s, ce);
-    TRY(ce);
-  }
-  switch (d) {
-    case 1: TRY(moments_d<1>(t, s, L)); break;
-    case 2: TRY(moments_d<2>(t, s, L)); break;
-    case 3: TRY(moments_d<3>(t, s, L)); break;
-    case 4: TRY(moments_d<4>(t, s, L)); break;
-    case 5: TRY(moments_d<5>(t, s, L)); break;
-    default:
-      k_count_moments<<<(t->nn + kT - 1) / kT, kT, 0, s>>>(t->view(), t->mom);
-      ++*L;
-      TRY(cudaGetLastError());
-  }
-  k_node_float_data<<<(t->nn + kT - 1) / kT, kT, 0, s>>>(t->view(), t->pm, t->chi, t->clo, t->whalf, t->mnorm);
-  ++*L;
-  TRY(cudaGetLastError());
-  TRY(cudaStreamSynchronize(s));  // calls return after their work
   rc = DFGT_OK;
 fail:
   if (rc != DFGT_OK) {
