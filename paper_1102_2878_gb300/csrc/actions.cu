@@ -781,9 +781,20 @@ struct LocalShape {
   static constexpr int NSTR = 32 / NPRE;               // streams per prefix
 };
 
+// Local moments over a balanced split: the references of all sorted
+// entries form one concatenated sequence (entry e covers [eoff[e],
+// eoff[e+1])), and warp k of NW takes the k-th of NW equal slices of it, so
+// no warp waits on one large reference node.  A warp walks its slice 32
+// entries at a time; consecutive entries of one (bandwidth, query node) key
+// form a run whose coefficients accumulate in registers, and they are
+// added to the node's moments (float64 atomics) when the key changes or the
+// slice ends.  Each reference is tabulated once per lane (Hermite values
+// h_e((Q.c - r) s), zero beyond the entry's order), and lane (stream,
+// prefix) owns the coefficients of one prefix of the multi-index.
 template <int D>
 __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
-                                                 const int* __restrict__ ksorted, int n,
+                                                 const int* __restrict__ ksorted,
+                                                 const long long* __restrict__ eoff, int n,
                                                  const float* __restrict__ sfv,
                                                  double* __restrict__ L, int* __restrict__ pused) {
   using LS = LocalShape<D>;
@@ -793,23 +804,30 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
   constexpr int kFlush = 8;  // batches between compensated additions
   __shared__ __align__(16) float sH[kWarpsPerBlock][32][D][PM];
   __shared__ float sRed[kWarpsPerBlock][NSTR][P];
-  __shared__ int sOff[kWarpsPerBlock][33], sRb[kWarpsPerBlock][32], sRp[kWarpsPerBlock][32];
+  __shared__ long long sOff[kWarpsPerBlock][33];
+  __shared__ int sRb[kWarpsPerBlock][32], sRp[kWarpsPerBlock][32];
   const unsigned FULL = 0xffffffffu;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kEntryChunk;
-  if (i0 >= n) return;
-  const int m = (int)min((long)kEntryChunk, n - i0);
-  int key = -1 - lane, rb = 0, rn = 0, rp = 0;
-  if (lane < m) {
-    key = ksorted[i0 + lane];
-    const int v = rsorted[i0 + lane];
-    const int r = v & kNodeMask;
-    rp = v >> kNodeBits;
-    rb = R.beg[r];
-    rn = R.cnt[r];
+  const long long gw = (long long)blockIdx.x * kWarpsPerBlock + wib, NW = (long long)gridDim.x * kWarpsPerBlock;
+  const long long T = eoff[n];
+  const long long per = T / NW, extra = T % NW;
+  const long long lo = per * gw + min(gw, extra);
+  const long long hi = lo + per + (gw < extra ? 1 : 0);
+  if (lo >= hi) return;
+  // the entry holding reference lo: the last e with eoff[e] <= lo, found 32
+  // probes at a time (eoff[base] <= lo holds throughout)
+  int base = 0, len = n;
+  while (len > 32) {
+    const int step = (len + 31) / 32;
+    const int idx = base + lane * step;
+    const unsigned ok = __ballot_sync(FULL, idx < base + len && eoff[idx] <= lo);
+    const int l = 31 - __clz(ok);
+    const int nb = base + l * step;
+    len = min(step, base + len - nb);
+    base = nb;
   }
-  const int keyp = __shfl_up_sync(FULL, key, 1);
-  const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
+  int e = base + 31 - __clz(__ballot_sync(FULL, lane < len && eoff[base + lane] <= lo));
+
   // this lane's prefix, stream and prefix digits
   const int pre = lane % NPRE, str = lane / NPRE;
   int pd[D - B > 0 ? D - B : 1];
@@ -818,110 +836,22 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
 #pragma unroll
     for (int k = D - B - 1; k >= 0; --k) { pd[k] = v % PM; v /= PM; }
   }
-  int t = 0;
-  while (t < m) {
-    const unsigned later = starts & ~((2u << t) - 1u);
-    const int e = later ? __ffs(later) - 1 : m;
-    const int key_t = __shfl_sync(FULL, key, t);
-    const int hidx = key_t / Q.nn, q = key_t - hidx * Q.nn;
-    const float sf = sfv[hidx];
-    CenterHL cQ[D];
+  float2 accS[NB2], accC[NB2], blk[NB2];
 #pragma unroll
-    for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, q, k);
-    // the run's entries t..e-1 as a table: offset in the concatenated list,
-    // first point, order
-    const int in_run = (lane >= t && lane < e) ? rn : 0;
-    int incl = in_run;
+  for (int i = 0; i < NB2; ++i) accS[i] = accC[i] = blk[i] = make_float2(0.f, 0.f);
+  int cur_key = -1, prun = 0, nb = 0;
+  float sf = 0.f;
+  CenterHL cQ[D];
+
+  // adds the run's coefficients to the query node's moments and clears them
+  auto flush = [&]() {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += v;
+    for (int i = 0; i < NB2; ++i) {
+      kahan_add(accS[i].x, accC[i].x, blk[i].x);
+      kahan_add(accS[i].y, accC[i].y, blk[i].y);
+      blk[i] = make_float2(0.f, 0.f);
     }
-    const int tot = __shfl_sync(FULL, incl, 31);
-    const int prun = __reduce_max_sync(FULL, (lane >= t && lane < e) ? rp : 0);
-    if (lane >= t && lane < e) {
-      sOff[wib][lane - t] = incl - in_run;
-      sRb[wib][lane - t] = rb;
-      sRp[wib][lane - t] = rp;
-    }
-    if (lane == 0) sOff[wib][e - t] = tot;
-    __syncwarp();
-    // reference J of the run (J advances by 32 per batch, so a cursor over
-    // the table moves forward only)
-    int cur = 0;
-    auto fetch = [&](int J, float* pv, int& pp) {
-      if (J < tot) {
-        while (sOff[wib][cur + 1] <= J) ++cur;
-        pp = sRp[wib][cur];
-        load_point<D>(R.pts + (size_t)(sRb[wib][cur] + J - sOff[wib][cur]) * R.dp, pv);
-      } else {
-        pp = 0;
-#pragma unroll
-        for (int k = 0; k < D; ++k) pv[k] = 0.f;
-      }
-    };
-    float2 accS[NB2], accC[NB2], blk[NB2];
-#pragma unroll
-    for (int i = 0; i < NB2; ++i) accS[i] = accC[i] = blk[i] = make_float2(0.f, 0.f);
-    float pv[D];
-    int pp = 0;
-    fetch(lane, pv, pp);
-    int nb = 0;
-    for (int j0 = 0; j0 < tot; j0 += 32) {
-      // tabulate this lane's reference: h_e((Q.c - r) s) for e < p, 0 beyond
-#pragma unroll
-      for (int k = 0; k < D; ++k) {
-        float H[PM];
-        hermite_f32<PM>(-minus_center(pv[k], cQ[k]) * sf, H);
-#pragma unroll
-        for (int e2 = 0; e2 < PM; e2 += 2)
-          *reinterpret_cast<float2*>(&sH[wib][lane][k][e2]) =
-              make_float2(e2 < pp ? H[e2] : 0.f, e2 + 1 < pp ? H[e2 + 1] : 0.f);
-      }
-      __syncwarp();
-      float nv[D];
-      int np = 0;
-      if (j0 + 32 < tot) fetch(j0 + 32 + lane, nv, np);
-      // this lane's stream: references str, str + NSTR, ...
-      if (str < NSTR) {
-        for (int j = str; j < 32; j += NSTR) {
-          float pr = 1.f;
-#pragma unroll
-          for (int k = 0; k < D - B; ++k) pr *= sH[wib][j][k][pd[k]];
-          const float2* hl = reinterpret_cast<const float2*>(&sH[wib][j][D - 1][0]);
-          if constexpr (B == 1) {
-            const float2 p2 = make_float2(pr, pr);
-#pragma unroll
-            for (int i = 0; i < NB2; ++i) blk[i] = __ffma2_rn(p2, hl[i], blk[i]);
-          } else {
-#pragma unroll
-            for (int e1 = 0; e1 < PM; ++e1) {
-              const float t1 = pr * sH[wib][j][D - 2][e1];
-              const float2 t2 = make_float2(t1, t1);
-#pragma unroll
-              for (int i = 0; i < PM / 2; ++i)
-                blk[e1 * (PM / 2) + i] = __ffma2_rn(t2, hl[i], blk[e1 * (PM / 2) + i]);
-            }
-          }
-        }
-      }
-      if (++nb == kFlush || j0 + 32 >= tot) {
-        nb = 0;
-#pragma unroll
-        for (int i = 0; i < NB2; ++i) {
-          kahan_add(accS[i].x, accC[i].x, blk[i].x);
-          kahan_add(accS[i].y, accC[i].y, blk[i].y);
-          blk[i] = make_float2(0.f, 0.f);
-        }
-      }
-      __syncwarp();
-      if (j0 + 32 < tot) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) pv[k] = nv[k];
-        pp = np;
-      }
-    }
-    // streams -> coefficients
+    nb = 0;
     if (str < NSTR) {
 #pragma unroll
       for (int i = 0; i < NB2; ++i) {
@@ -929,7 +859,10 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
         sRed[wib][str][pre * NB + 2 * i + 1] = accS[i].y - accC[i].y;
       }
     }
+#pragma unroll
+    for (int i = 0; i < NB2; ++i) accS[i] = accC[i] = make_float2(0.f, 0.f);
     __syncwarp();
+    const int hidx = cur_key / Q.nn, q = cur_key - hidx * Q.nn;
     const size_t hq = (size_t)hidx * Q.nn + q;
 #pragma unroll
     for (int sl = 0; sl < S; ++sl) {
@@ -951,8 +884,124 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
     }
     if (lane == 0) atomicMax(&pused[hq], prun);
     __syncwarp();
-    t = e;
+  };
+
+  long long pos = lo;
+  while (pos < hi) {
+    // a window of 32 entries: offsets, first points, orders, keys
+    const int ei = e + lane;
+    int key = -1, rb = 0, rp = 0;
+    long long eo = T, ee = T;
+    if (ei < n) {
+      key = ksorted[ei];
+      const int v = rsorted[ei];
+      rp = v >> kNodeBits;
+      rb = R.beg[v & kNodeMask];
+      eo = eoff[ei];
+      ee = eoff[ei + 1];
+    }
+    sOff[wib][lane] = eo;
+    sRb[wib][lane] = rb;
+    sRp[wib][lane] = rp;
+    if (lane == 31) sOff[wib][32] = ee;
+    const int keyp = __shfl_up_sync(FULL, key, 1);
+    const unsigned starts = __ballot_sync(FULL, lane == 0 || key != keyp);
+    __syncwarp();
+    int t = 0;
+    while (t < 32) {
+      const unsigned later = starts & ~((2u << t) - 1u);
+      const int u = later ? __ffs(later) - 1 : 32;
+      const long long a = max(pos, sOff[wib][t]), b = min(hi, sOff[wib][u]);
+      const int key_t = __shfl_sync(FULL, key, t);
+      const int prun_t = __reduce_max_sync(FULL, (lane >= t && lane < u) ? rp : 0);
+      if (a < b && key_t >= 0) {
+        if (key_t != cur_key) {
+          if (cur_key >= 0) flush();
+          cur_key = key_t;
+          prun = 0;
+          const int hidx = key_t / Q.nn, q = key_t - hidx * Q.nn;
+          sf = sfv[hidx];
+#pragma unroll
+          for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, q, k);
+        }
+        prun = max(prun, prun_t);
+        // references a .. b-1 of the run, 32 per batch; a lane's table
+        // cursor only moves forward
+        int cur = t;
+        auto fetch = [&](long long J, float* pv, int& pp) {
+          if (J < b) {
+            while (cur + 1 < u && sOff[wib][cur + 1] <= J) ++cur;
+            pp = sRp[wib][cur];
+            load_point<D>(R.pts + (size_t)(sRb[wib][cur] + (J - sOff[wib][cur])) * R.dp, pv);
+          } else {
+            pp = 0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) pv[k] = 0.f;
+          }
+        };
+        float pv[D];
+        int pp = 0;
+        fetch(a + lane, pv, pp);
+        for (long long j0 = a; j0 < b; j0 += 32) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            float H[PM];
+            hermite_f32<PM>(-minus_center(pv[k], cQ[k]) * sf, H);
+#pragma unroll
+            for (int e2 = 0; e2 < PM; e2 += 2)
+              *reinterpret_cast<float2*>(&sH[wib][lane][k][e2]) =
+                  make_float2(e2 < pp ? H[e2] : 0.f, e2 + 1 < pp ? H[e2 + 1] : 0.f);
+          }
+          __syncwarp();
+          float nv[D];
+          int np = 0;
+          if (j0 + 32 < b) fetch(j0 + 32 + lane, nv, np);
+          if (str < NSTR) {
+            for (int j = str; j < 32; j += NSTR) {
+              float pr = 1.f;
+#pragma unroll
+              for (int k = 0; k < D - B; ++k) pr *= sH[wib][j][k][pd[k]];
+              const float2* hl = reinterpret_cast<const float2*>(&sH[wib][j][D - 1][0]);
+              if constexpr (B == 1) {
+                const float2 p2 = make_float2(pr, pr);
+#pragma unroll
+                for (int i = 0; i < NB2; ++i) blk[i] = __ffma2_rn(p2, hl[i], blk[i]);
+              } else {
+#pragma unroll
+                for (int e1 = 0; e1 < PM; ++e1) {
+                  const float t1 = pr * sH[wib][j][D - 2][e1];
+                  const float2 t2 = make_float2(t1, t1);
+#pragma unroll
+                  for (int i = 0; i < PM / 2; ++i)
+                    blk[e1 * (PM / 2) + i] = __ffma2_rn(t2, hl[i], blk[e1 * (PM / 2) + i]);
+                }
+              }
+            }
+          }
+          if (++nb == kFlush) {
+            nb = 0;
+#pragma unroll
+            for (int i = 0; i < NB2; ++i) {
+              kahan_add(accS[i].x, accC[i].x, blk[i].x);
+              kahan_add(accS[i].y, accC[i].y, blk[i].y);
+              blk[i] = make_float2(0.f, 0.f);
+            }
+          }
+          __syncwarp();
+          if (j0 + 32 < b) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) pv[k] = nv[k];
+            pp = np;
+          }
+        }
+      }
+      t = u;
+    }
+    pos = max(pos, sOff[wib][32]);
+    e += 32;
+    __syncwarp();
   }
+  if (cur_key >= 0) flush();
 }
 
 // --------------------------------------------------------- far to local
@@ -1333,6 +1382,11 @@ cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuff
   return cudaGetLastError();
 }
 
+__global__ void k_entry_refs(const TreeView R, const int* __restrict__ rsorted, int n, int* __restrict__ cnt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) cnt[i] = R.cnt[rsorted[i] & kNodeMask];
+}
+
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                          const Action* list, int n, BaseScratch& sc, cudaStream_t s,
                          long long* launches) {
@@ -1342,9 +1396,17 @@ cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers
     cudaError_t e = sort_by_query(reinterpret_cast<const Pair*>(list), n, Q.nn, b.nh, sc, s, launches,
                                   &vsorted, &ksorted);
     if (e != cudaSuccess) return e;
-    const long warps = (n + kEntryChunk - 1) / kEntryChunk;
-    const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, vsorted, ksorted, n, b.sf, b.L, b.pused));
+    // reference counts of the sorted entries and their 64-bit prefix
+    if ((e = sc.cnt->ensure((size_t)n * sizeof(int))) != cudaSuccess) return e;
+    if ((e = sc.off->ensure(((size_t)n + 1) * sizeof(long long))) != cudaSuccess) return e;
+    k_entry_refs<<<(n + kT - 1) / kT, kT, 0, s>>>(R, vsorted, n, sc.cnt->as<int>());
+    ++*launches;
+    if ((e = scan_exclusive64(sc.cnt->as<int>(), sc.off->as<long long>(), n, *sc.scan_tmp, s, launches)) !=
+        cudaSuccess)
+      return e;
+    const int g = 3 * std::max(1, b.sms);  // every warp resident: three blocks per SM
+    DISPATCH_D(Q.d, k_local<DD><<<g, kT, 0, s>>>(Q, R, vsorted, ksorted, sc.off->as<long long>(), n, b.sf, b.L,
+                                                  b.pused));
   } else {
     k_local_g<<<warp_grid(n), kT, 0, s>>>(Q, R, list, n, b.h, b.L, b.pused);
   }

@@ -118,6 +118,10 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   // tau = eps_eff |R| G^l / |R_total| with G^l = lb |R_total| 2^-62
   b->tau_scale_dn = std::nextafter((float)std::ldexp(eps_eff, -62), 0.f);
   b->p_limit = std::min(qt->p_limit, rt->p_limit);
+  if (ctx->sms == 0 &&
+      cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device) != cudaSuccess)
+    return fail(ctx, DFGT_ECUDA, "dfgt_sum: device query failed");
+  b->sms = ctx->sms;
   return DFGT_OK;
 }
 

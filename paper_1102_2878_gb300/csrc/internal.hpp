@@ -96,6 +96,7 @@ struct dfgt_ctx {
   DevBuf bscratch;          // tree-build per-point scratch
   DevBuf bnodes;            // tree-build per-node scratch (left counts, prefixes, split ranks)
   std::shared_ptr<TreePool> tpool;
+  int sms = 0;                // SMs of the device (0: not yet queried)
   int build_grid = 0;         // blocks of the cooperative level build (0: not yet chosen)
   int mom_grid[6] = {};       // blocks of the cooperative moment pass per dimension (0: D >= 6)
   size_t cap_frontier = 1 << 20;
@@ -143,6 +144,9 @@ namespace dfgt {
 // scan.cu: exclusive prefix sum of n int32 values into out[0..n].
 cudaError_t scan_exclusive(const int* in, int* out, int n, DevBuf& tmp, cudaStream_t s,
                            long long* launches);
+// The same with 64-bit sums: out[0..n] of int64.
+cudaError_t scan_exclusive64(const int* in, long long* out, int n, DevBuf& tmp, cudaStream_t s,
+                             long long* launches);
 
 // bruteforce.cu
 // Slices the references are split into for nq queries (1 = no split).
@@ -191,6 +195,7 @@ struct TravBuffers {
   double inv_nr;    // 1 / |R|
   int p_limit;
   long long base_block;  // exact sum without recursing when |Q||R| <= this
+  int sms;               // SMs of the device (sizes the balanced launches)
 };
 
 cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s);
