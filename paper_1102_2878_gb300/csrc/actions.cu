@@ -759,11 +759,11 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
 // ------------------------------------------------------------ direct local
 // AccumulateDirectLocalMoment:
 // L_beta(Q) += ((-1)^{|beta|}/beta!) sum_{r in R} h_beta((Q.c - r)/sqrt(2h^2)).
-// The list is sorted by (bandwidth, query node) like the base case, and a
-// warp takes kEntryChunk consecutive sorted entries, one per lane; a run of
-// one query node is one concatenated list of references, taken in batches
-// of 32 (one per lane, the next batch's point loaded while the current one
-// is summed).  The coefficient sum_r prod_k h_{beta_k}(t_rk) factors over
+// The list is sorted by (bandwidth, query node) like the base case, and
+// the warps split the sorted entries' references evenly (k_local below); a
+// run of one query node is one concatenated list of references, taken in
+// batches of 32 (one per lane, the next batch's point loaded while the
+// current one is summed).  The coefficient sum_r prod_k h_{beta_k}(t_rk) factors over
 // dimensions, so a lane owns the coefficients of one prefix (beta_0 ..
 // beta_{D-B-1}) and all PM^B values of the last B digits: per reference it
 // forms the prefix product once and multiplies it out over the block, with
@@ -781,16 +781,19 @@ struct LocalShape {
   static constexpr int NSTR = 32 / NPRE;               // streams per prefix
 };
 
-// Local moments over a balanced split: the references of all sorted
-// entries form one concatenated sequence (entry e covers [eoff[e],
-// eoff[e+1])), and warp k of NW takes the k-th of NW equal slices of it, so
-// no warp waits on one large reference node.  A warp walks its slice 32
+// Local moments over a balanced split: every sorted entry weighs its
+// reference count plus kEntryCost (its share of the fixed per-entry and
+// per-run work, in reference units), the weights form one sequence (entry e
+// covers [eoff[e], eoff[e+1]): kEntryCost units of set-up, then one unit
+// per reference), and warp k of NW takes the k-th of NW equal slices of it,
+// so no warp waits on one large reference node.  A warp walks its slice 32
 // entries at a time; consecutive entries of one (bandwidth, query node) key
 // form a run whose coefficients accumulate in registers, and they are
 // added to the node's moments (float64 atomics) when the key changes or the
 // slice ends.  Each reference is tabulated once per lane (Hermite values
 // h_e((Q.c - r) s), zero beyond the entry's order), and lane (stream,
 // prefix) owns the coefficients of one prefix of the multi-index.
+constexpr int kEntryCost = 32;
 template <int D>
 __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                                  const int* __restrict__ ksorted,
@@ -804,8 +807,7 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
   constexpr int kFlush = 8;  // batches between compensated additions
   __shared__ __align__(16) float sH[kWarpsPerBlock][32][D][PM];
   __shared__ float sRed[kWarpsPerBlock][NSTR][P];
-  __shared__ long long sOff[kWarpsPerBlock][33];
-  __shared__ int sRb[kWarpsPerBlock][32], sRp[kWarpsPerBlock][32];
+  __shared__ int sCum[kWarpsPerBlock][33], sRs[kWarpsPerBlock][32], sRp[kWarpsPerBlock][32];
   const unsigned FULL = 0xffffffffu;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long gw = (long long)blockIdx.x * kWarpsPerBlock + wib, NW = (long long)gridDim.x * kWarpsPerBlock;
@@ -888,22 +890,36 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
 
   long long pos = lo;
   while (pos < hi) {
-    // a window of 32 entries: offsets, first points, orders, keys
+    // a window of 32 entries: the part of each entry's references inside
+    // the slice (first point, count), orders, keys, and the window-wide
+    // prefix of the counts
     const int ei = e + lane;
-    int key = -1, rb = 0, rp = 0;
-    long long eo = T, ee = T;
+    int key = -1, rp = 0, rs = 0, c = 0;
+    long long ee = T;
     if (ei < n) {
       key = ksorted[ei];
       const int v = rsorted[ei];
       rp = v >> kNodeBits;
-      rb = R.beg[v & kNodeMask];
-      eo = eoff[ei];
+      const int rb = R.beg[v & kNodeMask];
+      const long long eo = eoff[ei] + kEntryCost;
       ee = eoff[ei + 1];
+      const long long s0 = max(pos, eo), s1 = min(hi, ee);
+      if (s1 > s0) {
+        c = (int)(s1 - s0);
+        rs = rb + (int)(s0 - eo);
+      }
     }
-    sOff[wib][lane] = eo;
-    sRb[wib][lane] = rb;
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    sCum[wib][lane] = incl - c;
+    sRs[wib][lane] = rs;
     sRp[wib][lane] = rp;
-    if (lane == 31) sOff[wib][32] = ee;
+    if (lane == 31) sCum[wib][32] = incl;
+    const long long wend = __shfl_sync(FULL, ee, 31);
     const int keyp = __shfl_up_sync(FULL, key, 1);
     const unsigned starts = __ballot_sync(FULL, lane == 0 || key != keyp);
     __syncwarp();
@@ -911,9 +927,9 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
     while (t < 32) {
       const unsigned later = starts & ~((2u << t) - 1u);
       const int u = later ? __ffs(later) - 1 : 32;
-      const long long a = max(pos, sOff[wib][t]), b = min(hi, sOff[wib][u]);
+      const int a = sCum[wib][t], b = sCum[wib][u];
       const int key_t = __shfl_sync(FULL, key, t);
-      const int prun_t = __reduce_max_sync(FULL, (lane >= t && lane < u) ? rp : 0);
+      const int prun_t = __reduce_max_sync(FULL, (lane >= t && lane < u && c > 0) ? rp : 0);
       if (a < b && key_t >= 0) {
         if (key_t != cur_key) {
           if (cur_key >= 0) flush();
@@ -925,14 +941,14 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
           for (int k = 0; k < D; ++k) cQ[k] = center_hl(Q, q, k);
         }
         prun = max(prun, prun_t);
-        // references a .. b-1 of the run, 32 per batch; a lane's table
-        // cursor only moves forward
+        // references a .. b-1 of the window's concatenation, 32 per batch;
+        // a lane's table cursor only moves forward
         int cur = t;
-        auto fetch = [&](long long J, float* pv, int& pp) {
+        auto fetch = [&](int J, float* pv, int& pp) {
           if (J < b) {
-            while (cur + 1 < u && sOff[wib][cur + 1] <= J) ++cur;
+            while (cur + 1 < u && sCum[wib][cur + 1] <= J) ++cur;
             pp = sRp[wib][cur];
-            load_point<D>(R.pts + (size_t)(sRb[wib][cur] + (J - sOff[wib][cur])) * R.dp, pv);
+            load_point<D>(R.pts + (size_t)(sRs[wib][cur] + (J - sCum[wib][cur])) * R.dp, pv);
           } else {
             pp = 0;
 #pragma unroll
@@ -942,7 +958,7 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
         float pv[D];
         int pp = 0;
         fetch(a + lane, pv, pp);
-        for (long long j0 = a; j0 < b; j0 += 32) {
+        for (int j0 = a; j0 < b; j0 += 32) {
 #pragma unroll
           for (int k = 0; k < D; ++k) {
             float H[PM];
@@ -997,7 +1013,7 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
       }
       t = u;
     }
-    pos = max(pos, sOff[wib][32]);
+    pos = max(pos, wend);
     e += 32;
     __syncwarp();
   }
@@ -1371,7 +1387,7 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
 }
 
 cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Action* list, int n, cudaStream_t s) {
+                            const Action* list, int n, BaseScratch&, cudaStream_t s, long long* launches) {
   if (n <= 0) return cudaSuccess;
   const int g = warp_grid(n);
   if (Q.d <= 5) {
@@ -1379,12 +1395,13 @@ cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuff
   } else {
     k_farfield_g<<<g, kT, 0, s>>>(Q, R, list, n, b.h, b.gacc);
   }
+  ++*launches;
   return cudaGetLastError();
 }
 
 __global__ void k_entry_refs(const TreeView R, const int* __restrict__ rsorted, int n, int* __restrict__ cnt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) cnt[i] = R.cnt[rsorted[i] & kNodeMask];
+  if (i < n) cnt[i] = R.cnt[rsorted[i] & kNodeMask] + kEntryCost;
 }
 
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,

@@ -168,13 +168,16 @@ dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const
     BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
     CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), ls.count, sc, s, &ctx->launches));
   }
-  else if (which == 1) CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), ls.count, s));
-  else if (which == 2) {
+  else if (which == 1) {
+    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+    CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), ls.count, sc, s, &ctx->launches));
+  } else if (which == 2) {
     BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
     CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), ls.count, sc, s, &ctx->launches));
+  } else {
+    CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), ls.count, s));
+    ++ctx->launches;
   }
-  else CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), ls.count, s));
-  ++ctx->launches;
   CK(cudaEventRecord(ls.e1, s));
   ls.timed = true;
   CK(cudaMemsetAsync(dcount, 0, sizeof(int), s));
@@ -646,7 +649,7 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   CK(launch_prune_apply(Q, R, b, ctx->frontier[0].as<Pair>(), (int)prune.size(), s));
   BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
   CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), (int)base.size(), sc, s, &ctx->launches));
-  CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), (int)far.size(), s));
+  CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), (int)far.size(), sc, s, &ctx->launches));
   CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), (int)loc.size(), sc, s, &ctx->launches));
   CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), (int)f2l.size(), s));
   CK(cudaEventRecord(ctx->ev[2], s));

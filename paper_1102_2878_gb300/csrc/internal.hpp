@@ -217,7 +217,7 @@ struct BaseScratch {
 cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                         const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
 cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Action* list, int n, cudaStream_t s);
+                            const Action* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                          const Action* list, int n, BaseScratch& sc, cudaStream_t s,
                          long long* launches);
