@@ -53,6 +53,8 @@ def _load():
     lib.orc_cv_lk.restype = C.c_double
     lib.orc_cv_ls.argtypes = [dp, i64, C.c_int, C.c_double]
     lib.orc_cv_ls.restype = C.c_double
+    lib.orc_cv_lk_grad.argtypes = [dp, i64, C.c_int, C.c_double, dp, dp]
+    lib.orc_cv_lk_grad.restype = None
     lib.orc_pmax.argtypes = [C.c_int]
     lib.orc_pmax.restype = C.c_int
     lib.orc_multi_to_pos.argtypes = [ip, C.c_int, C.c_int]
@@ -135,6 +137,17 @@ def cv_lk(X, h):
     """Likelihood cross-validation score CV_LK(h) of the introduction."""
     X, xp = _d(X)
     return _load().orc_cv_lk(xp, X.shape[0], X.shape[1], float(h))
+
+
+def cv_lk_grad(X, h):
+    """(dCV_LK/dlog h, dCV_LK/dx [n][D]) from the derivative of the definition."""
+    X, xp = _d(X)
+    n, D = X.shape
+    assert D <= 64
+    dx, dxp = _d(np.empty((n, D)))
+    g = C.c_double()
+    _load().orc_cv_lk_grad(xp, n, D, float(h), C.byref(g), dxp)
+    return g.value, dx
 
 
 def cv_ls(X, h):

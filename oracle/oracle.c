@@ -250,6 +250,42 @@ double orc_cv_ls(const double* X, int64_t n, int D, double h) {
   return acc / (double)n;
 }
 
+/* Gradient of CV_LK(h) with respect to log h and to every point x_k.
+ * With K_ij = exp(-|x_i - x_j|^2 / 2h^2) and S_i the leave-one-out sums,
+ *   dCV/dlog h = (1/N) sum_i (1/S_i) sum_{j != i} K_ij |x_i - x_j|^2 / h^2 - D
+ * (dK/dlog h = K |x_i - x_j|^2 / h^2, and log V_{D,h} grows by D per unit of
+ * log h), and, since x_k enters S_k and every S_j with j != k,
+ *   dCV/dx_k = -(1/(N h^2)) sum_{j != k} K_kj (x_k - x_j) (1/S_k + 1/S_j).
+ * Plain double loops over all pairs; dx is [n][D]. */
+void orc_cv_lk_grad(const double* X, int64_t n, int D, double h, double* dlogh, double* dx) {
+  double* S = (double*)malloc(sizeof(double) * (size_t)n);
+  orc_loo_sums(X, n, D, h, S);
+  const double inv = 1.0 / (2.0 * h * h), h2 = h * h;
+  double acc = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : acc)
+  for (int64_t k = 0; k < n; ++k) {
+    double a = 0.0;
+    double g[64];
+    for (int d = 0; d < D; ++d) g[d] = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == k) continue;
+      double d2 = 0.0;
+      for (int d = 0; d < D; ++d) {
+        const double t = X[k * D + d] - X[j * D + d];
+        d2 += t * t;
+      }
+      const double K = exp(-d2 * inv);
+      a += K * d2 / h2;
+      const double w = K * (1.0 / S[k] + 1.0 / S[j]);
+      for (int d = 0; d < D; ++d) g[d] += w * (X[k * D + d] - X[j * D + d]);
+    }
+    acc += a / S[k];
+    for (int d = 0; d < D; ++d) dx[k * D + d] = -g[d] / ((double)n * h2);
+  }
+  *dlogh = acc / (double)n - (double)D;
+  free(S);
+}
+
 /* ------------------------------------------------------------------ */
 /* Expansions (Section 3.3) and translations (Section 3.5)             */
 /* All tables have radix pm; only multi-indices below p are written.   */

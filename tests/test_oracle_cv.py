@@ -74,3 +74,41 @@ def test_invariances():
     # densities scale by s^-D when points and bandwidth scale by s
     assert oracle.cv_lk(s * X, s * h) == pytest.approx(lk - 2 * math.log(s), rel=1e-12)
     assert oracle.cv_ls(s * X, s * h) == pytest.approx(ls / s ** 2, rel=1e-11)
+
+
+# ------------------------------------------------------ gradient of CV_LK
+@pytest.mark.parametrize("D,h", [(1, 0.05), (2, 0.08), (3, 0.15)])
+def test_cv_lk_grad_log_h_central_difference(D, h):
+    rng = np.random.default_rng(10 + D)
+    X = rng.random((60, D))
+    g, _ = oracle.cv_lk_grad(X, h)
+    dl = 1e-4
+    fd = (oracle.cv_lk(X, h * math.exp(dl)) - oracle.cv_lk(X, h * math.exp(-dl))) / (2 * dl)
+    assert g == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("D,h", [(1, 0.05), (2, 0.08), (3, 0.15)])
+def test_cv_lk_grad_points_central_difference(D, h):
+    rng = np.random.default_rng(20 + D)
+    X = rng.random((50, D))
+    _, dx = oracle.cv_lk_grad(X, h)
+    dl = 1e-6
+    for k in (0, 7, 31):
+        for d in range(D):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[k, d] += dl
+            Xm[k, d] -= dl
+            fd = (oracle.cv_lk(Xp, h) - oracle.cv_lk(Xm, h)) / (2 * dl)
+            assert dx[k, d] == pytest.approx(fd, rel=1e-5, abs=1e-7), (k, d)
+
+
+def test_cv_lk_grad_translation_and_scaling_identities():
+    # CV_LK(X + t, h) = CV_LK(X, h): the point gradients sum to zero; and
+    # CV_LK(sX, sh) = CV_LK(X, h) - D log s: sum_k x_k . dx_k + dCV/dlog h = -D
+    rng = np.random.default_rng(5)
+    for D in (1, 2, 4):
+        X = rng.normal(size=(45, D))
+        g, dx = oracle.cv_lk_grad(X, 0.4)
+        scale = np.abs(dx).sum()
+        assert np.abs(dx.sum(0)).max() <= 1e-12 * scale
+        assert float((X * dx).sum()) + g == pytest.approx(-D, abs=1e-10)
