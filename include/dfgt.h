@@ -137,6 +137,23 @@ dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h
                            double eps, double* cv_lk_host, double* cv_ls_host,
                            double* lk_bound_host, double* ls_bound_host, dfgt_stats* stats);
 
+/* Gradient of the leave-one-out likelihood score CV_LK (introduction) with
+ * respect to log h and to every point, from exact sums (the adjoint of the
+ * score's definition; no approximation).  With K_ij = exp(-|x_i-x_j|^2/2h^2)
+ * and S_i = sum_{j != i} K_ij:
+ *   cv[k]        = (1/N) sum_i log(S_i / ((N-1) V_{D,h})),
+ *   dcv_dlogh[k] = (1/N) sum_i sum_{j != i} K_ij |x_i - x_j|^2 / (h^2 S_i) - D,
+ *   dcv_dx[k][i] = -(1/(N h^2)) sum_{j != i} K_ij (x_i - x_j) (1/S_i + 1/S_j).
+ * x_dev: float32 [n][d] points (device, caller-owned, row-major); they are
+ * the query and the reference set.  h_host: nh bandwidths (host).
+ * cv, dcv_dlogh: host arrays of nh; dcv_dx_dev: device float64
+ * [nh][n][d], or NULL for the scalars only.  Two passes over all n^2 pairs
+ * per bandwidth (kernel values in float32, sums in float64).
+ * 2 <= n < 2^29, 1 <= d <= 32, 1 <= nh <= 512; a point with no neighbour
+ * above float32 underflow (S_i = 0) makes cv = -inf and its gradient NaN. */
+dfgt_status dfgt_cv_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n, int d, const double* h_host, int nh,
+                         double* cv, double* dcv_dlogh, double* dcv_dx_dev);
+
 /* Choose the tree options that make a dual-tree sum of these points
  * fastest on this GPU.  No counterpart in the paper (its leaf size is
  * unstated): the leaf size and the exact-sum threshold base_block trade

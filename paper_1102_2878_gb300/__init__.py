@@ -16,8 +16,9 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_bruteforce", "kde_sum_bruteforce_static",
-           "kde_host", "apply_pairs", "build"]
+__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_batches", "kde_sum_bruteforce",
+           "kde_sum_bruteforce_static", "kde_host", "apply_pairs", "cv_scores", "cv_grad", "cv_likelihood",
+           "autotune", "build"]
 
 
 class DFGTError(RuntimeError):
@@ -186,6 +187,56 @@ def cv_scores(ctx: Context, tree: Tree, hs, eps: float):
     ctx.check(st, "dfgt_cv_scores")
     outs["stats"] = stats.as_dict()
     return outs
+
+
+def cv_grad(ctx: Context, points, hs, want_points: bool = True):
+    """dfgt_cv_grad: CV_LK, dCV_LK/dlog h (numpy [nh]) and dCV_LK/dx (float64
+    CUDA tensor [nh, n, d], or None) over the points, from exact sums."""
+    torch = _torch()
+    if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
+            and points.dim() == 2):
+        raise TypeError("points must be a float32 CUDA tensor [n, d]")
+    x = points.contiguous()
+    n, d = x.shape
+    ha, hp = _hs(hs)
+    nh = len(ha)
+    cv, dlogh = np.empty(nh), np.empty(nh)
+    dx = torch.empty((nh, n, d), dtype=torch.float64, device=x.device) if want_points else None
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_cv_grad(ctx.h, C.c_void_p(x.data_ptr()), n, d, hp, nh,
+                              cv.ctypes.data_as(C.POINTER(C.c_double)),
+                              dlogh.ctypes.data_as(C.POINTER(C.c_double)),
+                              C.c_void_p(dx.data_ptr() if dx is not None else 0))
+    ctx.check(st, "dfgt_cv_grad")
+    return cv, dlogh, dx
+
+
+def cv_likelihood(ctx: Context, points, log_h):
+    """CV_LK at the bandwidths exp(log_h) as a differentiable function of
+    the points (float32 CUDA [n, d]) and of log_h (float64 tensor [nh]):
+    the backward pass is the hand-written adjoint of dfgt_cv_grad."""
+    torch = _torch()
+
+    class _CVLikelihood(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, x, lh):
+            hs = torch.exp(lh.detach().double()).cpu().numpy()
+            cv, dlogh, dx = cv_grad(ctx, x.detach(), hs, want_points=x.requires_grad)
+            fctx.save_for_backward(torch.from_numpy(dlogh), dx if dx is not None else torch.empty(0))
+            fctx.has_dx = dx is not None
+            return torch.from_numpy(cv).to(lh.device)
+
+        @staticmethod
+        def backward(fctx, g):
+            dlogh, dx = fctx.saved_tensors
+            g64 = g.double()
+            gl = (g64.cpu() * dlogh).to(g.device)
+            gx = None
+            if fctx.has_dx:
+                gx = torch.einsum("k,knd->nd", g64.to(dx.device), dx).float()
+            return gx, gl
+
+    return _CVLikelihood.apply(points, log_h)
 
 
 def autotune(ctx: Context, points, hs, eps: float, trials: int = 2, p_max: int = 0, eps_fp: float = 0.0):

@@ -474,6 +474,43 @@ dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h
   return DFGT_OK;
 }
 
+dfgt_status dfgt_cv_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n64, int d, const double* h_host, int nh,
+                         double* cv, double* dcv_dlogh, double* dcv_dx_dev) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!x_dev || !cv || !dcv_dlogh || n64 < 2 || n64 > (int64_t)std::numeric_limits<int>::max() / 4 || d < 1 ||
+      d > kMaxD)
+    return fail(ctx, DFGT_EINVAL, "dfgt_cv_grad: need points, 2 <= n < 2^29, 1 <= d <= 32 and score outputs");
+  if (bad_h(h_host, nh) || nh > 512)
+    return fail(ctx, DFGT_EINVAL, "dfgt_cv_grad: need 1..512 finite bandwidths > 0");
+  const int n = (int)n64;
+  const int nb = (n + 255) / 256;
+  const size_t nS = (size_t)n, nP = (size_t)n * d;
+  CK(cudaSetDevice(ctx->device));
+  CK(ctx->grad_buf.ensure((2 * nS + 2 * nP + 2 * (size_t)nb + 2 * (size_t)nh) * sizeof(double)));
+  double* S = ctx->grad_buf.as<double>();
+  double* A = S + nS;
+  double* P = A + nS;
+  double* Y = P + nP;
+  double* part = Y + nP;
+  double* out = part + 2 * (size_t)nb;
+  cudaStream_t s = ctx->stream;
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < nh; ++k) {
+    double* dx = dcv_dx_dev ? dcv_dx_dev + (size_t)k * nP : nullptr;
+    CK(launch_cv_grad(x_dev, n, d, h_host[k], S, P, A, Y, part, out + 2 * k, dx, s, &ctx->launches));
+  }
+  std::vector<double> o(2 * (size_t)nh);
+  CK(cudaMemcpyAsync(o.data(), out, o.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int k = 0; k < nh; ++k) {
+    const double h = h_host[k];
+    const double lognorm = std::log((double)(n - 1)) + 0.5 * d * std::log(2.0 * pi * h * h);
+    cv[k] = o[2 * k] / n - lognorm;
+    dcv_dlogh[k] = o[2 * k + 1] / n - d;
+  }
+  return DFGT_OK;
+}
+
 dfgt_status dfgt_autotune(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d, const double* h_host,
                           int nh, double eps, int trials, dfgt_opts* best, double* best_ms) {
   if (!ctx) return DFGT_EINVAL;

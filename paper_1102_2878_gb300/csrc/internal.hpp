@@ -93,6 +93,7 @@ struct dfgt_ctx {
   DevBuf io_q, io_r, io_g;  // dfgt_kde_host staging
   DevBuf bf_partials;       // brute-force slice partials
   DevBuf cv_buf;            // cross-validation normalisers, partials and scores
+  DevBuf grad_buf;          // exact CV gradient sums (S, A, P, Y, partials)
   DevBuf bscratch;          // tree-build per-point scratch
   DevBuf bnodes;            // tree-build per-node scratch (left counts, prefixes, split ranks)
   std::shared_ptr<TreePool> tpool;
@@ -163,6 +164,12 @@ cudaError_t launch_bruteforce(const float* q, int nq, const float* r, int nr, in
 // part holds nh * nblk * 4 doubles, out nh * 4 (CV_LK, bound, CV_LS, bound).
 cudaError_t launch_cv_scores(const double* G, int n, int nh, const double* norm, double eps, double* part,
                              int nblk, double* out, cudaStream_t s, long long* launches);
+
+// cvgrad.cu: CV_LK, dCV/dlog h and dCV/dx at one bandwidth from exact sums.
+// S, A: n doubles; P, Y: n*d doubles; part: 2*ceil(n/256) doubles; out[2] =
+// {sum_i log S_i, sum_i A_i/(h^2 S_i)}; dx ([n][d], nullable) the point gradients.
+cudaError_t launch_cv_grad(const float* X, int n, int d, double h, double* S, double* P, double* A, double* Y,
+                           double* part, double* out, double* dx, cudaStream_t s, long long* launches);
 
 // tree.cu: build the tree (points, nodes, raw moments) on ctx's stream.
 dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n, int d,
