@@ -613,40 +613,153 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
   }
 }
 
-// D >= 6: the same chunked walk with runtime dimension and scalar math.
-__global__ void __launch_bounds__(kT) k_base_g(TreeView Q, TreeView R, const int* __restrict__ rsorted,
-                                               const int* __restrict__ ksorted, int n,
-                                               const double* __restrict__ hv,
-                                               double* __restrict__ gacc) {
+// D >= 6: exact sums in the direct form over the same sorted entries and
+// runs as k_base, with the dimension padded to DM = 8, 16 or 32 (the
+// tree's rows are zero-padded, so the extra coordinates add nothing).  A
+// run's references are staged in shared memory a tile at a time, negated,
+// as interleaved pairs (r_j, r_j+1 coordinate by coordinate, each pair slot
+// padded by 16 bytes so that lane groups reading different pairs do not
+// collide on banks); up to 128 of the run's queries are kept in flight,
+// 32 per query block, a lane holding one query of a block and, for blocks
+// of fewer than 32 queries, sharing the references with the other lanes of
+// that query.  Per two interactions: DM packed subtractions and FMAs, one
+// packed multiply, two ex2; blocks of 8 steps summed in float32 and added
+// with Kahan compensation (so the rounding is that of the D <= 5 direct form,
+// at most (D+3) u x per term).
+constexpr int kHdQBlocks = 4;  // query blocks of 32 in flight per pass
+
+template <int DM>
+struct HdShape {
+  static constexpr int TP = DM == 8 ? 64 : DM == 16 ? 32 : 16;   // reference pairs per tile
+  static constexpr int PS = 2 * DM + 4;                          // floats per pair slot
+};
+
+template <int DM>
+__global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const int* __restrict__ rsorted,
+                                                const int* __restrict__ ksorted, int n,
+                                                const float* __restrict__ c2v, double* __restrict__ gacc) {
+  constexpr int TP = HdShape<DM>::TP, PS = HdShape<DM>::PS;
+  __shared__ __align__(16) float sT[kWarpsPerBlock][TP * PS];
+  __shared__ int sOff[kWarpsPerBlock][kEntryChunk + 1], sRb[kWarpsPerBlock][kEntryChunk];
+  const unsigned FULL = 0xffffffffu;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kBaseChunk;
+  const long i0 = ((long)blockIdx.x * kWarpsPerBlock + wib) * kEntryChunk;
   if (i0 >= n) return;
-  const int m = (int)min((long)kBaseChunk, n - i0);
-  const int d = Q.d;
-  for (int u = 0; u < m; ++u) {
-    const int key = ksorted[i0 + u], r = rsorted[i0 + u] & kNodeMask;
-    const int hidx = key / Q.nn, q = key % Q.nn;
-    const double h = hv[hidx];
-    const float c2 = (float)(-kLog2e / (2.0 * h * h));
-    const int qb = Q.beg[q], qn = Q.cnt[q], rb = R.beg[r], rn = R.cnt[r];
-    for (int qi = lane; qi < qn; qi += 32) {
-      float qv[kMaxD];
+  const int m = (int)min((long)kEntryChunk, n - i0);
+  const int dpr = R.dp, dpq = Q.dp;
+  int key = -1 - lane, rb = 0, rn = 0, qbeg = 0, qcnt = 0;
+  if (lane < m) {
+    key = ksorted[i0 + lane];
+    const int r = rsorted[i0 + lane] & kNodeMask;
+    const int q = key % Q.nn;
+    rb = R.beg[r];
+    rn = R.cnt[r];
+    qbeg = Q.beg[q];
+    qcnt = Q.cnt[q];
+  }
+  const int keyp = __shfl_up_sync(FULL, key, 1);
+  const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
+  float* T = sT[wib];
+  int t = 0;
+  while (t < m) {
+    const unsigned later = starts & ~((2u << t) - 1u);
+    const int e = later ? __ffs(later) - 1 : m;
+    // the run's reference table
+    const int in_run = (lane >= t && lane < e) ? rn : 0;
+    int incl = in_run;
 #pragma unroll
-      for (int k = 0; k < kMaxD; ++k) qv[k] = k < d ? Q.pts[(size_t)(qb + qi) * Q.dp + k] : 0.f;
-      float part = 0.f;
-      for (int j = 0; j < rn; ++j) {
-        float d2 = 0.f;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const int tot = __shfl_sync(FULL, incl, 31);
+    if (lane >= t && lane < e) {
+      sOff[wib][lane - t] = incl - in_run;
+      sRb[wib][lane - t] = rb;
+    }
+    if (lane == 0) sOff[wib][e - t] = tot;
+    const int key_t = __shfl_sync(FULL, key, t);
+    const int hidx = key_t / Q.nn;
+    const int qb = __shfl_sync(FULL, qbeg, t), qn = __shfl_sync(FULL, qcnt, t);
+    const float c2 = c2v[hidx];
+    const float2 c2p = make_float2(c2, c2);
+    __syncwarp();
+    for (int qs = 0; qs < qn; qs += 32 * kHdQBlocks) {
+      const int nblk = min(kHdQBlocks, (qn - qs + 31) / 32);
+      float S[kHdQBlocks], Cc[kHdQBlocks];
 #pragma unroll
-        for (int k = 0; k < kMaxD; ++k) {
-          if (k < d) {
-            const float tt = qv[k] - R.pts[(size_t)(rb + j) * R.dp + k];
-            d2 = fmaf(tt, tt, d2);
+      for (int b = 0; b < kHdQBlocks; ++b) S[b] = Cc[b] = 0.f;
+      for (int j0 = 0; j0 < tot; j0 += 2 * TP) {
+        const int tn = min(2 * TP, tot - j0);
+        const int np = (tn + 1) >> 1;
+        // stage references j0 .. j0+tn-1 as interleaved pairs; a missing
+        // partner gets far coordinates (its kernel value is 0)
+        {
+          int u = 0;
+          for (int jj = lane; jj < 2 * np; jj += 32) {
+            const int J = j0 + jj;
+            float* slot = T + (jj >> 1) * PS + (jj & 1);
+            if (J < tot) {
+              while (sOff[wib][u + 1] <= J) ++u;
+              const float* src = R.pts + (size_t)(sRb[wib][u] + J - sOff[wib][u]) * dpr;
+#pragma unroll
+              for (int k = 0; k < DM; ++k) slot[2 * k] = k < dpr ? -src[k] : 0.f;
+            } else {
+#pragma unroll
+              for (int k = 0; k < DM; ++k) slot[2 * k] = -1.0e18f;
+            }
           }
         }
-        part += ex2_approx(d2 * c2);
+        __syncwarp();
+        for (int b = 0; b < nblk; ++b) {
+          const int qbk = min(32, qn - qs - 32 * b);
+          const int QL = qbk > 16 ? 32 : qbk > 8 ? 16 : qbk > 4 ? 8 : qbk > 2 ? 4 : qbk > 1 ? 2 : 1;
+          const int NG = 32 / QL, ql = lane & (QL - 1), grp = lane / QL;
+          const bool vq = ql < qbk;
+          const int qi = qs + 32 * b + ql;
+          float2 qq[DM];
+#pragma unroll
+          for (int k = 0; k < DM; ++k) {
+            const float v = (vq && k < dpq) ? Q.pts[(size_t)(qb + qi) * dpq + k] : 0.f;
+            qq[k] = make_float2(v, v);
+          }
+          float2 blk = make_float2(0.f, 0.f);
+          int steps = 0;
+          for (int p = grp; p < np; p += NG) {
+            const float4* rp = reinterpret_cast<const float4*>(T + p * PS);
+            float2 d2 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < DM; k += 2) {
+              const float4 r4 = rp[k >> 1];  // -(r_j,k, r_j+1,k, r_j,k+1, r_j+1,k+1)
+              const float2 da = __fadd2_rn(qq[k], make_float2(r4.x, r4.y));
+              const float2 db = __fadd2_rn(qq[k + 1], make_float2(r4.z, r4.w));
+              d2 = __ffma2_rn(da, da, d2);
+              d2 = __ffma2_rn(db, db, d2);
+            }
+            const float2 x = __fmul2_rn(d2, c2p);
+            blk = __fadd2_rn(blk, make_float2(ex2_approx(x.x), ex2_approx(x.y)));
+            if (++steps == 8) {
+              steps = 0;
+              kahan_add(S[b], Cc[b], blk.x + blk.y);
+              blk = make_float2(0.f, 0.f);
+            }
+          }
+          kahan_add(S[b], Cc[b], blk.x + blk.y);
+        }
+        __syncwarp();
       }
-      atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qi], (double)part);
+      // the lane groups of each query block hold parts of its sums
+      for (int b = 0; b < nblk; ++b) {
+        const int qbk = min(32, qn - qs - 32 * b);
+        const int QL = qbk > 16 ? 32 : qbk > 8 ? 16 : qbk > 4 ? 8 : qbk > 2 ? 4 : qbk > 1 ? 2 : 1;
+        float v = S[b] - Cc[b];
+        for (int o = QL; o < 32; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
+        const int ql = lane & (QL - 1);
+        if (lane < QL && ql < qbk) atomicAdd(&gacc[(size_t)hidx * Q.n + qb + qs + 32 * b + ql], (double)v);
+      }
     }
+    __syncwarp();
+    t = e;
   }
 }
 
@@ -1378,9 +1491,14 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
     DISPATCH_D(Q.d, k_base<DD><<<g, kBaseWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up,
                                                               b.gacc, b.base_exp));
   } else {
-    const long warps = (n + kBaseChunk - 1) / kBaseChunk;
+    const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    k_base_g<<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.h, b.gacc);
+    if (Q.dp <= 8)
+      k_base_hd<8><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc);
+    else if (Q.dp <= 16)
+      k_base_hd<16><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc);
+    else
+      k_base_hd<32><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc);
   }
   ++*launches;
   return cudaGetLastError();
