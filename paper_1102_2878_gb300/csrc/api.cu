@@ -38,10 +38,16 @@ bool bad_h(const double* h, int nh) {
 
 // DFGTPost: local expansions shifted to the leaves, read out and added to
 // the exact and far-field parts, into G_dev (one fused kernel).
+// The stream waits until the tree's moment pass has run.
+cudaError_t wait_ready(cudaStream_t s, const dfgt_tree* t) {
+  return t->ready ? cudaStreamWaitEvent(s, t->ready, 0) : cudaSuccess;
+}
+
 dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, double* G_dev,
                  dfgt_stats* st) {
   cudaStream_t s = ctx->stream;
   const TreeView Q = qt->view();
+  CK(wait_ready(s, qt));
   CK(launch_post(Q, qt->leaves, qt->nleaves, b, G_dev, s));
   ++ctx->launches;
   CK(cudaMemcpyAsync(ctx->h_counters, ctx->counters.p, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
@@ -162,6 +168,10 @@ dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const
   if (ls.timed) {  // the previous launch of this list has finished reading by now
     CK(cudaEventSynchronize(ls.e1));
     ls.collect();
+  }
+  if (which != 0) {  // far field, local moments, far to local: the trees' moments and float node data
+    CK(wait_ready(s, qt));
+    CK(wait_ready(s, rt));
   }
   CK(cudaEventRecord(ls.e0, s));
   if (which == 0) {
@@ -342,6 +352,8 @@ dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream) {
     ctx->tpool->stream = ctx->stream;
   }
   for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->moments_done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     dfgt_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? DFGT_ENOMEM : DFGT_ECUDA;
@@ -364,6 +376,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->side) cudaStreamSynchronize(ctx->side);
   DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1],
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
@@ -380,6 +393,8 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   for (int i = 0; i < 16; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->moments_done) cudaEventDestroy(ctx->moments_done);
   delete ctx;
 }
 
@@ -625,6 +640,7 @@ dfgt_status dfgt_tree_export(const dfgt_tree* t, int32_t* perm, float* lo, float
                              int32_t* begin, int32_t* count, int32_t* left, double* moments) {
   if (!t) return DFGT_EINVAL;
   if (cudaSetDevice(t->device) != cudaSuccess) return DFGT_ECUDA;
+  if (t->ready && cudaEventSynchronize(t->ready) != cudaSuccess) return DFGT_ECUDA;
   struct Item { void* dst; const void* src; size_t bytes; } items[] = {
       {perm, t->perm, (size_t)t->n * sizeof(int)},
       {lo, t->lo, (size_t)t->nn * t->d * sizeof(float)},
@@ -667,6 +683,8 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   ctx->err.clear();
   cudaStream_t s = ctx->stream;
   TravBuffers b;
+  CK(wait_ready(s, qt));
+  CK(wait_ready(s, rt));
   dfgt_status rc = setup_state(ctx, qt, rt, &h, 1, 0.5, &b);
   if (rc != DFGT_OK) return rc;
   const size_t need = std::max<size_t>({prune.size(), base.size(), far.size(), loc.size(), f2l.size(), 1});

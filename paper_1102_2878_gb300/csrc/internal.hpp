@@ -76,6 +76,8 @@ struct dfgt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t side = nullptr;          // the moment pass of a build runs here
+  cudaEvent_t moments_done = nullptr;   // the last moment pass issued on `side`
   std::string err;
   long long launches = 0;
   // cached workspace
@@ -108,6 +110,7 @@ struct dfgt_ctx {
 
 struct dfgt_tree {
   int device = 0;
+  cudaEvent_t ready = nullptr;  // moments and float node data written (recorded on the building context's side stream)
   int64_t n = 0;
   int d = 0, dp = 0, leaf = 32, pm = 1, P = 1, p_limit = 1;
   long long base_block = 0;

@@ -559,9 +559,6 @@ constexpr int kMW = kMT / 32;
 
 struct MomArgs {
   const float *pbuf0, *pbuf1;  // the level build's point buffers (ctl[1] holds the final one)
-  const int *perm0, *perm1;
-  float* pts;                  // the tree's points and permutation
-  int* perm;
   const float *lo, *hi;
   const int *beg, *cnt, *left, *parent, *leaves;
   double* mom;                 // [nodes][P] raw moments
@@ -758,8 +755,8 @@ __device__ void node_float_data(const MomArgs& M, int j) {
 }
 
 // Every moment of the tree, after the level build has finished (it returns
-// at once otherwise): the final points are copied into the tree, each warp
-// sums the moments of its leaves, and the warp that finishes the second
+// at once otherwise): each warp sums the moments of its leaves, and the
+// warp that finishes the second
 // child of a node translates both children's moments to it (Lemma 3.5) and
 // goes on up, so no warp waits for another.  Each node's float data follows
 // its moments.  D = 0 stands for D >= 6, where p_max = 1 and the only
@@ -775,10 +772,6 @@ __global__ void __launch_bounds__(kMT) k_moments(MomArgs M) {
   const int gw = blockIdx.x * kMW + wib, nw = G * kMW;
   const int cur = __ldcg(M.ctl + 1), nleaves = __ldcg(M.ctl + 3);
   const float* pin = cur ? M.pbuf1 : M.pbuf0;
-  const int* permin = cur ? M.perm1 : M.perm0;
-  for (size_t i = (size_t)blockIdx.x * kMT + threadIdx.x; i < (size_t)M.n * M.dp; i += (size_t)G * kMT)
-    M.pts[i] = pin[i];
-  for (int i = blockIdx.x * kMT + threadIdx.x; i < M.n; i += G * kMT) M.perm[i] = permin[i];
   for (int li = gw; li < nleaves; li += nw) {
     int w = M.leaves[li];
     if constexpr (D > 0) {
@@ -898,11 +891,20 @@ cudaError_t launch_moments(dfgt_ctx* ctx, const MomArgs& M, cudaStream_t s) {
 
 void free_tree(dfgt_tree* t) {
   if (t->arena) {
-    // every call on the tree has completed (calls return after their work),
-    // so the arena can go back to the pool in any stream's order
+    // every call on the tree has completed (calls return after their work)
+    // but the build's moment pass may still run: the arena goes back to the
+    // pool after it, in the pool stream's order
     std::lock_guard<std::mutex> g(t->tpool->m);
+    if (t->ready) {
+      if (t->tpool->stream)
+        cudaStreamWaitEvent(t->tpool->stream, t->ready, 0);
+      else
+        cudaEventSynchronize(t->ready);
+    }
     cudaFreeAsync(t->arena, t->tpool->stream);
   }
+  if (t->ready) cudaEventDestroy(t->ready);
+  t->ready = nullptr;
   t->arena = nullptr;
   t->tpool.reset();
   t->chi = t->clo = t->whalf = t->mnorm = nullptr;
@@ -953,6 +955,9 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
 
   const size_t np = (size_t)n;
   Carver cv;
+  // the previous build's moment pass may still read the build scratch
+  TRY(cudaStreamWaitEvent(s, ctx->moments_done, 0));
+  TRY(cudaEventCreateWithFlags(&t->ready, cudaEventDisableTiming));
   for (int pass = 0; pass < 2; ++pass) {
     cv.off = 0;
     pbuf[0] = cv.take<float>(np * t->dp);
@@ -1016,22 +1021,26 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       void* args[] = {&A};
       TRY(cudaLaunchCooperativeKernel((const void*)k_build_levels, dim3(ctx->build_grid), dim3(kBT), args, 0, s));
       ++*L;
+      // the moment pass runs on the side stream after the level build; the
+      // next call on the context overlaps it (readers wait on t->ready)
+      TRY(cudaEventRecord(ctx->ev[4], s));
+      TRY(cudaStreamWaitEvent(ctx->side, ctx->ev[4], 0));
       MomArgs M;
-      M.pbuf0 = pbuf[0]; M.pbuf1 = pbuf[1]; M.perm0 = perm2[0]; M.perm1 = perm2[1];
-      M.pts = t->pts; M.perm = t->perm;
+      M.pbuf0 = pbuf[0]; M.pbuf1 = pbuf[1];
       M.lo = t->lo; M.hi = t->hi; M.beg = t->beg; M.cnt = t->cnt; M.left = t->left; M.leaves = t->leaves;
       M.mom = t->mom; M.chi = t->chi; M.clo = t->clo; M.whalf = t->whalf; M.mnorm = t->mnorm;
       M.parent = t->parent; M.arrive = ns.arrive; M.ctl = ctl;
       M.n = n; M.d = d; M.dp = t->dp; M.pm = t->pm; M.P = t->P;
       switch (d) {
-        case 1: TRY(launch_moments<1>(ctx, M, s)); break;
-        case 2: TRY(launch_moments<2>(ctx, M, s)); break;
-        case 3: TRY(launch_moments<3>(ctx, M, s)); break;
-        case 4: TRY(launch_moments<4>(ctx, M, s)); break;
-        case 5: TRY(launch_moments<5>(ctx, M, s)); break;
-        default: TRY(launch_moments<0>(ctx, M, s)); break;
+        case 1: TRY(launch_moments<1>(ctx, M, ctx->side)); break;
+        case 2: TRY(launch_moments<2>(ctx, M, ctx->side)); break;
+        case 3: TRY(launch_moments<3>(ctx, M, ctx->side)); break;
+        case 4: TRY(launch_moments<4>(ctx, M, ctx->side)); break;
+        case 5: TRY(launch_moments<5>(ctx, M, ctx->side)); break;
+        default: TRY(launch_moments<0>(ctx, M, ctx->side)); break;
       }
       ++*L;
+      TRY(cudaEventRecord(ctx->moments_done, ctx->side));
       TRY(cudaMemcpyAsync(h_ctl, ctl, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaMemcpyAsync(lvh.data(), lv, lvh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaStreamSynchronize(s));
@@ -1065,6 +1074,8 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
         goto fail;
       }
       // grow: a new arena and node scratch, the finished levels copied over
+      // (once the moment pass, which found the tree unfinished, is done)
+      TRY(cudaStreamSynchronize(ctx->side));
       const size_t nc = std::max(need + need / 2, cap * 2);
       const size_t nl = (size_t)h_ctl[3];
       dfgt_tree old = *t;
@@ -1102,7 +1113,11 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       cap = nc;
       init_from = (int)keep;
     }
+    TRY(cudaEventRecord(t->ready, ctx->side));
     const int last = h_ctl[2];
+    const int cur = h_ctl[1];
+    TRY(copy_d2d(t->pts, pbuf[cur], np * t->dp * sizeof(float), s, cudaSuccess));
+    TRY(copy_d2d(t->perm, perm2[cur], np * sizeof(int), s, cudaSuccess));
     t->nleaves = h_ctl[3];
     t->lvl_off.assign(1, 0);
     for (int Lk = 0; Lk <= last; ++Lk) t->lvl_off.push_back(lvh[3 * Lk + 1]);
@@ -1118,6 +1133,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
 fail:
   if (rc != DFGT_OK) {
     cudaStreamSynchronize(s);
+    cudaStreamSynchronize(ctx->side);
     free_tree(t);
   }
   return rc;
