@@ -381,7 +381,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,
-                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes, &ctx->cv_buf};
+                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes, &ctx->cv_buf, &ctx->grad_buf};
   for (DevBuf* b : bufs) b->release();
   if (ctx->tpool) {
     // trees that outlive the context return their arenas in default-stream order
