@@ -38,6 +38,22 @@ bool bad_h(const double* h, int nh) {
 
 // DFGTPost: local expansions shifted to the leaves, read out and added to
 // the exact and far-field parts, into G_dev (one fused kernel).
+// Grow a buffer to `bytes`, keeping its first `keep` bytes.
+cudaError_t grow_keep(DevBuf& buf, size_t bytes, size_t keep, cudaStream_t s) {
+  if (bytes <= buf.bytes) return cudaSuccess;
+  DevBuf nb;
+  cudaError_t e = nb.ensure(bytes);
+  if (e == cudaSuccess && keep) e = cudaMemcpyAsync(nb.p, buf.p, keep, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    nb.release();
+    return e;
+  }
+  buf.release();
+  buf = nb;
+  return cudaSuccess;
+}
+
 // The stream waits until the tree's moment pass has run.
 cudaError_t wait_ready(cudaStream_t s, const dfgt_tree* t) {
   return t->ready ? cudaStreamWaitEvent(s, t->ready, 0) : cudaSuccess;
@@ -224,8 +240,19 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
   ++ctx->launches;
   int cur = 0, nF = nh, rounds = 0;
   long long visited = 0;
-  while (nF > 0) {
-    if (rounds >= max_rounds) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: traversal did not finish");
+  // Device-driven rounds: one cooperative launch runs rounds until the
+  // frontier empties or the next round might not fit the buffers; the host
+  // then drains full lists or grows the frontier and launches again.
+  CK(ctx->trav_ctl.ensure(64));
+  TravControl* dtc = ctx->trav_ctl.as<TravControl>();
+  unsigned* dbar = reinterpret_cast<unsigned*>(ctx->trav_ctl.as<char>() + 48);
+  {
+    const TravControl init{nh, 0, 0, -1, 0};
+    CK(cudaMemcpyAsync(dtc, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  }
+  TravControl htc{};
+  for (int launch = 0;; ++launch) {
+    if (launch > max_rounds + 8) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: traversal did not finish");
     if ((size_t)nF > kHardCap) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: frontier exceeds 2^28 node pairs");
     // a round appends at most one item per pair to each list
     for (int w = 0; w < 4; ++w) {
@@ -245,40 +272,49 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       rc = ensure_lists(ctx);
       if (rc != DFGT_OK) return rc;
     }
-    // the next frontier: at most four child pairs per pair
-    CK(ctx->frontier[cur ^ 1].ensure(4 * (size_t)nF * sizeof(Pair)));
-    ctx->cap_frontier = std::max(ctx->cap_frontier, 4 * (size_t)nF);
-    CK(ctx->kus.ensure((size_t)nF * sizeof(float)));
+    // both frontier buffers (and the per-pair bounds) hold at least 8 nF
+    // pairs, so the frontier can grow twofold before the next return
+    const size_t capf = std::min<size_t>(std::max(ctx->cap_frontier, 8 * (size_t)nF), INT32_MAX);
+    ctx->cap_frontier = capf;
+    CK(grow_keep(ctx->frontier[cur], capf * sizeof(Pair), (size_t)nF * sizeof(Pair), s));
+    CK(ctx->frontier[cur ^ 1].ensure(capf * sizeof(Pair)));
+    CK(ctx->kus.ensure(capf * sizeof(float)));
     b.ku = ctx->kus.as<float>();
+    CK(cudaMemsetAsync(dbar, 0, sizeof(unsigned), s));
     CK(cudaEventRecord(ctx->ev[6], s));
-    CK(launch_fold(b, qt->nn, s));
-    CK(launch_lb(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, s));
-    CK(cudaMemsetAsync(&dctr->n_next, 0, sizeof(int), s));
-    CK(launch_classify(Q, R, b, ctx->frontier[cur].as<Pair>(), nF, ctx->frontier[cur ^ 1].as<Pair>(),
-                       (int)std::min<size_t>(4 * (size_t)nF, INT32_MAX),
-                       ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(),
-                       ctx->list_f2l.as<Action>(), ctx->list_base.as<Pair>(), (int)ctx->cap_lists,
-                       dctr, s));
-    ctx->launches += 3;
+    CK(launch_traverse(Q, R, b, ctx->frontier[0].as<Pair>(), ctx->frontier[1].as<Pair>(), (int)capf,
+                       ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(), ctx->list_f2l.as<Action>(),
+                       ctx->list_base.as<Pair>(), (int)ctx->cap_lists, dctr, dtc, dbar, max_rounds,
+                       ctx->trav_grid, s));
+    ++ctx->launches;
     CK(cudaEventRecord(ctx->ev[7], s));
     CK(cudaMemcpyAsync(hc, dctr, sizeof(RoundCounters), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&htc, dtc, sizeof(htc), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     {
       float t = 0.f;
       cudaEventElapsedTime(&t, ctx->ev[6], ctx->ev[7]);
       ms_classify += t;
     }
-    if (hc->status & kStOverflow) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work list overflow");
-    visited += nF;
-    ++rounds;
+    if (hc->status & kStTimeout) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: a grid barrier wait timed out");
+    if ((hc->status & kStOverflow) || htc.stop == kTravOverflow)
+      return fail(ctx, DFGT_ECAPACITY, "dfgt_sum: work list overflow");
+    if (htc.stop < 0) return fail(ctx, DFGT_ECUDA, "dfgt_sum: traversal launch did not complete");
     for (int w = 0; w < 4; ++w) lists[w].collect();
     const int got[4] = {hc->n_base, hc->n_far, hc->n_loc, hc->n_f2l};
     for (int w = 0; w < 4; ++w) {
       lists[w].total += got[w] - lists[w].count;
       lists[w].count = got[w];
     }
-    nF = hc->n_next;
-    cur ^= 1;
+    nF = htc.nF;
+    cur = htc.cur;
+    rounds = htc.rounds;
+    visited = htc.visited;
+    if (htc.stop == kTravDone) break;
+    if (htc.stop == kTravRounds) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: traversal did not finish");
+    // kTravRoom: drain or grow at the top of the loop and go on
+    htc.stop = -1;
+    CK(cudaMemcpyAsync(&dtc->stop, &htc.stop, sizeof(int), cudaMemcpyHostToDevice, s));
   }
   CK(cudaEventRecord(ctx->ev[1], s));
   for (int w = 0; w < 4; ++w) {

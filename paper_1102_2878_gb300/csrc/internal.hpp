@@ -101,6 +101,8 @@ struct dfgt_ctx {
   std::shared_ptr<TreePool> tpool;
   int sms = 0;                // SMs of the device (0: not yet queried)
   int build_grid = 0;         // blocks of the cooperative level build (0: not yet chosen)
+  int trav_grid[6] = {};      // blocks of the cooperative traversal per dimension template
+  DevBuf trav_ctl;            // TravControl and the traversal's grid-barrier counter
   int mom_grid[6] = {};       // blocks of the cooperative moment pass per dimension (0: D >= 6)
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
@@ -208,12 +210,19 @@ struct TravBuffers {
   int sms;               // SMs of the device (sizes the balanced launches)
 };
 
-cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s);
-cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
-                      int nF, cudaStream_t s);
-cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Pair* F, int nF, Pair* next, int cap_next, Action* far, Action* loc,
-                            Action* f2l, Pair* base, int cap_lists, RoundCounters* counters,
+// State of the device-driven traversal between launches (device memory).
+struct TravControl {
+  int nF;              // pairs in the current frontier
+  int cur;             // which frontier buffer holds them
+  int rounds;          // rounds done
+  int stop;            // why the last launch returned (kTrav*; -1 while running)
+  long long visited;   // pairs classified so far
+};
+enum : int { kTravDone = 0, kTravRoom = 1, kTravRounds = 2, kTravOverflow = 3 };
+
+cudaError_t launch_traverse(const TreeView& Q, const TreeView& R, const TravBuffers& b, Pair* F0, Pair* F1,
+                            int cap_front, Action* far, Action* loc, Action* f2l, Pair* base, int cap_lists,
+                            RoundCounters* ctr, TravControl* tc, unsigned* bar, int max_rounds, int* grid,
                             cudaStream_t s);
 cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s);
 

@@ -1,5 +1,6 @@
 // traverse.cu -- level-synchronous dual-tree traversal (the DFGT recursion of
-// Section 3.6, one round per kernel sweep over a frontier of node pairs).
+// Section 3.6, one round per sweep over a frontier of node pairs; all rounds
+// run in one cooperative launch, phases separated by grid barriers).
 //
 // Every round classifies all frontier pairs (Q, R, h) at once:
 //   * the distance-bound prune (the finite-difference approximation of the
@@ -96,13 +97,14 @@ __device__ __forceinline__ void warp_add_u64_block(unsigned long long* counter, 
   }
 }
 
-__global__ void k_fold(u64* __restrict__ decided, u64* __restrict__ incr, u64* __restrict__ lbsum,
-                       int total) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  decided[i] += incr[i];
-  incr[i] = 0;
-  lbsum[i] = 0;
+// Round start: fold the previous round's decided bounds into `decided` and
+// clear the per-round sums.
+__device__ __forceinline__ void fold_phase(const TravBuffers& b, int total) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    b.decided[i] = __ldcg(b.decided + i) + __ldcg(b.incr + i);
+    b.incr[i] = 0;
+    b.lbsum[i] = 0;
+  }
 }
 
 __global__ void k_init_frontier(Pair* F, int nh) {
@@ -110,40 +112,44 @@ __global__ void k_init_frontier(Pair* F, int nh) {
   if (i < nh) F[i] = Pair{0, 0, i, 0};
 }
 
+__device__ __forceinline__ Pair load_pair(const Pair* F, int i) {
+  const int4 v = __ldcg(reinterpret_cast<const int4*>(F) + i);
+  return Pair{v.x, v.y, v.z, v.w};
+}
+
 // Pending lower bounds: inherit the decided bound of a just-split parent,
-// then add delta^l of every pending pair of the node.
+// then add delta^l of every pending pair of the node.  Pair i is handled by
+// the same thread as in the classification that follows.
 template <int D>
-__global__ void __launch_bounds__(kT) k_lb(TreeView Q, TreeView R, TravBuffers b,
-                                           const Pair* __restrict__ F, int nF) {
-  const int i = blockIdx.x * kT + threadIdx.x;
-  if (i >= nF) return;
-  const Pair pr = F[i];
-  const size_t hq = (size_t)pr.h * Q.nn + pr.q;
-  if (pr.flags & kFlagSplitQ) {
-    const size_t hp = (size_t)pr.h * Q.nn + Q.parent[pr.q];
-    b.inherited[hq] = b.inherited[hp] + b.decided[hp];  // same value from every pair of q
+__device__ __forceinline__ void lb_phase(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                                         const Pair* __restrict__ F, int nF) {
+  for (int i = blockIdx.x * kT + threadIdx.x; i < nF; i += gridDim.x * kT) {
+    const Pair pr = load_pair(F, i);
+    const size_t hq = (size_t)pr.h * Q.nn + pr.q;
+    if (pr.flags & kFlagSplitQ) {
+      const size_t hp = (size_t)pr.h * Q.nn + Q.parent[pr.q];
+      b.inherited[hq] = __ldcg(b.inherited + hp) + __ldcg(b.decided + hp);  // same value from every pair of q
+    }
+    float dl2, du2, sq, sr;
+    box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
+    const float Ku = kernel_lower(du2, b.inv2h2_up[pr.h]);
+    b.ku[i] = Ku;  // reused by the classification of the same pair
+    const u64 f = to_fix_f((float)R.cnt[pr.r], Ku, b.fix_scale_dn);
+    if (f) atomicAdd(&b.lbsum[hq], f);
   }
-  float dl2, du2, sq, sr;
-  box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
-  const float Ku = kernel_lower(du2, b.inv2h2_up[pr.h]);
-  b.ku[i] = Ku;  // reused by the classification of the same pair
-  const u64 f = to_fix_f((float)R.cnt[pr.r], Ku, b.fix_scale_dn);
-  if (f) atomicAdd(&b.lbsum[hq], f);
 }
 
 template <int D>
-__global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuffers b,
-                                                 const Pair* __restrict__ F, int nF,
-                                                 Pair* __restrict__ next, int cap_next,
-                                                 Action* __restrict__ far, Action* __restrict__ loc,
-                                                 Action* __restrict__ f2l, Pair* __restrict__ base,
-                                                 int cap_lists, RoundCounters* ctr) {
+__device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView& R, const TravBuffers& b,
+                                               const Pair* __restrict__ F, int nF,
+                                               Pair* __restrict__ next, int cap_next,
+                                               Action* __restrict__ far, Action* __restrict__ loc,
+                                               Action* __restrict__ f2l, Pair* __restrict__ base,
+                                               int cap_lists, RoundCounters* ctr, u64* sWarp, int* sBase) {
   const int d = D > 0 ? D : Q.d;
   const int P = Q.P;
   const int stride = gridDim.x * kT;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __shared__ u64 sWarp[kT / 32];
-  __shared__ int sBase[5];
   unsigned long long my_prune = 0, my_inter = 0;
   for (int i0 = blockIdx.x * kT; i0 < nF; i0 += stride) {
     const int i = i0 + threadIdx.x;
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
     Pair pr{0, 0, 0, 0};
     unsigned long long inter = 0;
     if (i < nF) {
-      pr = F[i];
+      pr = load_pair(F, i);
       const size_t hq = (size_t)pr.h * Q.nn + pr.q;
       const int cQ = Q.cnt[pr.q], cR = R.cnt[pr.r];
       const float nQ = (float)cQ, nR = (float)cR;
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
       box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
       const float Kl = kernel_upper(dl2, b.inv2h2_dn[pr.h]);
       const float Ku = b.ku[i];
-      const u64 lbf = b.inherited[hq] + b.decided[hq] + b.lbsum[hq];
+      const u64 lbf = __ldcg(b.inherited + hq) + __ldcg(b.decided + hq) + __ldcg(b.lbsum + hq);
       // tau = eps |R| G^l(Q) / |R_total| (CanSummarize), rounded down
       const float tau = __fmul_rd(__fmul_rd(b.tau_scale_dn, nR), u64_to_f_rd(lbf));
       // prune: the kernel over the pair lies in [Ku, Kl]; the midpoint is off by
@@ -291,54 +297,122 @@ __global__ void __launch_bounds__(kT) k_classify(TreeView Q, TreeView R, TravBuf
   warp_add_u64_block(&ctr->base_inter, my_inter, sWarp);
 }
 
+// Every round of the traversal in one cooperative launch: fold, lower
+// bounds, classification, each phase over the whole frontier and closed by
+// a bounded grid barrier; the frontier swaps on the device.  The launch
+// returns when the frontier is empty, when the next round might not fit
+// the frontier buffers or the action lists (the host then drains or grows
+// them and launches again), after max_rounds rounds, or on an overflow.
+struct TravArgs {
+  TreeView Q, R;
+  TravBuffers b;
+  Pair* F[2];
+  int cap_front;                 // pairs each frontier buffer (and b.ku) holds
+  Action *far, *loc, *f2l;
+  Pair* base;
+  int cap_lists;
+  RoundCounters* ctr;
+  TravControl* tc;
+  unsigned* bar;
+  int max_rounds;
+};
+
 template <int D>
-cudaError_t classify_d(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
-                       int nF, Pair* next, int cap_next, Action* far, Action* loc, Action* f2l,
-                       Pair* base, int cap_lists, RoundCounters* ctr, cudaStream_t s) {
-  int grid = (nF + kT - 1) / kT;
-  if (grid > 152 * 16) grid = 152 * 16;
-  k_classify<D><<<grid, kT, 0, s>>>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr);
-  return cudaGetLastError();
+__global__ void __launch_bounds__(kT) k_traverse(TravArgs A) {
+  __shared__ u64 sWarp[kT / 32];
+  __shared__ int sBase[5];
+  const TravBuffers& b = A.b;
+  RoundCounters* ctr = A.ctr;
+  unsigned target = 0;
+  int nF = __ldcg(&A.tc->nF), cur = __ldcg(&A.tc->cur), rounds = __ldcg(&A.tc->rounds);
+  long long visited = __ldcg(&A.tc->visited);
+  const int total = b.nh * A.Q.nn;
+  int stop = 0;
+  for (;;) {
+    if (nF == 0) { stop = kTravDone; break; }
+    if (rounds >= A.max_rounds) { stop = kTravRounds; break; }
+    // room for this round: 4 children per pair, one item per pair per list
+    const long long room = (long long)A.cap_lists - nF;
+    if (4LL * nF > A.cap_front || __ldcg(&ctr->n_far) > room || __ldcg(&ctr->n_loc) > room ||
+        __ldcg(&ctr->n_f2l) > room || __ldcg(&ctr->n_base) > room) {
+      stop = kTravRoom;
+      break;
+    }
+    fold_phase(b, total);
+    if (!grid_barrier(A.bar, &ctr->status, target)) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctr->n_next, 0);
+    lb_phase<D>(A.Q, A.R, b, A.F[cur], nF);
+    if (!grid_barrier(A.bar, &ctr->status, target)) return;
+    classify_phase<D>(A.Q, A.R, b, A.F[cur], nF, A.F[cur ^ 1], 4 * nF, A.far, A.loc, A.f2l, A.base,
+                      A.cap_lists, ctr, sWarp, sBase);
+    if (!grid_barrier(A.bar, &ctr->status, target)) return;
+    visited += nF;
+    ++rounds;
+    cur ^= 1;
+    nF = __ldcg(&ctr->n_next);
+    if (__ldcg(&ctr->status) & kStOverflow) { stop = kTravOverflow; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    A.tc->nF = nF;
+    A.tc->cur = cur;
+    A.tc->rounds = rounds;
+    A.tc->visited = visited;
+    A.tc->stop = stop;
+  }
+}
+
+template <int D>
+cudaError_t traverse_d(const TravArgs& A, int* grid, cudaStream_t s) {
+  if (*grid == 0) {
+    int sms = 0, occ = 0, coop = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_traverse<D>, kT, 0);
+    if (e != cudaSuccess) return e;
+    if (!coop || occ < 1) return cudaErrorNotSupported;
+    // two blocks per SM: more (6 per SM measured) only makes the barriers dearer
+    *grid = sms * (occ < 2 ? occ : 2);
+  }
+  TravArgs a = A;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)k_traverse<D>, dim3(*grid), dim3(kT), args, 0, s);
 }
 
 }  // namespace
-
-cudaError_t launch_fold(const TravBuffers& b, int nnQ, cudaStream_t s) {
-  const int total = b.nh * nnQ;
-  k_fold<<<(total + kT - 1) / kT, kT, 0, s>>>(b.decided, b.incr, b.lbsum, total);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s) {
   k_init_frontier<<<(nh + kT - 1) / kT, kT, 0, s>>>(F, nh);
   return cudaGetLastError();
 }
 
-cudaError_t launch_lb(const TreeView& Q, const TreeView& R, const TravBuffers& b, const Pair* F,
-                      int nF, cudaStream_t s) {
-  const int grid = (nF + kT - 1) / kT;
-  switch (Q.d) {
-    case 1: k_lb<1><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
-    case 2: k_lb<2><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
-    case 3: k_lb<3><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
-    case 4: k_lb<4><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
-    case 5: k_lb<5><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
-    default: k_lb<0><<<grid, kT, 0, s>>>(Q, R, b, F, nF); break;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_classify(const TreeView& Q, const TreeView& R, const TravBuffers& b,
-                            const Pair* F, int nF, Pair* next, int cap_next, Action* far, Action* loc,
-                            Action* f2l, Pair* base, int cap_lists, RoundCounters* ctr,
+cudaError_t launch_traverse(const TreeView& Q, const TreeView& R, const TravBuffers& b, Pair* F0, Pair* F1,
+                            int cap_front, Action* far, Action* loc, Action* f2l, Pair* base, int cap_lists,
+                            RoundCounters* ctr, TravControl* tc, unsigned* bar, int max_rounds, int* grid,
                             cudaStream_t s) {
-  switch (Q.d) {
-    case 1: return classify_d<1>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 2: return classify_d<2>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 3: return classify_d<3>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 4: return classify_d<4>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    case 5: return classify_d<5>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
-    default: return classify_d<0>(Q, R, b, F, nF, next, cap_next, far, loc, f2l, base, cap_lists, ctr, s);
+  TravArgs A;
+  A.Q = Q;
+  A.R = R;
+  A.b = b;
+  A.F[0] = F0;
+  A.F[1] = F1;
+  A.cap_front = cap_front;
+  A.far = far;
+  A.loc = loc;
+  A.f2l = f2l;
+  A.base = base;
+  A.cap_lists = cap_lists;
+  A.ctr = ctr;
+  A.tc = tc;
+  A.bar = bar;
+  A.max_rounds = max_rounds;
+  switch (Q.d) {  // grid[d]: the cooperative grid of each dimension's kernel
+    case 1: return traverse_d<1>(A, grid + 1, s);
+    case 2: return traverse_d<2>(A, grid + 2, s);
+    case 3: return traverse_d<3>(A, grid + 3, s);
+    case 4: return traverse_d<4>(A, grid + 4, s);
+    case 5: return traverse_d<5>(A, grid + 5, s);
+    default: return traverse_d<0>(A, grid, s);
   }
 }
 

@@ -67,41 +67,6 @@ __global__ void k_init_root(int n, int* beg, int* cnt, int* left, int* parent, i
 constexpr int kBT = 1024;       // threads per block of the level build
 constexpr int kKB = 2;          // points per thread per pass
 constexpr int kMaxGrid = 1024;  // blocks of the level build at most
-constexpr long long kSpinLimit = 1LL << 25;  // barrier polls before giving up (~1 s)
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid barrier of a cooperative launch on a monotone arrival counter:
-// every block passes the same sequence of barriers, so the k-th barrier
-// opens when the counter reaches k * gridDim.x (`target`, kept by each
-// block).  The wait is bounded: a block that polls kSpinLimit times sets
-// kStTimeout and leaves; every block returns false from then on, as it does
-// once a non-finite coordinate has been seen.
-__device__ bool grid_barrier(unsigned* bar, int* status, unsigned& target) {
-  __shared__ int s_ok;
-  __syncthreads();
-  target += gridDim.x;
-  if (threadIdx.x == 0) {
-    __threadfence();
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
-    long long it = 0;
-    while ((int)(ld_acquire(bar) - target) < 0) {
-      if (++it > kSpinLimit) {
-        atomicOr(status, kStTimeout);
-        break;
-      }
-    }
-    __threadfence();
-    s_ok = (*reinterpret_cast<volatile int*>(status) & (kStTimeout | kStNonFinite)) == 0;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // Exclusive prefix of v over the block's threads; `total` gets the sum.
 __device__ __forceinline__ int block_exclusive_scan(int v, int& total, int* sw) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
