@@ -116,6 +116,19 @@ const char* dfgt_last_error(const dfgt_ctx* ctx);
 dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
                        const dfgt_opts* opts, dfgt_tree** out);
 
+/* Leave-one-out sums over one point set: for every point x_i (tree order
+ * undone, caller's order) and bandwidth h_host[k],
+ *   S_dev[k * n + i] = sum_{j != i} exp(-|x_i - x_j|^2 / 2h^2)
+ * with |S~ - S| <= eps S (Definition 1.2 for the leave-one-out sum itself).
+ * The dual-tree recursion runs with the query tree equal to the reference
+ * tree; a node pair whose point ranges meet counts |R| - 1 other points in
+ * its lower bound and error budget, is summarised only when R holds all of
+ * Q (the summary's exact self term 1 is then taken off), and otherwise goes
+ * to the exact sums, which leave the self interaction out.  Duplicate
+ * points are other points.  n >= 2; otherwise as dfgt_sum. */
+dfgt_status dfgt_sum_loo(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh, double eps,
+                         double* S_dev, dfgt_stats* stats);
+
 /* Cross-validation scores of a bandwidth sweep over one point set (the
  * introduction's CV_LK and CV_LS, with the density estimate of Eq. 1 for
  * the Gaussian kernel, V_{D,h} = (2 pi h^2)^{D/2}).  `tree` holds the
@@ -124,14 +137,14 @@ dfgt_status dfgt_build(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
  *   cv_ls[k] = (1/N) sum_j ( S*_j / ((N-1) V_{D,sqrt2 h}) - 2 S_j / ((N-1) V_{D,h}) ),
  * S_j the leave-one-out sum at h and S*_j at sqrt(2) h (the convolution
  * kernel K_h * K_h; the text's "bandwidth 2h" is read as variance 2h^2).
- * Runs dfgt_sum(tree, tree) over the 2 nh bandwidths {h, sqrt(2) h} with
- * the relative error eps of Definition 1.2 (S_j = G_j - 1, the self term
- * being exact), then reduces on the device in float64.  lk_bound[k] and
- * ls_bound[k] (may be NULL) bound |score - exact score| from that
- * guarantee: (1/N) sum_j -log(1 - eps' G~_j / S~_j) and
- * (1/N) sum_j eps' (G~*_j / ((N-1) V*) + 2 G~_j / ((N-1) V)),
- * eps' = eps / (1 - eps); a leave-one-out sum that may be 0 gives an
- * infinite lk bound, and an estimate S~_j <= 0 a score of -inf.
+ * Runs dfgt_sum_loo over the 2 nh bandwidths {h, sqrt(2) h}, so every
+ * leave-one-out sum has |S~_j - S_j| <= eps S_j, then reduces on the device
+ * in float64.  lk_bound[k] and ls_bound[k] (may be NULL) bound
+ * |score - exact score| from that guarantee: -log(1 - eps) and
+ * (1/N) sum_j eps' (S~*_j / ((N-1) V*) + 2 S~_j / ((N-1) V)),
+ * eps' = eps / (1 - eps); an estimate S~_j <= 0 (a point with no
+ * neighbour above float32 underflow) gives a score of -inf and an infinite
+ * lk bound.
  * Host outputs have nh entries; 1 <= nh <= 512; N >= 2. */
 dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh,
                            double eps, double* cv_lk_host, double* cv_ls_host,

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_batches", "kde_sum_bruteforce",
+__all__ = ["Context", "Tree", "DFGTError", "kde_sum", "kde_sum_loo", "kde_sum_batches", "kde_sum_bruteforce",
            "kde_sum_bruteforce_static", "kde_host", "apply_pairs", "cv_scores", "cv_grad", "cv_likelihood",
            "autotune", "build"]
 
@@ -155,6 +155,21 @@ def kde_sum(ctx: Context, qtree: Tree, rtree: Tree, hs, eps: float, out=None):
     st = ctx.lib.dfgt_sum(ctx.h, qtree.h, rtree.h, hp, len(ha), float(eps), C.c_void_p(out.data_ptr()),
                           C.byref(stats))
     ctx.check(st, "dfgt_sum")
+    return out, stats.as_dict()
+
+
+def kde_sum_loo(ctx: Context, tree: Tree, hs, eps: float, out=None):
+    """dfgt_sum_loo: leave-one-out sums S~ [nh, n] float64 (CUDA) over the
+    tree's points, |S~ - S| <= eps S, and work stats."""
+    torch = _torch()
+    ha, hp = _hs(hs)
+    if out is None:
+        out = torch.empty((len(ha), tree.n), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    stats = _lib.Stats()
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_sum_loo(ctx.h, tree.h, hp, len(ha), float(eps), C.c_void_p(out.data_ptr()),
+                              C.byref(stats))
+    ctx.check(st, "dfgt_sum_loo")
     return out, stats.as_dict()
 
 

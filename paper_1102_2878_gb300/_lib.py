@@ -70,6 +70,8 @@ SIGNATURES = {
     "dfgt_cv_scores": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double,
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(Stats)]),
+    "dfgt_sum_loo": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double,
+                               C.c_void_p, C.POINTER(Stats)]),
     "dfgt_cv_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_int,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "dfgt_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_int,

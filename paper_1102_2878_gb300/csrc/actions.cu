@@ -297,6 +297,55 @@ __device__ __forceinline__ void base_tile_sums(const float4* __restrict__ T, int
   }
 }
 
+// Direct form with the self interaction left out (leave-one-out sums over
+// one tree): the pair slot carries the two references' point indices after
+// their coordinates, and a query meets its own index with weight 0.
+template <int D>
+__device__ __forceinline__ void base_step_loo(const float4* __restrict__ p, const float2* wa, const float2* wb,
+                                              float2 c2p, int ia, int ib, float2& pa, float2& pb) {
+  constexpr int NV = BaseShape<D>::NV;
+  float f[4 * NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float4 t4 = p[v];
+    f[4 * v] = t4.x; f[4 * v + 1] = t4.y; f[4 * v + 2] = t4.z; f[4 * v + 3] = t4.w;
+  }
+  float2 da = make_float2(0.f, 0.f), db = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float2 rk = make_float2(f[2 * k], f[2 * k + 1]);
+    const float2 ta = __fadd2_rn(wa[k], rk);
+    const float2 tb = __fadd2_rn(wb[k], rk);
+    da = __ffma2_rn(ta, ta, da);
+    db = __ffma2_rn(tb, tb, db);
+  }
+  const float2 xa = __fmul2_rn(da, c2p), xb = __fmul2_rn(db, c2p);
+  const int r0 = __float_as_int(f[2 * D]), r1 = __float_as_int(f[2 * D + 1]);
+  pa = __fadd2_rn(pa, make_float2(ia == r0 ? 0.f : ex2_approx(xa.x), ia == r1 ? 0.f : ex2_approx(xa.y)));
+  pb = __fadd2_rn(pb, make_float2(ib == r0 ? 0.f : ex2_approx(xb.x), ib == r1 ? 0.f : ex2_approx(xb.y)));
+}
+
+template <int D>
+__device__ __forceinline__ void base_tile_sums_loo(const float4* __restrict__ T, int np2, int gid, int ngrp,
+                                                   const float2* wa, const float2* wb, float2 c2p, int ia, int ib,
+                                                   float& Sa, float& Ca, float& Sb, float& Cb) {
+  constexpr int SV = BaseShape<D>::SV;
+  int left = np2 >> (31 - __clz(ngrp));
+  const float4* p = T + gid * SV;
+  const int stride = ngrp * SV;
+  while (left > 0) {
+    float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
+    const int nb = left < 16 ? left : 16;
+    for (int u = 0; u < nb; ++u) {
+      base_step_loo<D>(p, wa, wb, c2p, ia, ib, pa, pb);
+      p += stride;
+    }
+    left -= nb;
+    kahan_add(Sa, Ca, pa.x + pa.y);
+    kahan_add(Sb, Cb, pb.x + pb.y);
+  }
+}
+
 // First D coordinates of a staged raw row (RAW floats, 16-byte aligned for RAW >= 4).
 template <int D>
 __device__ __forceinline__ void load_raw(const float* row, float* a) {
@@ -361,9 +410,12 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
   float mc[D], rho2 = 0.f, far2 = 0.f, c2 = 0.f, i2h = 0.f;
 #pragma unroll
   for (int k = 0; k < D; ++k) mc[k] = 0.f;
+  bool self = false;  // leave-one-out: the entry's nodes share points
   if (lane < m) {
     key = ksorted[i0 + lane];
-    const int r = rsorted[i0 + lane] & kNodeMask;
+    const int rv = rsorted[i0 + lane];
+    const int r = rv & kNodeMask;
+    self = ((rv >> kNodeBits) & kSelfFlag) != 0;
     const int hidx = key / Q.nn, q = key - hidx * Q.nn;
     rb = R.beg[r];
     rn = R.cnt[r];
@@ -442,7 +494,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
   // run parameters (warp-uniform), refreshed when the run changes
   float c2r = 0.f, m_[D];
   int qb = 0, qn = 0, hidx = 0;
-  bool expanded = false;
+  bool expanded = false, self_run = false;
   bool new_run = true;
   int g = 32, lgg = 5, ngrp = 1, ql = 0, gid = 0, qcnt_blk = 0;
   while (true) {
@@ -458,7 +510,10 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
           __reduce_max_sync(FULL, (lane >= t && lane < e) ? __float_as_uint(far2) : 0u));
       const float span = __fadd_ru(__fsqrt_ru(rq2), __fsqrt_ru(f2));
       const float ui = (float)(D + 4) * 5.9604645e-08f * __shfl_sync(FULL, i2h, t);
-      expanded = ui * span * span <= kExpandedErr || 8.f * ui * rq2 <= kExpandedErr;
+      // a run with a self entry takes the direct form, which leaves the
+      // self interaction out exactly
+      self_run = __any_sync(FULL, lane >= t && lane < e && self);
+      expanded = !self_run && (ui * span * span <= kExpandedErr || 8.f * ui * rq2 <= kExpandedErr);
       if (expanded && lane == 0) atomicAdd(exp_ctr, (unsigned long long)qn * tot);
       new_run = false;
     }
@@ -526,6 +581,23 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
           f[2 * k] = has_a ? -a[k] : kFarNeg;
           f[2 * k + 1] = has_b ? -b[k] : kFarNeg;
         }
+        if (self_run) {
+          // the references' point indices, for the self test
+          int ga = -1, gb = -1;
+          for (int s2 = 0; s2 < 2; ++s2) {
+            const int J = j0 + 2 * jp + s2;
+            if (J >= j0 + tn) break;
+            int lo = 0, hi = e - t;  // sOff[lo] <= J < sOff[hi]
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (sOff[wib][ts][mid] <= J) lo = mid; else hi = mid;
+            }
+            const int g = sRb[wib][ts][lo] + J - sOff[wib][ts][lo];
+            if (s2 == 0) ga = g; else gb = g;
+          }
+          f[2 * D] = __int_as_float(ga);
+          f[2 * D + 1] = __int_as_float(gb);
+        }
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v)
@@ -573,6 +645,9 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
       float Sa = 0.f, Ca = 0.f, Sb = 0.f, Cb = 0.f;
       if (expanded)
         base_tile_sums<D, true>(sT[wib], np2, gid, ngrp, wqa, wqb, c2p, Sa, Ca, Sb, Cb);
+      else if (self_run)
+        base_tile_sums_loo<D>(sT[wib], np2, gid, ngrp, wqa, wqb, c2p, oka ? qb + qs + qia : -2,
+                              okb ? qb + qs + qib : -2, Sa, Ca, Sb, Cb);
       else
         base_tile_sums<D, false>(sT[wib], np2, gid, ngrp, wqa, wqb, c2p, Sa, Ca, Sb, Cb);
       float va = Sa - Ca, vb = Sb - Cb;
@@ -648,9 +723,12 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
   const int m = (int)min((long)kEntryChunk, n - i0);
   const int dpr = R.dp, dpq = Q.dp;
   int key = -1 - lane, rb = 0, rn = 0, qbeg = 0, qcnt = 0;
+  bool self = false;  // leave-one-out: the entry's nodes share points
   if (lane < m) {
     key = ksorted[i0 + lane];
-    const int r = rsorted[i0 + lane] & kNodeMask;
+    const int rv = rsorted[i0 + lane];
+    const int r = rv & kNodeMask;
+    self = ((rv >> kNodeBits) & kSelfFlag) != 0;
     const int q = key % Q.nn;
     rb = R.beg[r];
     rn = R.cnt[r];
@@ -683,6 +761,7 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
     const int qb = __shfl_sync(FULL, qbeg, t), qn = __shfl_sync(FULL, qcnt, t);
     const float c2 = c2v[hidx];
     const float2 c2p = make_float2(c2, c2);
+    const bool loo = __any_sync(FULL, lane >= t && lane < e && self);
     __syncwarp();
     for (int qs = 0; qs < qn; qs += 32 * kHdQBlocks) {
       const int nblk = min(kHdQBlocks, (qn - qs + 31) / 32);
@@ -701,12 +780,15 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
             float* slot = T + (jj >> 1) * PS + (jj & 1);
             if (J < tot) {
               while (sOff[wib][u + 1] <= J) ++u;
-              const float* src = R.pts + (size_t)(sRb[wib][u] + J - sOff[wib][u]) * dpr;
+              const int g = sRb[wib][u] + J - sOff[wib][u];
+              const float* src = R.pts + (size_t)g * dpr;
 #pragma unroll
               for (int k = 0; k < DM; ++k) slot[2 * k] = k < dpr ? -src[k] : 0.f;
+              slot[2 * DM] = __int_as_float(g);  // the point index, for the self test
             } else {
 #pragma unroll
               for (int k = 0; k < DM; ++k) slot[2 * k] = -1.0e18f;
+              slot[2 * DM] = __int_as_float(-1);
             }
           }
         }
@@ -717,6 +799,7 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
           const int NG = 32 / QL, ql = lane & (QL - 1), grp = lane / QL;
           const bool vq = ql < qbk;
           const int qi = qs + 32 * b + ql;
+          const int qg = vq ? qb + qi : -2;  // the query's point index
           float2 qq[DM];
 #pragma unroll
           for (int k = 0; k < DM; ++k) {
@@ -737,7 +820,13 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
               d2 = __ffma2_rn(db, db, d2);
             }
             const float2 x = __fmul2_rn(d2, c2p);
-            blk = __fadd2_rn(blk, make_float2(ex2_approx(x.x), ex2_approx(x.y)));
+            float e0 = ex2_approx(x.x), e1 = ex2_approx(x.y);
+            if (loo) {  // leave-one-out: a query meets its own index with weight 0
+              const int2 ids = *reinterpret_cast<const int2*>(T + p * PS + 2 * DM);
+              if (ids.x == qg) e0 = 0.f;
+              if (ids.y == qg) e1 = 0.f;
+            }
+            blk = __fadd2_rn(blk, make_float2(e0, e1));
             if (++steps == 8) {
               steps = 0;
               kahan_add(S[b], Cc[b], blk.x + blk.y);
@@ -813,7 +902,7 @@ __device__ __forceinline__ void eval_nested(const float* __restrict__ M, const f
 template <int D, int NQ>
 __device__ __forceinline__ void farfield_points(const TreeView& Q, const float* Ms, const CenterHL* cR,
                                                 float sf, int qb, int qn, int q0, int lane,
-                                                double* __restrict__ gout) {
+                                                double* __restrict__ gout, double sub) {
   constexpr int PM = pmax_of(D);
   float H[NQ][D][PM];
 #pragma unroll
@@ -831,7 +920,7 @@ __device__ __forceinline__ void farfield_points(const TreeView& Q, const float* 
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
     const int qi = q0 + lane + 32 * j;
-    if (qi < qn) atomicAdd(&gout[qb + qi], (double)acc[j]);
+    if (qi < qn) atomicAdd(&gout[qb + qi], (double)acc[j] - sub);
   }
 }
 
@@ -850,7 +939,10 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
   const Action a = list[w];
   const float sf = sfv[a.h];
   float* Ms = sM[wib];
-  stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * sf, a.p, Ms, lane);
+  // a summary over a node holding the query itself (leave-one-out sums)
+  // loses its exact self term 1
+  const double sub = (a.p & kSelfFlag) ? 1.0 : 0.0;
+  stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * sf, a.p & kOrderMask, Ms, lane);
   __syncwarp();
   CenterHL cR[D];
 #pragma unroll
@@ -860,10 +952,10 @@ __global__ void __launch_bounds__(kT) k_farfield(TreeView Q, TreeView R,
   double* gout = gacc + (size_t)a.h * Q.n;
   for (int q0 = 0; q0 < qn;) {
     if (qn - q0 > 32) {
-      farfield_points<D, 2>(Q, Ms, cR, sf, qb, qn, q0, lane, gout);
+      farfield_points<D, 2>(Q, Ms, cR, sf, qb, qn, q0, lane, gout, sub);
       q0 += 64;
     } else {
-      farfield_points<D, 1>(Q, Ms, cR, sf, qb, qn, q0, lane, gout);
+      farfield_points<D, 1>(Q, Ms, cR, sf, qb, qn, q0, lane, gout, sub);
       q0 += 32;
     }
   }
@@ -1012,7 +1104,7 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
     if (ei < n) {
       key = ksorted[ei];
       const int v = rsorted[ei];
-      rp = v >> kNodeBits;
+      rp = (v >> kNodeBits) & kOrderMask;
       const int rb = R.beg[v & kNodeMask];
       const long long eo = eoff[ei] + kEntryCost;
       ee = eoff[ei + 1];
@@ -1020,6 +1112,9 @@ __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const i
       if (s1 > s0) {
         c = (int)(s1 - s0);
         rs = rb + (int)(s0 - eo);
+        // a node holding the query itself (leave-one-out sums): the slice
+        // with the entry's first reference takes the self term 1 off L_0
+        if (((v >> kNodeBits) & kSelfFlag) && s0 == eo) atomicAdd(&L[(size_t)key * P], -1.0);
       }
     }
     int incl = c;
@@ -1160,9 +1255,11 @@ __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action
 #pragma unroll
     for (int e = 0; e < NH; ++e) sH[wib][lane][e] = (float)H[e];
   }
-  stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * (float)s, a.p, sM[wib], lane);
+  const int ord = a.p & kOrderMask;
+  stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * (float)s, ord, sM[wib], lane);
   __syncwarp();
   const size_t hq = (size_t)a.h * Q.nn + a.q;
+  if (lane == 0 && (a.p & kSelfFlag)) atomicAdd(&L[hq * P], -1.0);  // the node holds the query itself
 #pragma unroll
   for (int sl = 0; sl < S; ++sl) {
     const int idx = lane + 32 * sl;
@@ -1174,7 +1271,7 @@ __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action
     {
       int v = idx;
 #pragma unroll
-      for (int k = D - 1; k >= 0; --k) { be[k] = v % PM; v /= PM; ab += be[k]; ok = ok && be[k] < a.p; f *= fact_d(be[k]); }
+      for (int k = D - 1; k >= 0; --k) { be[k] = v % PM; v /= PM; ab += be[k]; ok = ok && be[k] < ord; f *= fact_d(be[k]); }
     }
     if (!ok) continue;
     float acc = 0.f;
@@ -1187,7 +1284,7 @@ __global__ void __launch_bounds__(kT) k_f2l(TreeView Q, TreeView R, const Action
     }
     atomicAdd(&L[hq * P + idx], ((ab & 1) ? -(double)acc : (double)acc) / f);
   }
-  if (lane == 0) atomicMax(&pused[hq], a.p);
+  if (lane == 0) atomicMax(&pused[hq], ord);
 }
 
 // ------------------------------------------------------------- prune
@@ -1374,7 +1471,8 @@ __global__ void __launch_bounds__(kT) k_farfield_g(TreeView Q, TreeView R, const
       const float t = minus_center(Q.pts[(size_t)(qb + qi) * Q.dp + k], center_hl(R, a.r, k));
       d2 = fmaf(t, t, d2);
     }
-    atomicAdd(&gacc[(size_t)a.h * Q.n + qb + qi], (double)(m0 * ex2_approx(d2 * c2)));
+    atomicAdd(&gacc[(size_t)a.h * Q.n + qb + qi],
+              (double)(m0 * ex2_approx(d2 * c2)) - ((a.p & kSelfFlag) ? 1.0 : 0.0));
   }
 }
 
@@ -1401,7 +1499,7 @@ __global__ void __launch_bounds__(kT) k_local_g(TreeView Q, TreeView R, const Ac
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const size_t hq = (size_t)a.h * Q.nn + a.q;
   if (lane == 0) {
-    atomicAdd(&L[hq], v);
+    atomicAdd(&L[hq], v - ((a.p & kSelfFlag) ? 1.0 : 0.0));
     atomicMax(&pused[hq], 1);
   }
 }
@@ -1419,7 +1517,7 @@ __global__ void k_f2l_g(TreeView Q, TreeView R, const Action* __restrict__ list,
     d2 += t * t;
   }
   const size_t hq = (size_t)a.h * Q.nn + a.q;
-  atomicAdd(&L[hq], R.mom[a.r] * exp(-d2 / (2.0 * h * h)));
+  atomicAdd(&L[hq], R.mom[a.r] * exp(-d2 / (2.0 * h * h)) - ((a.p & kSelfFlag) ? 1.0 : 0.0));
   atomicMax(&pused[hq], 1);
 }
 

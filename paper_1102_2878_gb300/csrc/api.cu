@@ -79,7 +79,7 @@ dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, doubl
 
 // Zeroed per-call state; returns the traversal buffers.
 dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
-                        const double* h_host, int nh, double eps_eff, TravBuffers* b) {
+                        const double* h_host, int nh, double eps_eff, TravBuffers* b, bool loo = false) {
   cudaStream_t s = ctx->stream;
   const size_t nodes = (size_t)nh * qt->nn;
   CK(ctx->hvals.ensure(4 * (size_t)nh * sizeof(double)));
@@ -133,7 +133,9 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
-  b->fix_scale = std::ldexp(1.0, 62) / (double)rt->n;
+  // lower bounds in units of the references each query can see, 2^-62
+  b->loo = loo ? 1 : 0;
+  b->fix_scale = std::ldexp(1.0, 62) / (double)(loo ? rt->n - 1 : rt->n);
   b->inv_fix = 1.0 / b->fix_scale;
   b->fix_scale_dn = std::nextafter((float)b->fix_scale, 0.f);
   b->inv_nr = 1.0 / (double)rt->n;
@@ -212,14 +214,14 @@ dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const
 }
 
 dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const double* h_host,
-                    int nh, double eps, double* G_dev, dfgt_stats* st) {
+                    int nh, double eps, double* G_dev, dfgt_stats* st, bool loo = false) {
   cudaStream_t s = ctx->stream;
   const long long launches0 = ctx->launches;
   const TreeView Q = qt->view(), R = rt->view();
   const double eps_eff = eps - std::max(qt->eps_fp, rt->eps_fp);
   const int max_rounds = qt->depth + rt->depth + 8;
   TravBuffers b;
-  dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, &b);
+  dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, &b, loo);
   if (rc != DFGT_OK) return rc;
   b.base_block = std::max(qt->base_block, rt->base_block);
   ctx->cap_frontier = std::max<size_t>(ctx->cap_frontier, (size_t)nh);
@@ -484,6 +486,21 @@ dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtr
   return run_sum(ctx, qtree, rtree, h_host, nh, eps, G_dev, stats);
 }
 
+dfgt_status dfgt_sum_loo(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh, double eps,
+                         double* S_dev, dfgt_stats* stats) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!tree || !S_dev || tree->n < 2)
+    return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: need a tree of at least 2 points and an output");
+  if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: need 1..1024 finite bandwidths > 0");
+  if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: need 0 < eps < 1");
+  if (!(tree->eps_fp < eps)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: eps must exceed the float allowance eps_fp");
+  if (tree->device != ctx->device) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: the tree lives on another device");
+  CK(cudaSetDevice(ctx->device));
+  ctx->err.clear();
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  return run_sum(ctx, tree, tree, h_host, nh, eps, S_dev, stats, true);
+}
+
 dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh, double eps,
                            double* cv_lk, double* cv_ls, double* lk_bound, double* ls_bound,
                            dfgt_stats* stats) {
@@ -502,7 +519,7 @@ dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h
   for (int k = 0; k < 2 * nh; ++k) norm[k] = (double)(n - 1) * std::pow(2.0 * pi * h2[k] * h2[k], 0.5 * d);
   CK(cudaSetDevice(ctx->device));
   CK(ctx->io_g.ensure(2 * (size_t)nh * n * sizeof(double)));
-  dfgt_status rc = dfgt_sum(ctx, tree, tree, h2.data(), 2 * nh, eps, ctx->io_g.as<double>(), stats);
+  dfgt_status rc = dfgt_sum_loo(ctx, tree, h2.data(), 2 * nh, eps, ctx->io_g.as<double>(), stats);
   if (rc != DFGT_OK) return rc;
   const int nblk = std::max(1, std::min(304, (n + 1023) / 1024));
   const size_t nnorm = 2 * (size_t)nh, npart = (size_t)nh * nblk * 4, nout = (size_t)nh * 4;

@@ -221,6 +221,20 @@ struct Action {
 };
 
 enum : int { kFlagSplitQ = 1 };
+// Leave-one-out sums: an action or base entry whose reference node holds the
+// query itself (the self term is removed exactly); kept above the order bits.
+enum : int { kSelfFlag = 16, kOrderMask = 15 };
+
+// Do the point ranges of node q of Q and node r of R (the same tree) meet?
+__device__ __forceinline__ bool ranges_meet(const TreeView& Q, int q, const TreeView& R, int r) {
+  const int qb = Q.beg[q], rb = R.beg[r];
+  return qb < rb + R.cnt[r] && rb < qb + Q.cnt[q];
+}
+// Does node r of R hold every point of node q of Q (the same tree)?
+__device__ __forceinline__ bool range_holds(const TreeView& R, int r, const TreeView& Q, int q) {
+  const int qb = Q.beg[q], rb = R.beg[r];
+  return rb <= qb && qb + Q.cnt[q] <= rb + R.cnt[r];
+}
 
 // Device status word bits (read back once per call).
 enum : int {

@@ -3,16 +3,16 @@
 // least-squares score CV_LS of the paper's introduction, with the density
 // estimate of Eq. 1 (Gaussian kernel, V_{D,h} = (2 pi h^2)^{D/2}).
 //
-// With Q = R the leave-one-out sum of point i is S_i = G_i - 1 (the self
-// term exp(0) = 1 is exact), and the convolution kernel K_h * K_h of CV_LS
-// is the Gaussian of deviation sqrt(2) h, so both scores follow from one
-// sum over the bandwidths h and sqrt(2) h:
+// The inputs are the leave-one-out sums S_i (dfgt_sum_loo, Q = R, each
+// point's own term left out) over the bandwidths h and sqrt(2) h (the
+// convolution kernel K_h * K_h of CV_LS is the Gaussian of deviation
+// sqrt(2) h):
 //   CV_LK(h) = (1/N) sum_i log(S_i / ((N-1) V_{D,h}))
 //   CV_LS(h) = (1/N) sum_i (S*_i / ((N-1) V_{D,sqrt2 h}) - 2 S_i / ((N-1) V_{D,h})).
-// The sums carry |G~ - G| <= eps G, i.e. |G~ - G| <= eps' G~ with
-// eps' = eps / (1 - eps), so S >= S~ - eps' G~ and
-// |log S~ - log S| <= -log(1 - eps' G~ / S~); the CV_LS error is linear in
-// the sums.  Both bounds are accumulated beside the scores.  The reduction
+// The sums carry |S~ - S| <= eps S, so |log S~ - log S| <= -log(1 - eps)
+// and |S~ - S| <= eps' S~ with eps' = eps / (1 - eps); the CV_LS error is
+// linear in the sums.  Both bounds are accumulated beside the scores.  The
+// reduction
 // is float64 and runs in a fixed order (per-block partials, then one pass
 // per bandwidth), so scores are reproducible.
 #include <cmath>
@@ -38,7 +38,7 @@ __device__ __forceinline__ double block_sum(double v, double* scratch) {
   return t;  // valid in thread 0
 }
 
-// G: [2 nh][n], rows k < nh at h_k and rows nh + k at sqrt(2) h_k.
+// G: [2 nh][n] leave-one-out sums, rows k < nh at h_k and rows nh + k at sqrt(2) h_k.
 // norm: [2 nh] (n - 1) V for the same rows.  part: [nh][gridDim.x][kTerms].
 __global__ void __launch_bounds__(kT) k_cv_partials(const double* __restrict__ G, int n, int nh,
                                                     const double* __restrict__ norm, double epsp,
@@ -49,14 +49,13 @@ __global__ void __launch_bounds__(kT) k_cv_partials(const double* __restrict__ G
   const double* gs = G + (size_t)(nh + k) * n;
   const double nv = norm[k], nvs = norm[nh + k];
   double t[kTerms] = {0.0, 0.0, 0.0, 0.0};
+  const double eps = epsp / (1.0 + epsp);
   for (int i = blockIdx.x * kT + threadIdx.x; i < n; i += gridDim.x * kT) {
-    const double Gi = g[i], Gs = gs[i];
-    const double S = Gi - 1.0, Ss = Gs - 1.0;
+    const double S = g[i], Ss = gs[i];
     t[0] += S > 0.0 ? log(S) : -INFINITY;
-    const double r = epsp * Gi / S;
-    t[1] += (S > 0.0 && r < 1.0) ? -log1p(-r) : INFINITY;
+    t[1] += S > 0.0 ? -log1p(-eps) : INFINITY;
     t[2] += Ss / nvs - 2.0 * S / nv;
-    t[3] += epsp * (Gs / nvs + 2.0 * Gi / nv);
+    t[3] += epsp * (Ss / nvs + 2.0 * S / nv);
   }
 #pragma unroll
   for (int q = 0; q < kTerms; ++q) {

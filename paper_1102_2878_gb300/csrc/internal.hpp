@@ -208,6 +208,7 @@ struct TravBuffers {
   int p_limit;
   long long base_block;  // exact sum without recursing when |Q||R| <= this
   int sms;               // SMs of the device (sizes the balanced launches)
+  int loo;               // leave-one-out sums: Q and R are one tree, each query's own term is left out
 };
 
 // State of the device-driven traversal between launches (device memory).

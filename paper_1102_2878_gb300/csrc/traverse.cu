@@ -134,7 +134,9 @@ __device__ __forceinline__ void lb_phase(const TreeView& Q, const TreeView& R, c
     box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
     const float Ku = kernel_lower(du2, b.inv2h2_up[pr.h]);
     b.ku[i] = Ku;  // reused by the classification of the same pair
-    const u64 f = to_fix_f((float)R.cnt[pr.r], Ku, b.fix_scale_dn);
+    // leave-one-out: a node meeting Q holds at most |R| - 1 other points for some query
+    const int nr = R.cnt[pr.r] - ((b.loo && ranges_meet(Q, pr.q, R, pr.r)) ? 1 : 0);
+    const u64 f = to_fix_f((float)nr, Ku, b.fix_scale_dn);
     if (f) atomicAdd(&b.lbsum[hq], f);
   }
 }
@@ -162,13 +164,23 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
       const size_t hq = (size_t)pr.h * Q.nn + pr.q;
       const int cQ = Q.cnt[pr.q], cR = R.cnt[pr.r];
       const float nQ = (float)cQ, nR = (float)cR;
+      // Leave-one-out sums (Q and R one tree): a pair whose nodes share
+      // points counts |R| - 1 other references (for the lower bound and the
+      // budget); it may be summarised only if R holds all of Q, and then the
+      // summary's exact self term 1 is taken off, so its error bound (for
+      // all |R| terms) is unchanged.  Pairs that only partly overlap go to
+      // exact sums, which skip the self interaction.
+      const bool meet = b.loo && ranges_meet(Q, pr.q, R, pr.r);
+      const bool holds = meet && range_holds(R, pr.r, Q, pr.q);
+      const bool summarise = !meet || holds;
+      const float nRo = meet ? nR - 1.f : nR;
       float dl2, du2, sideQ, sideR;
       box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
       const float Kl = kernel_upper(dl2, b.inv2h2_dn[pr.h]);
       const float Ku = b.ku[i];
       const u64 lbf = __ldcg(b.inherited + hq) + __ldcg(b.decided + hq) + __ldcg(b.lbsum + hq);
       // tau = eps |R| G^l(Q) / |R_total| (CanSummarize), rounded down
-      const float tau = __fmul_rd(__fmul_rd(b.tau_scale_dn, nR), u64_to_f_rd(lbf));
+      const float tau = __fmul_rd(__fmul_rd(b.tau_scale_dn, nRo), u64_to_f_rd(lbf));
       // prune: the kernel over the pair lies in [Ku, Kl]; the midpoint is off by
       // at most half the width, plus the float32 rounding of the midpoint
       // value itself (two roundings, covered by 4u of it)
@@ -176,13 +188,13 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
       const float value = halfR * (Kl + Ku);
       const float err_prune = __fadd_ru(__fmul_ru(halfR, __fsub_ru(Kl, Ku)),
                                         __fmul_ru(__fmul_ru(halfR, __fadd_ru(Kl, Ku)), 2.4e-7f));
-      if (err_prune <= tau) {
+      if (summarise && err_prune <= tau) {
         kind = 0;
-        atomicAdd(&b.L[hq * P], (double)value);
+        atomicAdd(&b.L[hq * P], (double)value - (holds ? 1.0 : 0.0));
         atomicMax(&b.pused[hq], 1);
       } else {
         int pF = 0, pD = 0, pT = 0;
-        if (tau > 0.f) {
+        if (summarise && tau > 0.f) {
           const float inv_2h = b.inv_2h_up[pr.h];
           pF = order_ff(__fmul_ru(sideR, inv_2h), nR, d, tau, b.p_limit);
           pD = order_ff(__fmul_ru(sideQ, inv_2h), nR, d, tau, b.p_limit);
@@ -224,9 +236,11 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
         }
       }
       if (kind <= 4) {
-        const u64 f = to_fix_f(nR, Ku, b.fix_scale_dn);
+        const u64 f = to_fix_f(nRo, Ku, b.fix_scale_dn);
         if (f) atomicAdd(&b.incr[hq], f);
       }
+      if (holds && kind >= 1 && kind <= 3) order |= kSelfFlag;
+      if (meet && kind == 4) order = kSelfFlag;
     }
     // Block-aggregated appends: the five counts of each pair (children,
     // F, D, T, base) packed in 12-bit fields of one word, one block-wide
@@ -287,7 +301,7 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
     if (kind == 1) { const int s1 = field(1); if (s1 < cap_lists) far[s1] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
     if (kind == 2) { const int s2 = field(2); if (s2 < cap_lists) loc[s2] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
     if (kind == 3) { const int s3 = field(3); if (s3 < cap_lists) f2l[s3] = Action{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
-    if (kind == 4) { const int s4 = field(4); if (s4 < cap_lists) base[s4] = Pair{pr.q, pr.r, pr.h, 0}; else atomicOr(&ctr->status, kStOverflow); }
+    if (kind == 4) { const int s4 = field(4); if (s4 < cap_lists) base[s4] = Pair{pr.q, pr.r, pr.h, order}; else atomicOr(&ctr->status, kStOverflow); }
     my_prune += kind == 0 ? 1ull : 0ull;
     my_inter += inter;
     __syncthreads();  // sWarp / sBase are reused by the next step
