@@ -275,8 +275,10 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
       if (rc != DFGT_OK) return rc;
     }
     // both frontier buffers (and the per-pair bounds) hold at least 8 nF
-    // pairs, so the frontier can grow twofold before the next return
-    const size_t capf = std::min<size_t>(std::max(ctx->cap_frontier, 8 * (size_t)nF), INT32_MAX);
+    // pairs, so the frontier can grow twofold before the next return; a
+    // launch that stopped for room doubles them at least
+    const size_t grown = launch > 0 ? 2 * ctx->cap_frontier : ctx->cap_frontier;
+    const size_t capf = std::min<size_t>(std::max(grown, 8 * (size_t)nF), INT32_MAX);
     ctx->cap_frontier = capf;
     CK(grow_keep(ctx->frontier[cur], capf * sizeof(Pair), (size_t)nF * sizeof(Pair), s));
     CK(ctx->frontier[cur ^ 1].ensure(capf * sizeof(Pair)));
@@ -323,6 +325,8 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     rc = drain(ctx, qt, rt, b, w, lists[w], dcount[w]);
     if (rc != DFGT_OK) return rc;
   }
+  // a sum that had to drain lists early leaves room for the next one
+  if (flushes > 0) ctx->cap_lists = std::min(kHardCap, 2 * ctx->cap_lists);
   CK(cudaEventRecord(ctx->ev[2], s));
   rc = post(ctx, qt, b, G_dev, st);
   if (rc != DFGT_OK) return rc;
