@@ -276,8 +276,9 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     }
     // both frontier buffers (and the per-pair bounds) hold at least 8 nF
     // pairs, so the frontier can grow twofold before the next return; a
-    // launch that stopped for room doubles them at least
-    const size_t grown = launch > 0 ? 2 * ctx->cap_frontier : ctx->cap_frontier;
+    // launch that stopped because the frontier outgrew them doubles them
+    const bool outgrew = 4 * (size_t)nF > ctx->cap_frontier;
+    const size_t grown = outgrew ? 2 * ctx->cap_frontier : ctx->cap_frontier;
     const size_t capf = std::min<size_t>(std::max(grown, 8 * (size_t)nF), INT32_MAX);
     ctx->cap_frontier = capf;
     CK(grow_keep(ctx->frontier[cur], capf * sizeof(Pair), (size_t)nF * sizeof(Pair), s));
