@@ -199,6 +199,8 @@ struct BaseShape {
   static constexpr int NV = PAIRW / 4;
   static constexpr int SV = (2 * RAW > PAIRW ? 2 * RAW : PAIRW) / 4;
   static constexpr int TILE = D == 1 ? 1024 : D == 2 ? 512 : D == 3 ? 448 : 192;
+  // a tile's reference pairs are padded to a multiple of the lane groups (up to 32)
+  static_assert((TILE / 2) % 32 == 0, "TILE / 2 must be a multiple of 32");
 };
 
 __device__ __forceinline__ void cp_async_row(float* dst, const float* src, int bytes) {
