@@ -117,11 +117,17 @@ __device__ __forceinline__ float pow_int_f(float x, int e) {
   return r;
 }
 
-__device__ inline float rsqrt_fact_f(int p) {
-  // 1/sqrt(p!) for p = 0..8
-  const float t[9] = {1.f, 1.f, 0.70710678f, 0.40824829f, 0.20412415f,
-                      0.091287093f, 0.037267800f, 0.014085904f, 0.0049801192f};
-  return t[p < 9 ? p : 8];
+__device__ __forceinline__ float rsqrt_fact_f(int p) {
+  // 1/sqrt(p!) for p = 0..8, as a chain of selects (no indexed local array)
+  float t = 1.f;
+  t = p == 2 ? 0.70710678f : t;
+  t = p == 3 ? 0.40824829f : t;
+  t = p == 4 ? 0.20412415f : t;
+  t = p == 5 ? 0.091287093f : t;
+  t = p == 6 ? 0.037267800f : t;
+  t = p == 7 ? 0.014085904f : t;
+  t = p >= 8 ? 0.0049801192f : t;
+  return t;
 }
 
 // Eq. error_bound_far_field (and error_bound_local) plus the rounding
@@ -135,7 +141,7 @@ __device__ inline float bound_ff_total(float nR, int D, float r, int p) {
     ak *= a;
     c = c * (float)(D - k) / (float)(k + 1);
   }
-  const float g = 1.f / (1.f - r);
+  const float g = __frcp_rn(1.f - r);  // correctly rounded, as 1 / (1 - r)
   const float gD = pow_int_f(g, D);
   const float S = pow_int_f(a * g, D);
   const float cfp = fp_allowance_c(p, D) * 5.9604645e-08f;
@@ -152,7 +158,7 @@ __device__ inline float bound_f2l_total(float nR, int D, float r, int p) {
     ak *= a;
     c = c * (float)(D - k) / (float)(k + 1);
   }
-  const float g = 1.f / (1.f - 2.f * r);
+  const float g = __frcp_rn(1.f - 2.f * r);  // correctly rounded, as 1 / (1 - 2r)
   const float g2D = pow_int_f(g, 2 * D);
   const float S = pow_int_f((1.f - q) * g, 2 * D);
   const float cfp = fp_allowance_c(p, D) * 5.9604645e-08f;
