@@ -120,7 +120,6 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 // f32x2 step on two interactions.  Each lane holds two queries; for a run
 // of few queries the warp splits into lane groups that share the queries
 // and divide the references.
-constexpr int kBaseChunk = 8;     // entries per warp of the local-moment kernel
 constexpr int kEntryChunk = 32;   // entries per warp of the base case
 constexpr int kBaseWarps = 4;     // warps per block of the base case
 constexpr int kNodeBits = 27;  // node indices stay below 2^27 (checked by the tree build)
@@ -265,7 +264,6 @@ template <int D, bool EXP>
 __device__ __forceinline__ void base_tile_sums(const float4* __restrict__ T, int np2, int gid, int ngrp,
                                                const float2* wa, const float2* wb, float2 c2p,
                                                float& Sa, float& Ca, float& Sb, float& Cb) {
-  constexpr int NV = BaseShape<D>::NV;
   // np2 is padded to a multiple of ngrp (a power of two): the same count in every lane
   int left = np2 >> (31 - __clz(ngrp));
   constexpr int SV = BaseShape<D>::SV;
