@@ -54,7 +54,9 @@ typedef struct {
                       (Section 3.6: 6 for D=2, 4 for D=3, 2 for D=4,5, 1 for D>=6;
                       8 for D=1); a smaller positive value lowers it */
   double eps_fp;   /* part of eps reserved for float32 rounding in exact sums;
-                      0 -> 2e-5; must be < eps */
+                      0 -> chosen per sum: 1% of eps, within [2e-5, 1e-4]
+                      (a sum takes the larger of its two trees' values);
+                      must be < eps */
   long long base_block; /* a node pair that no summary can take is summed exactly,
                       without splitting further, once |Q| |R| <= base_block;
                       0 -> 4096, -1 -> only leaf pairs (as in DFGT) */

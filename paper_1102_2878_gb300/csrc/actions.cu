@@ -375,12 +375,12 @@ __device__ __forceinline__ void load_raw(const float* row, float* a) {
 //    cannot overflow, and it underflows only where 2^x does).  Its error in
 //    x, with the rounding of q~ and r~ taken as a perturbation of the points,
 //    is at most (D+4) u (|q~| + |r~|)^2 / 2h^2.  A run uses it when that is
-//    at most kExpandedErr for the query box and the farthest corner of every
-//    reference box, or when 8 (D+4) u rho_Q^2 / 2h^2 <= kExpandedErr for the
-//    query box radius rho_Q alone: with |r~| <= |q~| + |q - r| and
-//    (a + b)^2 <= 2a^2 + 2b^2 the error is then at most
-//    kExpandedErr + 2 (D+4) u x per term.  Otherwise the direct form.
-constexpr float kExpandedErr = 5e-6f;
+//    at most E for the query box and the farthest corner of every reference
+//    box, or when 8 (D+4) u rho_Q^2 / 2h^2 <= E for the query box radius
+//    rho_Q alone: with |r~| <= |q~| + |q - r| and (a + b)^2 <= 2a^2 + 2b^2
+//    the error is then at most E + 2 (D+4) u x per term.  Otherwise the
+//    direct form.  E is a quarter of the float allowance eps_fp, so a term
+//    stays within eps_fp whenever 2^-21 + eps_fp / 4 + 2 (D+4) u x <= eps_fp.
 
 constexpr int kQCap = 128;  // queries of a run staged at a time
 
@@ -388,7 +388,7 @@ template <int D>
 __global__ void __launch_bounds__(kBaseWarps * 32, 5)
     k_base(TreeView Q, TreeView R, const int* __restrict__ rsorted, const int* __restrict__ ksorted, int n,
            const float* __restrict__ c2v, const float* __restrict__ inv2h2_up, double* __restrict__ gacc,
-           unsigned long long* __restrict__ exp_ctr) {
+           unsigned long long* __restrict__ exp_ctr, float exp_err) {
   using SH = BaseShape<D>;
   constexpr int TILE = SH::TILE, RAW = SH::RAW, NV = SH::NV, SV = SH::SV;
   constexpr int QV = (D + 1 + 3) / 4;  // float4 per staged query: W (or q) then A
@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 5)
       // a run with a self entry takes the direct form, which leaves the
       // self interaction out exactly
       self_run = __any_sync(FULL, lane >= t && lane < e && self);
-      expanded = !self_run && (ui * span * span <= kExpandedErr || 8.f * ui * rq2 <= kExpandedErr);
+      expanded = !self_run && (ui * span * span <= exp_err || 8.f * ui * rq2 <= exp_err);
       if (expanded && lane == 0) atomicAdd(exp_ctr, (unsigned long long)qn * tot);
       new_run = false;
     }
@@ -1587,7 +1587,7 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
     const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kBaseWarps - 1) / kBaseWarps);
     DISPATCH_D(Q.d, k_base<DD><<<g, kBaseWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up,
-                                                              b.gacc, b.base_exp));
+                                                              b.gacc, b.base_exp, b.exp_err));
   } else {
     const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);

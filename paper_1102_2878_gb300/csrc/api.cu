@@ -77,9 +77,17 @@ dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, doubl
   return DFGT_OK;
 }
 
+// Part of eps reserved for float32 rounding in exact sums: the larger of
+// the trees' eps_fp, or, where both leave it 0, 1% of eps within
+// [2e-5, 1e-4].
+double float_allowance(const dfgt_tree* a, const dfgt_tree* b, double eps) {
+  const double v = std::max(a->eps_fp, b->eps_fp);
+  return v > 0.0 ? v : std::min(1e-4, std::max(2e-5, 0.01 * eps));
+}
+
 // Zeroed per-call state; returns the traversal buffers.
-dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
-                        const double* h_host, int nh, double eps_eff, TravBuffers* b, bool loo = false) {
+dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const double* h_host, int nh,
+                        double eps_eff, double eps_fp, TravBuffers* b, bool loo = false) {
   cudaStream_t s = ctx->stream;
   const size_t nodes = (size_t)nh * qt->nn;
   CK(ctx->hvals.ensure(4 * (size_t)nh * sizeof(double)));
@@ -133,6 +141,8 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
+  // the expanded form of exact sums may spend a quarter of the float allowance
+  b->exp_err = std::nextafter((float)(0.25 * eps_fp), 0.f);
   // lower bounds in units of the references each query can see, 2^-62
   b->loo = loo ? 1 : 0;
   b->fix_scale = std::ldexp(1.0, 62) / (double)(loo ? rt->n - 1 : rt->n);
@@ -218,10 +228,11 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
   cudaStream_t s = ctx->stream;
   const long long launches0 = ctx->launches;
   const TreeView Q = qt->view(), R = rt->view();
-  const double eps_eff = eps - std::max(qt->eps_fp, rt->eps_fp);
+  const double eps_fp = float_allowance(qt, rt, eps);
+  const double eps_eff = eps - eps_fp;
   const int max_rounds = qt->depth + rt->depth + 8;
   TravBuffers b;
-  dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, &b, loo);
+  dfgt_status rc = setup_state(ctx, qt, rt, h_host, nh, eps_eff, eps_fp, &b, loo);
   if (rc != DFGT_OK) return rc;
   b.base_block = std::max(qt->base_block, rt->base_block);
   ctx->cap_frontier = std::max<size_t>(ctx->cap_frontier, (size_t)nh);
@@ -481,7 +492,7 @@ dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtr
     return fail(ctx, DFGT_EINVAL, "dfgt_sum: need two trees of the same dimension and an output");
   if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_sum: need 1..1024 finite bandwidths > 0");
   if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, DFGT_EINVAL, "dfgt_sum: need 0 < eps < 1");
-  if (!(std::max(qtree->eps_fp, rtree->eps_fp) < eps))
+  if (!(float_allowance(qtree, rtree, eps) < eps))
     return fail(ctx, DFGT_EINVAL, "dfgt_sum: eps must exceed the float allowance eps_fp");
   if (qtree->device != ctx->device || rtree->device != ctx->device)
     return fail(ctx, DFGT_EINVAL, "dfgt_sum: trees live on another device");
@@ -498,7 +509,7 @@ dfgt_status dfgt_sum_loo(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_h
     return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: need a tree of at least 2 points and an output");
   if (bad_h(h_host, nh)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: need 1..1024 finite bandwidths > 0");
   if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: need 0 < eps < 1");
-  if (!(tree->eps_fp < eps)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: eps must exceed the float allowance eps_fp");
+  if (!(float_allowance(tree, tree, eps) < eps)) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: eps must exceed the float allowance eps_fp");
   if (tree->device != ctx->device) return fail(ctx, DFGT_EINVAL, "dfgt_sum_loo: the tree lives on another device");
   CK(cudaSetDevice(ctx->device));
   ctx->err.clear();
@@ -743,7 +754,8 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   TravBuffers b;
   CK(wait_ready(s, qt));
   CK(wait_ready(s, rt));
-  dfgt_status rc = setup_state(ctx, qt, rt, &h, 1, 0.5, &b);
+  // exact sums here take the trees' float allowance, or the smallest automatic one
+  dfgt_status rc = setup_state(ctx, qt, rt, &h, 1, 0.5, float_allowance(qt, rt, 0.0), &b);
   if (rc != DFGT_OK) return rc;
   const size_t need = std::max<size_t>({prune.size(), base.size(), far.size(), loc.size(), f2l.size(), 1});
   ctx->cap_lists = std::max(ctx->cap_lists, need);

@@ -201,6 +201,7 @@ struct TravBuffers {
   float* ku;        // [frontier] lower bound on K(d^u) of each pending pair
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums
+  float exp_err;    // exponent error the expanded form of exact sums may take (eps_fp / 4)
   double fix_scale; // 2^62 / |R|
   double inv_fix;   // 1 / fix_scale
   float fix_scale_dn;  // fix_scale rounded down

@@ -898,7 +898,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   t->pm = pmax_of(d);
   t->P = ipow_c(t->pm, d);
   t->p_limit = (opts && opts->p_max > 0) ? std::min(opts->p_max, t->pm) : t->pm;
-  t->eps_fp = (opts && opts->eps_fp > 0) ? opts->eps_fp : 2e-5;
+  t->eps_fp = (opts && opts->eps_fp > 0) ? opts->eps_fp : 0.0;  // 0: chosen per sum from eps
   {
     const long long bb = opts ? opts->base_block : 0;
     t->base_block = bb > 0 ? bb : bb < 0 ? 0 : kDefaultBaseBlock;

@@ -35,3 +35,21 @@ def test_bad_arguments_rejected(dev):
     # the context stays usable after rejected calls
     G, _ = dfgt.kde_sum(dev, t, t, [0.1], 1e-2)
     assert np.isfinite(G.cpu().numpy()).all()
+
+
+def test_float_allowance_rule(dev):
+    # eps_fp = 0 leaves the float allowance to each sum: 1% of eps within
+    # [2e-5, 1e-4]; eps must exceed it.  An explicit eps_fp on either tree
+    # takes precedence.
+    x = np.random.default_rng(2).random((300, 2)).astype(np.float32)
+    t = dfgt.Tree(dev, to_cuda(x))
+    dfgt.kde_sum(dev, t, t, [0.1], 1e-4)       # allowance 2e-5
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.kde_sum(dev, t, t, [0.1], 1.5e-5)  # below the 2e-5 floor
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.kde_sum_loo(dev, t, [0.1], 1.5e-5)
+    te = dfgt.Tree(dev, to_cuda(x), eps_fp=5e-4)
+    with pytest.raises(dfgt.DFGTError, match="EINVAL"):
+        dfgt.kde_sum(dev, t, te, [0.1], 4e-4)
+    G, _ = dfgt.kde_sum(dev, t, te, [0.1], 1e-3)
+    assert np.isfinite(G.cpu().numpy()).all()
