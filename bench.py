@@ -34,10 +34,12 @@ from paper_1102_2878_gb300 import datagen  # noqa: E402
 METRIC = "effective query-ref pairs/s (|Q|·|R|/time) at ε=1e-2, DFGT vs GPU brute force"
 UNIT = "pairs/s"
 DEFAULT_WORKLOAD = "kde3d_n2e5_sweep10"
-# GB300: 152 SMs.  A loop of nothing but ex2.approx and adds on every SM
-# retired 52.6 ex2 per clock per SM at 2070 MHz, more than a 32-wide unit
-# can, so the roofline takes 64 ex2 per clock per SM (16 per sub-partition)
-SM_COUNT, SFU_EX2_PER_CLK_PER_SM = 152, 64
+# GB300: 152 SMs.  A loop of eight independent ex2.approx chains per thread
+# on every SM retired 31.4 ex2 per clock per SM at the sampled 1987 MHz, and
+# the profiler puts the exact-sum kernel's XU pipe at 43% while it runs 12.8
+# ex2 per clock per SM: the unit takes 32 ex2 per clock per SM (8 per
+# sub-partition)
+SM_COUNT, SFU_EX2_PER_CLK_PER_SM = 152, 32
 
 
 def dist_env():
@@ -135,7 +137,7 @@ def measured_peaks():
 # DRAM bytes read + written by one k_base launch (one launch per step at the
 # default options) of a workload, from an ncu capture of
 # `bench.py --steps 1 --warmup 1 --only-dfgt` with the current kernel.
-K_BASE_TRAFFIC = {"kde3d_n2e5_sweep10": 40034304 + 256}
+K_BASE_TRAFFIC = {"kde3d_n2e5_sweep10": 40074752}
 
 
 def cpu_oracle_rate(x, hs, target_s, seed=0):
@@ -295,8 +297,8 @@ def run_dfgt(args, rank, world, local):
     roof = {"bound": "alu", "kernel": "k_base (DFGTBase exact sums)", "achieved": achieved,
             "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
             "traffic": K_BASE_TRAFFIC.get(args.workload),
-            "peak_source": f"one ex2 per interaction: 152 SMs x 64 ex2/clk x {sm_clk:.0f} MHz (unit counts; "
-                           "an ex2+add loop alone measured 52.6 ex2/clk/SM)"}
+            "peak_source": f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz (measured: "
+                           "independent ex2.approx chains retired 31.4 ex2/clk/SM)"}
     cpu_rate, cpu_desc, cores = (None, None, None)
     if not args.no_cpu_baseline:
         cpu_rate, cpu_desc, cores, _ = cpu_oracle_rate(x, hs, args.cpu_seconds)
