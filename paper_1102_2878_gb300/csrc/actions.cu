@@ -9,6 +9,7 @@
 // p_max = 1 and uses the order-0 kernels at the end of the file.  Sums of
 // the exact and far-field parts go to a float64 per-query accumulator;
 // local moments are float64 per (bandwidth, query node).
+#include "base_hd_forms.cuh"
 #include "internal.hpp"
 
 namespace dfgt {
@@ -715,7 +716,8 @@ struct HdShape {
 template <int DM>
 __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                                 const int* __restrict__ ksorted, int n,
-                                                const float* __restrict__ c2v, double* __restrict__ gacc) {
+                                                const float* __restrict__ c2v, const float* __restrict__ inv2h2_up,
+                                                double* __restrict__ gacc, float exp_err) {
   constexpr int TP = HdShape<DM>::TP, PS = HdShape<DM>::PS;
   __shared__ __align__(16) float sT[kWarpsPerBlock][TP * PS];
   __shared__ int sOff[kWarpsPerBlock][kEntryChunk + 1], sRb[kWarpsPerBlock][kEntryChunk];
@@ -738,6 +740,8 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
     qbeg = Q.beg[q];
     qcnt = Q.cnt[q];
   }
+  float rho2 = 0.f, far2 = 0.f;  // for the choice of form (base_hd_forms.cuh)
+  if (lane < m) hd_entry_bounds(Q, R, key % Q.nn, rsorted[i0 + lane] & kNodeMask, rho2, far2);
   const int keyp = __shfl_up_sync(FULL, key, 1);
   const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
   float* T = sT[wib];
@@ -765,6 +769,18 @@ __global__ void __launch_bounds__(kT) k_base_hd(TreeView Q, TreeView R, const in
     const float c2 = c2v[hidx];
     const float2 c2p = make_float2(c2, c2);
     const bool loo = __any_sync(FULL, lane >= t && lane < e && self);
+    {
+      // a run of the tensor form is summed by k_base_hd_tc
+      const float rq2 = __shfl_sync(FULL, rho2, t);
+      const float f2 = __uint_as_float(
+          __reduce_max_sync(FULL, (lane >= t && lane < e) ? __float_as_uint(far2) : 0u));
+      HtScale sc;
+      if (hd_tensor_form(Q.d, ht_chunks(DM), rq2, f2, inv2h2_up[hidx], c2, loo, qn, exp_err, &sc)) {
+        __syncwarp();
+        t = e;
+        continue;
+      }
+    }
     __syncwarp();
     for (int qs = 0; qs < qn; qs += 32 * kHdQBlocks) {
       const int nblk = min(kHdQBlocks, (qn - qs + 31) / 32);
@@ -1595,11 +1611,14 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
     const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (Q.dp <= 8)
-      k_base_hd<8><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc);
+      k_base_hd<8><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.exp_err);
     else if (Q.dp <= 16)
-      k_base_hd<16><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc);
+      k_base_hd<16><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.exp_err);
     else
-      k_base_hd<32><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.gacc);
+      k_base_hd<32><<<g, kT, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.exp_err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ++*launches;
+    return launch_base_hd_tc(Q, R, b, rsorted, ksorted, n, s, launches);
   }
   ++*launches;
   return cudaGetLastError();

@@ -237,6 +237,9 @@ struct BaseScratch {
 };
 cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                         const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
+// base_hd_tc.cu: the tensor-core runs of a sorted base list (D >= 6).
+cudaError_t launch_base_hd_tc(const TreeView& Q, const TreeView& R, const TravBuffers& b, const int* rsorted,
+                              const int* ksorted, int n, cudaStream_t s, long long* launches);
 cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                             const Action* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,

@@ -62,3 +62,35 @@ def test_forms_partition_the_interactions(dev):
     assert std["base_expanded"] < 0.01 * std["base_interactions"]
     rel = (G - Gd).abs() / Gd
     assert rel.max().item() <= 2e-2
+
+
+@pytest.mark.parametrize("D,side,h,efp", [(8, 0.2, 0.3, 0.0), (12, 0.15, 0.3, 0.0), (16, 0.1, 0.25, 0.0),
+                                          (16, 1.0, 0.5, 1e-3), (32, 0.05, 0.2, 0.0), (32, 1.0, 0.9, 1e-3)])
+def test_whole_node_exact_sum_high_dimension(dev, orc, D, side, h, efp):
+    # D >= 6: one base entry (root, root) whose expansion bound puts it in
+    # the tensor-core form; each term's error is then at most eps_fp / 4
+    # (plus ex2.approx's 2^-21 and the float32 summation)
+    rng = np.random.default_rng(60 + D)
+    X = (side * rng.random((2000, D))).astype(np.float32)
+    t = dfgt.Tree(dev, to_cuda(X), eps_fp=efp)
+    G = dfgt.apply_pairs(dev, t, t, [0], [0], [_lib.ACT_BASE], [1], h).cpu().numpy()
+    want = orc.naive_kde(X.astype(np.float64), X.astype(np.float64), h)
+    rel = np.abs(G - want) / want
+    allowance = efp if efp > 0 else 2e-5
+    assert rel.max() <= allowance / 4 + 2e-6, (D, rel.max())
+
+
+@pytest.mark.parametrize("eps", [1e-2, 1e-3])
+def test_high_dimension_traversal_with_tensor_form(dev, orc, eps):
+    x = datagen.manifold_points(6000, 16, 4, 0.01, seed=12)
+    hs = [0.3, 0.6, 1.0]
+    t = dfgt.Tree(dev, to_cuda(x), eps_fp=2.5e-4 if eps == 1e-2 else 0.0)
+    G, st = dfgt.kde_sum(dev, t, t, hs, eps)
+    if eps == 1e-2:
+        assert st["base_expanded"] > 0
+    G = G.cpu().numpy()
+    x64 = x.astype(np.float64)
+    for i, h in enumerate(hs):
+        ref = orc.naive_kde(x64, x64, h)
+        rel = np.abs(G[i] - ref) / ref
+        assert rel.max() <= eps, (h, rel.max())
