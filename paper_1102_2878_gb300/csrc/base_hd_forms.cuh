@@ -9,8 +9,8 @@
 // W_q = -2c q~, B_r = c|r~|^2.  The tensor cores sum, per 16 queries x 8
 // references, the products Wh rh + Wh rl + Wl rh of the float16 splits
 // W_q 2^a = Wh + Wl and r~ 2^b = rh + rl per coordinate onto the C operand
-// B_r 2^(a+b), in KC chained m16n8k16 steps (K = 3D padded to 16 KC); the
-// result times 2^-(a+b) is the exponent less A_q.  The scales bring both
+// B_r 2^(a+b), in KC chained mma steps (three parts of DM padded
+// coordinates); the result times 2^-(a+b) is the exponent less A_q.  The scales bring both
 // operands' largest entries just below 2^13, so only entries below 2^-3
 // have subnormal lo parts, whose error (2^-25) moves a product by at most
 // 2^-38 of the largest one.
@@ -35,8 +35,9 @@ namespace dfgt {
 namespace {
 
 constexpr int kHtMinQ = 16;  // the tensor tile is 16 queries high
-// chained k16 mma steps for rows of DM coordinates (3 entries each)
-__host__ __device__ constexpr int ht_chunks(int dm) { return (3 * dm + 15) / 16; }
+// chained mma steps for DM (8, 16 or 32) padded coordinates: three parts
+// (Wh rh, Wh rl, Wl rh), each one m16n8k8 (DM = 8) or DM/16 m16n8k16
+__host__ __device__ constexpr int ht_chunks(int dm) { return dm == 8 ? 3 : 3 * (dm / 16); }
 constexpr float kHtUnit = 5.9604645e-08f;  // u = 2^-24
 
 // Squared radius of query box q about its centre and squared distance from

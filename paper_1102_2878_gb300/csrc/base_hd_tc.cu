@@ -4,15 +4,18 @@
 //
 // One warp per block walks the same 32-entry chunks of the sorted base
 // list as k_base_hd and sums the runs (one bandwidth, one query node) that
-// take the tensor form; k_base_hd sums the others.  Per run the warp
-// stages up to 64 queries as float16 rows (Wh, Wh, Wl per coordinate,
-// K = 3D entries padded to 16 KC) and then the references a tile of 64 at
-// a time, one lane per reference, as float16 columns (rh, rl, rh) written
-// in the order of the mma B fragment (the eight bytes a lane loads for one
-// chained step are adjacent), with B_r 2^(a+b) beside them.  Each step of 8
-// references runs KC chained m16n8k16 mma per 16 queries; every lane takes
-// ex2 of its four results (times 2^-(a+b)) and adds them to the two query
-// rows it holds.  Padding references carry C = -1e30 and add 0.
+// take the tensor form; k_base_hd sums the others.  The contraction is
+// split by parts: Wh . rh + Wh . rl + Wl . rh, each a dot product over the
+// DM (padded) coordinates, so a query row stores Wh and Wl (DM float16
+// each) and a reference column rh and rl, both converted two coordinates
+// at a time.  Per run the warp stages up to 64 queries, then the
+// references a tile of 64 at a time, one lane per reference, written in
+// the order of the mma B fragment (the bytes a lane loads for one step are
+// adjacent), with B_r 2^(a+b) beside them.  Each step of 8 references runs
+// 3 DM/16 chained m16n8k16 mma (3 m16n8k8 for DM = 8) per 16 queries;
+// every lane takes ex2 of its four results (times 2^-(a+b)) and adds them
+// to the two query rows it holds.  Padding references carry C = -1e30 and
+// add 0.
 #include <cuda_fp16.h>
 
 #include "base_hd_forms.cuh"
@@ -24,24 +27,32 @@ namespace {
 constexpr int kEntryChunkHt = 32;  // sorted entries per warp (as k_base_hd)
 constexpr int kNodeMaskHt = (1 << 27) - 1;
 constexpr int kHtQ = 64;           // queries staged at a time
-constexpr int kHtTile = 64;        // references per staged tile
+constexpr int kHtTile = 128;       // references per staged tile
 constexpr int kHtSteps = kHtTile / 8;
 constexpr float kHtPad = -1.0e30f;
 
 template <int DM>
 struct HtShape {
-  static constexpr int KC = ht_chunks(DM);      // chained k16 steps
-  static constexpr int W = 8 * KC;               // 32-bit words of a row or column
+  static constexpr bool K8 = DM == 8;            // m16n8k8 steps, else m16n8k16
+  static constexpr int NCH = K8 ? 1 : DM / 16;   // mma steps per part
+  static constexpr int HW = DM / 2;              // 32-bit words of one part (DM float16)
+  static constexpr int KW = K8 ? 4 : 8;          // words of one step's column
+  static_assert(DM == 8 || DM == 16 || DM == 32, "DM is 8, 16 or 32");
+  static_assert(3 * NCH == ht_chunks(DM), "the chained steps of the error bound");
 };
 
-__device__ __forceinline__ unsigned pack_h2(__half lo, __half hi) {
-  return (unsigned)__half_as_ushort(lo) | ((unsigned)__half_as_ushort(hi) << 16);
+__device__ __forceinline__ unsigned h2_bits(__half2 h) {
+  unsigned u;
+  memcpy(&u, &h, sizeof u);
+  return u;
 }
 
-// v = hi + lo + err with |err| <= 2^-22 |v| while lo is normal
-__device__ __forceinline__ void split_h(float v, __half& hi, __half& lo) {
-  hi = __float2half_rn(v);
-  lo = __float2half_rn(v - __half2float(hi));
+// (v.x, v.y) = hi + lo + err per element, |err| <= 2^-22 |v| while lo is normal
+__device__ __forceinline__ void split_h2(float2 v, unsigned& hi, unsigned& lo) {
+  const __half2 h = __float22half2_rn(v);
+  const float2 b = __half22float2(h);
+  hi = h2_bits(h);
+  lo = h2_bits(__float22half2_rn(make_float2(v.x - b.x, v.y - b.y)));
 }
 
 // 2^e as a float, |e| <= 126
@@ -54,6 +65,12 @@ __device__ __forceinline__ void mma16(const unsigned* a, uint2 b, float& d0, flo
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
 }
 
+__device__ __forceinline__ void mma8(const unsigned* a, unsigned b, float& d0, float& d1, float& d2, float& d3) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+      : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
+      : "r"(a[0]), "r"(a[1]), "r"(b));
+}
+
 // Kahan step of a float32 running sum.
 __device__ __forceinline__ void kahan_add_ht(float& S, float& C, float v) {
   const float y = v - C;
@@ -62,17 +79,35 @@ __device__ __forceinline__ void kahan_add_ht(float& S, float& C, float v) {
   S = t;
 }
 
+// DM coordinates of a tree row (dp floats, zero-padded, 16-byte aligned) minus the centre
+template <int DM>
+__device__ __forceinline__ void load_centred(const float* __restrict__ p, int dp, const float* __restrict__ m,
+                                             float* v) {
+#pragma unroll
+  for (int k4 = 0; k4 < DM / 4; ++k4) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * k4 < dp) a = __ldg(reinterpret_cast<const float4*>(p) + k4);
+    v[4 * k4] = a.x - m[4 * k4];
+    v[4 * k4 + 1] = a.y - m[4 * k4 + 1];
+    v[4 * k4 + 2] = a.z - m[4 * k4 + 2];
+    v[4 * k4 + 3] = a.w - m[4 * k4 + 3];
+  }
+}
+
 template <int DM>
 __global__ void __launch_bounds__(32)
     k_base_hd_tc(TreeView Q, TreeView R, const int* __restrict__ rsorted, const int* __restrict__ ksorted, int n,
                  const float* __restrict__ c2v, const float* __restrict__ inv2h2_up, double* __restrict__ gacc,
                  unsigned long long* __restrict__ tc_ctr, float exp_err) {
-  constexpr int KC = HtShape<DM>::KC, W = HtShape<DM>::W;
-  // B fragments: step s, chained step c, lane l = 4g + t holds k rows 2t,
-  // 2t+1 (x) and 2t+8, 2t+9 (y) of reference column g
-  __shared__ __align__(16) uint2 sF[kHtSteps][KC][32];
+  using SH = HtShape<DM>;
+  constexpr int NCH = SH::NCH, HW = SH::HW, KW = SH::KW;
+  // B fragments: step s, part (rh, rl), mma step c, then the words of lane
+  // l = 4g + t: k rows 2t, 2t+1 (and 2t+8, 2t+9 for k16) of reference column g
+  __shared__ __align__(16) unsigned sF[kHtSteps][2][NCH][32 * KW / 4];
   __shared__ __align__(16) float sB[kHtTile];
-  __shared__ __align__(16) unsigned sQh[kHtQ][W];
+  // query rows: Wh, then Wl, then 4 words of padding (the A-fragment loads
+  // of the 8 rows g then fall on distinct banks)
+  __shared__ __align__(16) unsigned sQh[kHtQ][2 * HW + 4];
   __shared__ float sA[kHtQ];
   __shared__ float2 sAcc[kHtQ];
   __shared__ float sM[DM];
@@ -125,9 +160,8 @@ __global__ void __launch_bounds__(32)
     return tot;
   };
 
-  // entries past 3D stay zero; rows of padding queries start zero
-  for (int i = lane; i < kHtSteps * KC * 32; i += 32) (&sF[0][0][0])[i] = make_uint2(0u, 0u);
-  for (int i = lane; i < kHtQ * W; i += 32) (&sQh[0][0])[i] = 0u;
+  // rows of padding queries start zero (their sums are dropped)
+  for (int i = lane; i < kHtQ * (2 * HW + 4); i += 32) (&sQh[0][0])[i] = 0u;
   __syncwarp();
 
   int t = 0, e = run_end(0), ts = 0, qs = 0, j0 = 0;
@@ -149,7 +183,7 @@ __global__ void __launch_bounds__(32)
           __reduce_max_sync(FULL, (lane >= t && lane < e) ? __float_as_uint(far2) : 0u));
       const bool self_run = __any_sync(FULL, lane >= t && lane < e && self);
       HtScale sc;
-      if (!hd_tensor_form(d, KC, rq2, f2, inv2h2_up[hidx], c2r, self_run, qn, exp_err, &sc)) {
+      if (!hd_tensor_form(d, ht_chunks(DM), rq2, f2, inv2h2_up[hidx], c2r, self_run, qn, exp_err, &sc)) {
         // summed by k_base_hd: on to the next run
         if (e >= m) break;
         t = e;
@@ -173,28 +207,22 @@ __global__ void __launch_bounds__(32)
       // a new query block: rows (Wh, Wh, Wl per coordinate) and A_q
       qcnt_blk = min(kHtQ, qn - qs);
       for (int qi = lane; qi < qcnt_blk; qi += 32) {
-        const float* qp = Q.pts + (size_t)(qb + qs + qi) * Q.dp;
-        __half hk[16 * KC];
-#pragma unroll
-        for (int i = 0; i < 16 * KC; ++i) hk[i] = __ushort_as_half((unsigned short)0);
+        float v[DM];
+        load_centred<DM>(Q.pts + (size_t)(qb + qs + qi) * Q.dp, Q.dp, sM, v);
         float a2 = 0.f;
+        unsigned wh[HW], wl[HW];
 #pragma unroll
-        for (int k = 0; k < DM; ++k) {
-          if (k < d) {
-            const float tqk = __ldg(qp + k) - sM[k];
-            a2 = fmaf(tqk, tqk, a2);
-            __half hi, lo;
-            split_h(-2.f * c2r * tqk * sw, hi, lo);
-            hk[3 * k] = hi;
-            hk[3 * k + 1] = hi;
-            hk[3 * k + 2] = lo;
-          }
+        for (int k = 0; k < DM; k += 2) {
+          a2 = fmaf(v[k], v[k], a2);
+          a2 = fmaf(v[k + 1], v[k + 1], a2);
+          split_h2(make_float2(-2.f * c2r * v[k] * sw, -2.f * c2r * v[k + 1] * sw), wh[k / 2], wl[k / 2]);
         }
         uint4* row = reinterpret_cast<uint4*>(&sQh[qi][0]);
 #pragma unroll
-        for (int v = 0; v < W / 4; ++v)
-          row[v] = make_uint4(pack_h2(hk[8 * v], hk[8 * v + 1]), pack_h2(hk[8 * v + 2], hk[8 * v + 3]),
-                              pack_h2(hk[8 * v + 4], hk[8 * v + 5]), pack_h2(hk[8 * v + 6], hk[8 * v + 7]));
+        for (int w = 0; w < HW / 4; ++w) {
+          row[w] = make_uint4(wh[4 * w], wh[4 * w + 1], wh[4 * w + 2], wh[4 * w + 3]);
+          row[HW / 4 + w] = make_uint4(wl[4 * w], wl[4 * w + 1], wl[4 * w + 2], wl[4 * w + 3]);
+        }
         sA[qi] = c2r * a2;
         sAcc[qi] = make_float2(0.f, 0.f);
       }
@@ -208,9 +236,9 @@ __global__ void __launch_bounds__(32)
       for (int i = 0; i < kHtTile / 32; ++i) {
         const int j = lane + 32 * i;
         if (j < nst * 8) {
-          __half hk[16 * KC];
+          unsigned rh[HW], rl[HW];
 #pragma unroll
-          for (int q = 0; q < 16 * KC; ++q) hk[q] = __ushort_as_half((unsigned short)0);
+          for (int w = 0; w < HW; ++w) rh[w] = rl[w] = 0u;
           float cb = kHtPad;
           if (j < tn) {
             const int J = j0 + j;
@@ -224,29 +252,36 @@ __global__ void __launch_bounds__(32)
             } else {
               while (sOff[ts][u + 1] <= J) ++u;
             }
-            const float* rp = R.pts + (size_t)(sRb[ts][u] + J - sOff[ts][u]) * R.dp;
+            float v[DM];
+            load_centred<DM>(R.pts + (size_t)(sRb[ts][u] + J - sOff[ts][u]) * R.dp, R.dp, sM, v);
             float b2 = 0.f;
 #pragma unroll
-            for (int k = 0; k < DM; ++k) {
-              if (k < d) {
-                const float rk = __ldg(rp + k) - sM[k];
-                b2 = fmaf(rk, rk, b2);
-                __half hi, lo;
-                split_h(rk * sr, hi, lo);
-                hk[3 * k] = hi;
-                hk[3 * k + 1] = lo;
-                hk[3 * k + 2] = hi;
-              }
+            for (int k = 0; k < DM; k += 2) {
+              b2 = fmaf(v[k], v[k], b2);
+              b2 = fmaf(v[k + 1], v[k + 1], b2);
+              split_h2(make_float2(v[k] * sr, v[k + 1] * sr), rh[k / 2], rl[k / 2]);
             }
             cb = c2r * b2 * sc_c;
           }
-          // chained step c, pair p of the column: lane 4g + (p mod 4), x for p < 4
+          // part p, mma step c: the column's KW words go to lanes 4g .. 4g+3
+          // (k16: lane t takes words t and t+4); the two 16-byte halves are
+          // written in an order that spreads the warp over the banks
+          const int g8 = j & 7, flip = (g8 >> 2) & 1;
 #pragma unroll
-          for (int c = 0; c < KC; ++c) {
-            uint4* col = reinterpret_cast<uint4*>(&sF[j >> 3][c][(j & 7) * 4]);
-            const __half* h = hk + 16 * c;
-            col[0] = make_uint4(pack_h2(h[0], h[1]), pack_h2(h[8], h[9]), pack_h2(h[2], h[3]), pack_h2(h[10], h[11]));
-            col[1] = make_uint4(pack_h2(h[4], h[5]), pack_h2(h[12], h[13]), pack_h2(h[6], h[7]), pack_h2(h[14], h[15]));
+          for (int p = 0; p < 2; ++p) {
+            const unsigned* w = p == 0 ? rh : rl;
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) {
+              uint4* col = reinterpret_cast<uint4*>(&sF[j >> 3][p][c][g8 * KW]);
+              const unsigned* x = w + KW * c;
+              if constexpr (SH::K8) {
+                col[0] = make_uint4(x[0], x[1], x[2], x[3]);
+              } else {
+                const uint4 h0 = make_uint4(x[0], x[4], x[1], x[5]), h1 = make_uint4(x[2], x[6], x[3], x[7]);
+                col[flip] = flip ? h1 : h0;
+                col[flip ^ 1] = flip ? h0 : h1;
+              }
+            }
           }
           sB[j] = cb;
         }
@@ -272,27 +307,45 @@ __global__ void __launch_bounds__(32)
 
     // this tile against the block's queries, 16 at a time
     const float2 so2 = make_float2(sout, sout);
-    for (int q0 = 0; q0 < qcnt_blk; q0 += 16) {
-      unsigned a[KC][4];
+    auto load_a = [&](int q0, unsigned (&ah)[NCH][4], unsigned (&al)[NCH][4]) {
 #pragma unroll
-      for (int c = 0; c < KC; ++c) {
-        a[c][0] = sQh[q0 + g][8 * c + tq];
-        a[c][1] = sQh[q0 + g + 8][8 * c + tq];
-        a[c][2] = sQh[q0 + g][8 * c + tq + 4];
-        a[c][3] = sQh[q0 + g + 8][8 * c + tq + 4];
+      for (int c = 0; c < NCH; ++c) {
+        ah[c][0] = sQh[q0 + g][KW * c + tq];
+        ah[c][1] = sQh[q0 + g + 8][KW * c + tq];
+        al[c][0] = sQh[q0 + g][HW + KW * c + tq];
+        al[c][1] = sQh[q0 + g + 8][HW + KW * c + tq];
+        if constexpr (!SH::K8) {
+          ah[c][2] = sQh[q0 + g][KW * c + tq + 4];
+          ah[c][3] = sQh[q0 + g + 8][KW * c + tq + 4];
+          al[c][2] = sQh[q0 + g][HW + KW * c + tq + 4];
+          al[c][3] = sQh[q0 + g + 8][HW + KW * c + tq + 4];
+        }
       }
-      const float2* B2 = reinterpret_cast<const float2*>(&sB[0]) + tq;
-      float2 pa = make_float2(0.f, 0.f), pb = make_float2(0.f, 0.f);
-#pragma unroll 2
-      for (int st = 0; st < nst; ++st) {
-        const float2 bc = B2[st * 4];
-        float d0 = bc.x, d1 = bc.y, d2 = bc.x, d3 = bc.y;
+    };
+    // the exponents of one step for the 16 rows held in ah, al: Wh rh + Wh rl + Wl rh onto C
+    auto step = [&](const unsigned (&ah)[NCH][4], const unsigned (&al)[NCH][4], int st, float2 bc,
+                    float2& pa, float2& pb) {
+      float d0 = bc.x, d1 = bc.y, d2 = bc.x, d3 = bc.y;
 #pragma unroll
-        for (int c = 0; c < KC; ++c) mma16(a[c], sF[st][c][lane], d0, d1, d2, d3);
-        const float2 xa = __fmul2_rn(make_float2(d0, d2), so2), xb = __fmul2_rn(make_float2(d1, d3), so2);
-        pa = __fadd2_rn(pa, make_float2(ex2_approx(xa.x), ex2_approx(xa.y)));
-        pb = __fadd2_rn(pb, make_float2(ex2_approx(xb.x), ex2_approx(xb.y)));
+      for (int c = 0; c < NCH; ++c) {
+        if constexpr (SH::K8) {
+          const unsigned bh = sF[st][0][c][lane], bl = sF[st][1][c][lane];
+          mma8(ah[c], bh, d0, d1, d2, d3);
+          mma8(ah[c], bl, d0, d1, d2, d3);
+          mma8(al[c], bh, d0, d1, d2, d3);
+        } else {
+          const uint2 bh = reinterpret_cast<const uint2*>(sF[st][0][c])[lane];
+          const uint2 bl = reinterpret_cast<const uint2*>(sF[st][1][c])[lane];
+          mma16(ah[c], bh, d0, d1, d2, d3);
+          mma16(ah[c], bl, d0, d1, d2, d3);
+          mma16(al[c], bh, d0, d1, d2, d3);
+        }
       }
+      const float2 xa = __fmul2_rn(make_float2(d0, d2), so2), xb = __fmul2_rn(make_float2(d1, d3), so2);
+      pa = __fadd2_rn(pa, make_float2(ex2_approx(xa.x), ex2_approx(xa.y)));
+      pb = __fadd2_rn(pb, make_float2(ex2_approx(xb.x), ex2_approx(xb.y)));
+    };
+    auto row_sums = [&](int q0, float2 pa, float2 pb) {
       float vg = pa.x + pb.x, vh = pa.y + pb.y;  // rows q0 + g and q0 + g + 8
       vg += __shfl_xor_sync(FULL, vg, 1);
       vh += __shfl_xor_sync(FULL, vh, 1);
@@ -310,6 +363,33 @@ __global__ void __launch_bounds__(32)
           sAcc[q0 + g + 8] = acc;
         }
       }
+    };
+    const float2* B2 = reinterpret_cast<const float2*>(&sB[0]) + tq;
+    int q0 = 0;
+    if constexpr (DM <= 16) {
+      // 32 queries a sweep: two row blocks share each step's B fragments
+      for (; q0 + 16 < qcnt_blk; q0 += 32) {
+        unsigned ah[NCH][4], al[NCH][4], eh[NCH][4], el[NCH][4];
+        load_a(q0, ah, al);
+        load_a(q0 + 16, eh, el);
+        float2 pa = make_float2(0.f, 0.f), pb = pa, ra = pa, rb2 = pa;
+#pragma unroll 2
+        for (int st = 0; st < nst; ++st) {
+          const float2 bc = B2[st * 4];
+          step(ah, al, st, bc, pa, pb);
+          step(eh, el, st, bc, ra, rb2);
+        }
+        row_sums(q0, pa, pb);
+        row_sums(q0 + 16, ra, rb2);
+      }
+    }
+    for (; q0 < qcnt_blk; q0 += 16) {
+      unsigned ah[NCH][4], al[NCH][4];
+      load_a(q0, ah, al);
+      float2 pa = make_float2(0.f, 0.f), pb = pa;
+#pragma unroll 2
+      for (int st = 0; st < nst; ++st) step(ah, al, st, B2[st * 4], pa, pb);
+      row_sums(q0, pa, pb);
     }
     if (last_tile) {
       // the block's sums, scaled by 2^A_q, one atomic per query
