@@ -171,7 +171,7 @@ def cpu_oracle_rate(x, hs, target_s, seed=0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    x, hs, eps = datagen.workload(args.workload)
+    x, hs, eps = datagen.workload(args.workload, args.n)
     vals, secs = [], []
     desc, cores = "", 0
     per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
@@ -200,7 +200,7 @@ def run_dfgt(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dfgt.build()
-    x, hs, eps = datagen.workload(args.workload)
+    x, hs, eps = datagen.workload(args.workload, args.n)
     x = replica_points(x, rank)  # independent replica per rank (weak scaling)
     N, D, nh = x.shape[0], x.shape[1], len(hs)
     ctx = dfgt.Context(local)
@@ -255,7 +255,7 @@ def run_dfgt(args, rank, world, local):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": world * N * N * nh / (ms / 1e3), "unit": UNIT,
                               "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
-                              "config": {"workload": args.workload}, "note": "dual-tree steps only"}))
+                              "config": {"workload": args.workload, "N": N}, "note": "dual-tree steps only"}))
         ctx.close()
         return
     # GPU brute force on the same data (the comparison named by the metric)
@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dfgt", "reference"], default="dfgt")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
+    ap.add_argument("--n", type=int, default=None,
+                    help="points drawn from the workload's recipe (default: its own count); for small profiling cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-dfgt", action="store_true",
                     help="time the dual-tree steps only (no brute force, e2e or CPU legs); for profiling")
