@@ -942,7 +942,7 @@ __device__ __forceinline__ void farfield_points(const TreeView& Q, const float* 
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
     const int qi = q0 + lane + 32 * j;
-    if (qi < qn) atomicAdd(&gout[qb + qi], sub != 0.0 ? (double)acc[j] - sub : (double)acc[j]);
+    if (qi < qn) atomicAdd(&gout[qb + qi], (double)acc[j] - sub);
   }
 }
 
