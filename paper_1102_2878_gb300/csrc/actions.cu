@@ -1020,7 +1020,7 @@ struct LocalShape {
 // slice ends.  Each reference is tabulated once per lane (Hermite values
 // h_e((Q.c - r) s), zero beyond the entry's order), and lane (stream,
 // prefix) owns the coefficients of one prefix of the multi-index.
-constexpr int kEntryCost = 32;
+constexpr int kEntryCost = 8;  // measured: 4, 8, 16, 32, 64, 128 -> 0.69, 0.69, 0.70, 0.74, 0.82, 0.96 ms
 template <int D>
 __global__ void __launch_bounds__(kT, 3) k_local(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                                  const int* __restrict__ ksorted,

@@ -94,3 +94,25 @@ def test_high_dimension_traversal_with_tensor_form(dev, orc, eps):
         ref = orc.naive_kde(x64, x64, h)
         rel = np.abs(G[i] - ref) / ref
         assert rel.max() <= eps, (h, rel.max())
+
+
+def test_high_dimension_bichromatic_and_leave_one_out(dev, orc):
+    # D = 8 with the tensor form engaged (eps_fp 1e-3): a separate query set
+    # against the references, and leave-one-out sums over the references
+    # (runs holding a self entry stay on the direct form)
+    rng = np.random.default_rng(77)
+    X = (0.4 * rng.random((5000, 8))).astype(np.float32)
+    Qp = (0.4 * rng.random((1500, 8))).astype(np.float32)
+    hs = [0.4, 0.8]
+    rt = dfgt.Tree(dev, to_cuda(X), eps_fp=1e-3)
+    qt = dfgt.Tree(dev, to_cuda(Qp), eps_fp=1e-3)
+    G, st = dfgt.kde_sum(dev, qt, rt, hs, 1e-2)
+    assert st["base_expanded"] > 0
+    G = G.cpu().numpy()
+    S, sl = dfgt.kde_sum_loo(dev, rt, hs, 1e-2)
+    S = S.cpu().numpy()
+    for i, h in enumerate(hs):
+        ref = orc.naive_kde(Qp.astype(np.float64), X.astype(np.float64), h)
+        assert (np.abs(G[i] - ref) / ref).max() <= 1e-2, h
+        refl = orc.loo_sums(X.astype(np.float64), h)
+        assert (np.abs(S[i] - refl) / refl).max() <= 1e-2, h
