@@ -924,7 +924,7 @@ __device__ __forceinline__ void eval_nested(const float* __restrict__ M, const f
 template <int D, int NQ>
 __device__ __forceinline__ void farfield_points(const TreeView& Q, const float* Ms, const CenterHL* cR,
                                                 float sf, int qb, int qn, int q0, int lane,
-                                                double* __restrict__ gout, double sub) {
+                                                double* __restrict__ gout, float sub) {
   constexpr int PM = pmax_of(D);
   float H[NQ][D][PM];
 #pragma unroll
@@ -942,7 +942,7 @@ __device__ __forceinline__ void farfield_points(const TreeView& Q, const float* 
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
     const int qi = q0 + lane + 32 * j;
-    if (qi < qn) atomicAdd(&gout[qb + qi], (double)acc[j] - sub);
+    if (qi < qn) atomicAdd(&gout[qb + qi], (double)(acc[j] - sub));
   }
 }
 
@@ -965,8 +965,10 @@ __global__ void __launch_bounds__(kFarWarps * 32) k_farfield(TreeView Q, TreeVie
   const float sf = sfv[a.h];
   float* Ms = sM[wib];
   // a summary over a node holding the query itself (leave-one-out sums)
-  // loses its exact self term 1
-  const double sub = (a.p & kSelfFlag) ? 1.0 : 0.0;
+  // loses its exact self term 1 (subtracted in float32: one more rounding
+  // of the value, inside the factor 2 of its rounding allowance; a float64
+  // subtraction per query kept the FP64 pipe at 46%)
+  const float sub = (a.p & kSelfFlag) ? 1.f : 0.f;
   stage_moments<D, PM, P>(R.mnorm + (size_t)a.r * P, R.whalf[a.r] * sf, a.p & kOrderMask, Ms, lane);
   __syncwarp();
   CenterHL cR[D];
