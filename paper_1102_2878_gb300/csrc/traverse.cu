@@ -385,8 +385,10 @@ cudaError_t traverse_d(const TravArgs& A, int* grid, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_traverse<D>, kT, 0);
     if (e != cudaSuccess) return e;
     if (!coop || occ < 1) return cudaErrorNotSupported;
-    // two blocks per SM: more (6 per SM measured) only makes the barriers dearer
-    *grid = sms * (occ < 2 ? occ : 2);
+    // four blocks per SM: 1, 2, 3, 4, 5, 6, 8 measured 1.38, 1.00, 0.92, 0.89,
+    // 1.01, 1.01, 1.01 ms for the bandwidth sweep's traversal (more blocks hide
+    // the gathers' latency until the grid barriers grow dearer)
+    *grid = sms * (occ < 4 ? occ : 4);
   }
   TravArgs a = A;
   void* args[] = {&a};
