@@ -121,13 +121,10 @@ __device__ __forceinline__ void load_point(const float* __restrict__ p, float* v
 // f32x2 step on two interactions.  Each lane holds two queries; for a run
 // of few queries the warp splits into lane groups that share the queries
 // and divide the references.
-constexpr int kEntryChunk = 32;   // entries per warp of the base case
 // One warp per block: the warps' work is uneven (runs of any length), and
 // a block of several warps holds the slots of its finished warps until
 // the slowest is done (one-warp blocks ran the exact sums 2.5% faster).
 constexpr int kBaseWarps = 1;     // warps per block of the base case
-constexpr int kNodeBits = 27;  // node indices stay below 2^27 (checked by the tree build)
-constexpr int kNodeMask = (1 << kNodeBits) - 1;
 constexpr float kFarNeg = -1.0e18f;  // padding point: contributes exp(-huge) = 0
 
 // Counting sort of a pair list by (bandwidth, query node).  Pair and Action

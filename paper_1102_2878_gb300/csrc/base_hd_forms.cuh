@@ -1,8 +1,9 @@
-// base_hd_forms.cuh -- the choice between the two forms of the exact sums
-// (DFGTBase, Section 3.6) for D >= 6, shared by k_base_hd (actions.cu,
-// direct form) and k_base_hd_tc (base_hd_tc.cu, expanded form on the
-// tensor cores): both kernels walk the same sorted entries and take the
-// same decisions from this code, each summing only the runs of its form.
+// base_hd_forms.cuh -- what the exact-sum kernels (DFGTBase, Section 3.6)
+// share: the layout of the sorted base list, and for D >= 6 the choice
+// between the direct form (k_base_hd, actions.cu) and the expanded form on
+// the tensor cores (k_base_hd_tc, base_hd_tc.cu): both kernels walk the
+// same sorted entries and take the same decisions from this code, each
+// summing only the runs of its form.
 //
 // Expanded form about the query box centre m (q~ = q - m, r~ = r - m,
 // c = -log2(e)/(2h^2)): x = A_q + B_r + W_q . r~ with A_q = c|q~|^2,
@@ -33,6 +34,13 @@
 
 namespace dfgt {
 namespace {
+
+// The sorted base list as both kernels read it: warp k takes entries
+// [32k, 32k + 32); an entry's reference node sits in the low kNodeBits bits
+// of its sorted value, its flags above them.
+constexpr int kEntryChunk = 32;
+constexpr int kNodeBits = 27;  // node indices stay below 2^27 (checked by the tree build)
+constexpr int kNodeMask = (1 << kNodeBits) - 1;
 
 constexpr int kHtMinQ = 16;  // the tensor tile is 16 queries high
 // chained mma steps for DM (8, 16 or 32) padded coordinates: three parts

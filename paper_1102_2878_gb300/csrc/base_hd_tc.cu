@@ -24,8 +24,6 @@
 namespace dfgt {
 namespace {
 
-constexpr int kEntryChunkHt = 32;  // sorted entries per warp (as k_base_hd)
-constexpr int kNodeMaskHt = (1 << 27) - 1;
 constexpr int kHtQ = 64;           // queries staged at a time
 constexpr int kHtTile = 128;       // references per staged tile
 constexpr int kHtSteps = kHtTile / 8;
@@ -111,12 +109,12 @@ __global__ void __launch_bounds__(32)
   __shared__ float sA[kHtQ];
   __shared__ float2 sAcc[kHtQ];
   __shared__ float sM[DM];
-  __shared__ int sOff[2][kEntryChunkHt + 1];
-  __shared__ int sRb[2][kEntryChunkHt];
+  __shared__ int sOff[2][kEntryChunk + 1];
+  __shared__ int sRb[2][kEntryChunk];
   const int lane = threadIdx.x;
-  const long i0 = (long)blockIdx.x * kEntryChunkHt;
+  const long i0 = (long)blockIdx.x * kEntryChunk;
   if (i0 >= n) return;
-  const int m = (int)min((long)kEntryChunkHt, n - i0);
+  const int m = (int)min((long)kEntryChunk, n - i0);
   const unsigned FULL = 0xffffffffu;
   const int d = Q.d;
 
@@ -127,8 +125,8 @@ __global__ void __launch_bounds__(32)
   if (lane < m) {
     key = ksorted[i0 + lane];
     const int rv = rsorted[i0 + lane];
-    const int r = rv & kNodeMaskHt;
-    self = ((rv >> 27) & kSelfFlag) != 0;
+    const int r = rv & kNodeMask;
+    self = ((rv >> kNodeBits) & kSelfFlag) != 0;
     const int q = key % Q.nn;
     rb = R.beg[r];
     rn = R.cnt[r];
@@ -417,7 +415,7 @@ __global__ void __launch_bounds__(32)
 cudaError_t launch_base_hd_tc(const TreeView& Q, const TreeView& R, const TravBuffers& b, const int* rsorted,
                               const int* ksorted, int n, cudaStream_t s, long long* launches) {
   if (n <= 0 || Q.d < 6) return cudaSuccess;
-  const int grid = (int)((n + kEntryChunkHt - 1) / kEntryChunkHt);
+  const int grid = (int)((n + kEntryChunk - 1) / kEntryChunk);
   if (Q.dp <= 8)
     k_base_hd_tc<8><<<grid, 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.base_exp, b.exp_err);
   else if (Q.dp <= 16)
