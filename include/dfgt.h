@@ -82,7 +82,8 @@ typedef struct {
   double ms_farfield;           /* device time of every far-field evaluation launch */
   double ms_local;              /* device time of every direct local accumulation launch */
   double ms_f2l;                /* device time of every far-to-local translation launch */
-  long long base_expanded;      /* part of base_interactions summed in the expanded form */
+  long long base_expanded;      /* part of base_interactions summed in the expanded form
+                                   (FMA pipe for D <= 5, tensor cores for D >= 6) */
 } dfgt_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
