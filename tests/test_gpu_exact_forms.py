@@ -64,8 +64,10 @@ def test_forms_partition_the_interactions(dev):
     assert rel.max().item() <= 2e-2
 
 
-@pytest.mark.parametrize("D,side,h,efp", [(8, 0.2, 0.3, 0.0), (12, 0.15, 0.3, 0.0), (16, 0.1, 0.25, 0.0),
-                                          (16, 1.0, 0.5, 1e-3), (32, 0.05, 0.2, 0.0), (32, 1.0, 0.9, 1e-3)])
+@pytest.mark.parametrize("D,side,h,efp", [(6, 0.2, 0.3, 0.0), (7, 0.2, 0.3, 0.0), (7, 1.0, 0.5, 1e-3),
+                                          (8, 0.2, 0.3, 0.0), (12, 0.15, 0.3, 0.0), (16, 0.1, 0.25, 0.0),
+                                          (16, 1.0, 0.5, 1e-3), (20, 0.08, 0.3, 0.0), (32, 0.05, 0.2, 0.0),
+                                          (32, 1.0, 0.9, 1e-3)])
 def test_whole_node_exact_sum_high_dimension(dev, orc, D, side, h, efp):
     # D >= 6: one base entry (root, root) whose expansion bound puts it in
     # the tensor-core form; each term's error is then at most eps_fp / 4
