@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(32)
       new_run = false;
     }
     if (j0 == 0) {
-      // a new query block: rows (Wh, Wh, Wl per coordinate) and A_q
+      // a new query block: rows Wh then Wl (DM float16 each) and A_q
       qcnt_blk = min(kHtQ, qn - qs);
       for (int qi = lane; qi < qcnt_blk; qi += 32) {
         float v[DM];
