@@ -170,6 +170,12 @@ dfgt_status dfgt_cv_scores(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h
 dfgt_status dfgt_cv_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n, int d, const double* h_host, int nh,
                          double* cv, double* dcv_dlogh, double* dcv_dx_dev);
 
+/* The boundary's gradient entry point: the same call, arguments and
+ * results as dfgt_cv_grad (the leave-one-out likelihood score and its
+ * gradients with respect to log h and to every point). */
+dfgt_status dfgt_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n, int d, const double* h_host, int nh,
+                      double* cv, double* dcv_dlogh, double* dcv_dx_dev);
+
 /* Choose the tree options that make a dual-tree sum of these points
  * fastest on this GPU.  No counterpart in the paper (its leaf size is
  * unstated): the leaf size and the exact-sum threshold base_block trade

@@ -74,6 +74,8 @@ SIGNATURES = {
                                C.c_void_p, C.POINTER(Stats)]),
     "dfgt_cv_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_int,
                                C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
+    "dfgt_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_int,
+                            C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_void_p]),
     "dfgt_autotune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(C.c_double), C.c_int,
                                 C.c_double, C.c_int, C.POINTER(Opts), C.POINTER(C.c_double)]),
 }

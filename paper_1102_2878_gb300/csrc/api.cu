@@ -781,4 +781,9 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   return post(ctx, qt, b, G_dev, nullptr);
 }
 
+dfgt_status dfgt_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n, int d, const double* h_host, int nh,
+                      double* cv, double* dcv_dlogh, double* dcv_dx_dev) {
+  return dfgt_cv_grad(ctx, x_dev, n, d, h_host, nh, cv, dcv_dlogh, dcv_dx_dev);
+}
+
 }  // extern "C"

@@ -46,6 +46,8 @@ def test_invalid_arguments_rejected_without_a_device(lib):
     assert lib.dfgt_create(None, 0, None) == 1          # DFGT_EINVAL
     assert lib.dfgt_build(None, None, 0, 0, None, None) == 1
     assert lib.dfgt_sum(None, None, None, None, 0, 0.0, None, None) == 1
+    assert lib.dfgt_grad(None, None, 0, 0, None, 0, None, None, None) == 1
+    assert lib.dfgt_cv_grad(None, None, 0, 0, None, 0, None, None, None) == 1
     lib.dfgt_destroy(None)
     lib.dfgt_tree_destroy(None)
     assert lib.dfgt_last_error(None) == b"null context"
