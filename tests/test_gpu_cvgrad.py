@@ -105,3 +105,23 @@ def test_cv_grad_rejects_bad_arguments(dev):
         dfgt.cv_grad(dev, x[:1], [0.1])
     with pytest.raises(dfgt.DFGTError):
         dfgt.cv_grad(dev, x, [0.0])
+
+
+def test_boundary_name_dfgt_grad_is_the_same_call(dev):
+    import ctypes as C
+
+    import torch
+
+    x = to_cuda(points(700, 3, 41))
+    hs = np.array([0.05, 0.2])
+    cv, dlogh, dx = dfgt.cv_grad(dev, x, hs)
+    cv2, dl2 = np.empty(2), np.empty(2)
+    dx2 = torch.empty_like(dx)
+    dev.order_after_torch()
+    st = dev.lib.dfgt_grad(dev.h, C.c_void_p(x.data_ptr()), 700, 3, hs.ctypes.data_as(C.POINTER(C.c_double)), 2,
+                           cv2.ctypes.data_as(C.POINTER(C.c_double)), dl2.ctypes.data_as(C.POINTER(C.c_double)),
+                           C.c_void_p(dx2.data_ptr()))
+    dev.check(st, "dfgt_grad")
+    torch.cuda.synchronize()
+    assert np.allclose(cv, cv2, rtol=1e-12, atol=0) and np.allclose(dlogh, dl2, rtol=1e-12, atol=1e-15)
+    assert torch.allclose(dx, dx2, rtol=1e-12, atol=1e-15)
