@@ -84,7 +84,7 @@ def test_bound_covers_the_emulated_form():
     log2e = 1.4426950408889634
     worst = 0.0
     for trial in range(400):
-        D = int(rng.choice([6, 8, 12, 16]))
+        D = int(rng.choice([6, 8, 12, 16, 20, 32]))
         h = float(np.exp(rng.uniform(np.log(0.05), np.log(1.0))))
         c = -log2e / (2 * h * h)
         m = f32(rng.random(D))
