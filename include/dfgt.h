@@ -202,7 +202,9 @@ void dfgt_tree_destroy(dfgt_tree* tree);
  * relative error bound eps of Definition 1.2 (Theorem 3.3), by the
  * dual-tree traversal of Section 3.6 (DFGTMain).
  *   h_host : nh finite values > 0 (host); 1 <= nh <= 1024
- *   eps    : 0 < eps < 1
+ *   eps    : 0 < eps < 1, above the trees' float allowance eps_fp (with
+ *            eps_fp = 0 that is 1% of eps within [2e-5, 1e-4], so
+ *            eps > 2e-5); else DFGT_EINVAL
  *   G_dev  : float64 [nh][nq] (device, caller-owned), written in the
  *            caller's original query order; unnormalised sums of Eq. 5
  *   stats  : optional work counters (host), may be NULL
