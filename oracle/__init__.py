@@ -45,6 +45,9 @@ def _load():
     ip = C.POINTER(C.c_int)
     i64 = C.c_int64
     lib.orc_naive_kde.argtypes = [dp, i64, dp, i64, C.c_int, C.c_double, dp]
+    lib.orc_log_naive_kde.argtypes = [dp, i64, dp, i64, C.c_int, C.c_double, dp]
+    lib.orc_num_threads.argtypes = []
+    lib.orc_num_threads.restype = C.c_int
     lib.orc_hermite_functions.argtypes = [C.c_double, C.c_int, dp]
     lib.orc_gauss_volume.argtypes = [C.c_int, C.c_double]
     lib.orc_gauss_volume.restype = C.c_double
@@ -116,6 +119,24 @@ def naive_kde(Q, R, h):
     gp = G.ctypes.data_as(C.POINTER(C.c_double))
     lib.orc_naive_kde(qp, Q.shape[0], rp, R.shape[0], D, float(h), gp)
     return G
+
+
+def log_naive_kde(Q, R, h):
+    """log G(q_i) of Eq. 5 by log-sum-exp with the per-query shift
+    m = min_j ||q_i - r_j||^2 / 2h^2 (finite where G underflows)."""
+    lib = _load()
+    Q, qp = _d(np.atleast_2d(Q))
+    R, rp = _d(np.atleast_2d(R))
+    D = Q.shape[1]
+    assert R.shape[1] == D
+    L = np.empty(Q.shape[0])
+    lib.orc_log_naive_kde(qp, Q.shape[0], rp, R.shape[0], D, float(h), L.ctypes.data_as(C.POINTER(C.c_double)))
+    return L
+
+
+def num_threads() -> int:
+    """Host threads the oracle's parallel loops use."""
+    return int(_load().orc_num_threads())
 
 
 # ---------------------------------------------------------- multi-indices

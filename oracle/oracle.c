@@ -30,6 +30,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXD 32
 #define ORC_INF_ORDER (-1)
@@ -177,6 +180,64 @@ void orc_naive_kde(const double* Q, int64_t nq, const double* R, int64_t nr, int
     }
     G[i] = s + comp;
   }
+}
+
+/* log G(q_i) for the same sum (Eq. 5), for sums that underflow double
+ * precision: with x_j = ||q_i - r_j||^2 / 2h^2 and the per-query shift
+ * m = min_j x_j,
+ *     log G(q_i) = -m + log sum_j exp(-(x_j - m)),
+ * the log-sum-exp form (every shifted term is <= 1 and the nearest one is
+ * exactly 1, so the sum lies in [1, nr] and never underflows).  Direct
+ * differences, Neumaier-compensated sum, log1p of the terms beyond the
+ * first. */
+void orc_log_naive_kde(const double* Q, int64_t nq, const double* R, int64_t nr, int D, double h,
+                       double* logG) {
+  const double inv = 1.0 / (2.0 * h * h);
+#pragma omp parallel for schedule(dynamic, 8)
+  for (int64_t i = 0; i < nq; ++i) {
+    double m = INFINITY;
+    for (int64_t j = 0; j < nr; ++j) {
+      double d2 = 0.0;
+      for (int d = 0; d < D; ++d) {
+        double t = Q[i * D + d] - R[j * D + d];
+        d2 += t * t;
+      }
+      if (d2 * inv < m) m = d2 * inv;
+    }
+    /* sum of exp(-(x_j - m)) minus the one term equal to 1, so that
+     * log(1 + rest) keeps full precision when the rest is small */
+    double s = 0.0, comp = 0.0;
+    int skipped = 0;
+    for (int64_t j = 0; j < nr; ++j) {
+      double d2 = 0.0;
+      for (int d = 0; d < D; ++d) {
+        double t = Q[i * D + d] - R[j * D + d];
+        d2 += t * t;
+      }
+      const double x = d2 * inv;
+      if (!skipped && x == m) {
+        skipped = 1;
+        continue;
+      }
+      double v = exp(-(x - m));
+      double t = s + v;
+      if (fabs(s) >= fabs(v))
+        comp += (s - t) + v;
+      else
+        comp += (v - t) + s;
+      s = t;
+    }
+    logG[i] = -m + log1p(s + comp);
+  }
+}
+
+/* Threads the OpenMP loops above use (1 without OpenMP). */
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------ */
