@@ -134,10 +134,77 @@ def measured_peaks():
         return {}
 
 
-# DRAM bytes read + written by one k_base launch (one launch per step at the
-# default options) of a workload, from an ncu capture of
-# `bench.py --steps 1 --warmup 1 --only-dfgt` with the current kernel.
-K_BASE_TRAFFIC = {"kde3d_n2e5_sweep10": 40073728}
+# DRAM bytes read + written by one exact-sum launch of a workload, from an
+# ncu capture of `bench.py --steps 1 --warmup 1 --only-dfgt`, with the
+# SHA-256 prefix of the kernel's source file at the time of the capture: a
+# figure whose source has changed since is stale and reported as null.
+K_BASE_TRAFFIC = {"kde3d_n2e5_sweep10": ("actions.cu", "", 40073728)}
+FMA_PER_CLK_PER_SM = 128  # FP32 FMA lanes per SM
+
+
+def source_sha(name):
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1102_2878_gb300", "csrc", name)
+    try:
+        with open(path, "rb") as f:
+            return hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def base_traffic(workload):
+    rec = K_BASE_TRAFFIC.get(workload)
+    if not rec:
+        return None
+    name, sha, value = rec
+    return value if sha and source_sha(name) == sha else None
+
+
+def roofline_by_kernel(stats, tinfo, N, D, nh, sm_clk, hbm_gbs):
+    """Achieved fraction of each kernel's bound, from the work counters of
+    the sums and the kernels' live CUDA-event times (means over the timed
+    steps).  Units: exact sums one ex2 per pair interaction; far field,
+    local moments and far-to-local one FMA per series term (|Q| p^D, |R| p^D
+    and p^{2D} per pair); traversal, post pass, level build and moment pass
+    their algorithmic bytes (node boxes and pair records read, sums and
+    coefficients read and written, point rows moved) against HBM."""
+    mean = lambda k: statistics.mean(s[k] for s in stats)  # noqa: E731
+    ex2_peak = SM_COUNT * SFU_EX2_PER_CLK_PER_SM * sm_clk * 1e6
+    fma_peak = SM_COUNT * FMA_PER_CLK_PER_SM * sm_clk * 1e6
+    hbm = hbm_gbs * 1e9
+    dp = D if D <= 2 else (D + 3) // 4 * 4
+    nn = statistics.mean(t["n_nodes"] for t in tinfo)
+    depth = statistics.mean(t["depth"] for t in tinfo)
+    P = tinfo[0]["n_coeff"]
+    out = {}
+
+    def put(kernel, units, unit, ms, bound, peak, peak_unit):
+        if ms is None or ms <= 0 or units <= 0:
+            return
+        rate = units / (ms / 1e3)
+        out[kernel] = {"units_per_step": units, "unit": unit, "ms_per_step": ms, "bound": bound,
+                       "achieved": rate, "peak": peak, "peak_unit": peak_unit, "frac": rate / peak}
+
+    base_name = "k_base" if D <= 5 else "k_base_hd + k_base_hd_tc"
+    put(base_name, mean("base_interactions"), "pair interactions", mean("ms_base"), "alu",
+        ex2_peak, "ex2/s (SFU)")
+    put("k_farfield", mean("farfield_terms"), "series terms |Q| p^D", mean("ms_farfield"), "alu",
+        fma_peak, "FMA/s")
+    put("k_local", mean("local_terms"), "series terms |R| p^D", mean("ms_local"), "alu", fma_peak, "FMA/s")
+    put("k_f2l", mean("f2l_terms"), "coefficient products p^2D", mean("ms_f2l"), "alu", fma_peak, "FMA/s")
+    # traversal: two boxes (2 D floats each) and a 16-byte pair record read per pair
+    put("k_traverse", mean("pairs_visited") * (16 * D + 16), "bytes", mean("ms_classify"), "hbm", hbm,
+        "B/s (measured copy)")
+    # post: per-query accumulators read and sums written, local coefficients read
+    put("k_post", nh * N * 16 + nh * nn * P * 8, "bytes", mean("ms_post"), "hbm", hbm, "B/s (measured copy)")
+    # level build: every level reads and writes each point row and its index
+    put("k_build_levels", depth * N * (2 * dp * 4 + 8), "bytes",
+        statistics.mean(t["ms_levels"] for t in tinfo), "hbm", hbm, "B/s (measured copy)")
+    # moment pass: points read once; float64 moments and float32 copies written per node
+    put("k_moments", N * dp * 4 + nn * P * 12, "bytes", statistics.mean(t["ms_moments"] for t in tinfo),
+        "hbm", hbm, "B/s (measured copy)")
+    return out
 
 
 def cpu_oracle_rate(x, hs, target_s, seed=0):
@@ -163,7 +230,7 @@ def cpu_oracle_rate(x, hs, target_s, seed=0):
         per_query = dt / len(sel)
         batch = int(max(64, min(len(x) - done, (target_s - spent) / max(per_query, 1e-9))))
     pairs = done * len(x) * len(hs)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.num_threads()
     desc = f"{done} of {len(x)} queries x all {len(x)} references x {len(hs)} bandwidths, {spent:.1f} s"
     return pairs / spent, desc, cores, spent
 
@@ -209,12 +276,14 @@ def run_dfgt(args, rank, world, local):
     torch.cuda.synchronize()
 
     ev_build = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    tinfo = []
 
     def step():
         ev_build[0].record(ctx.stream)
         tree = dfgt.Tree(ctx, pts)
         ev_build[1].record(ctx.stream)
         G, st = dfgt.kde_sum(ctx, tree, tree, hs, eps)
+        tinfo.append(tree.info())
         tree.close()
         st["ms_build"] = ev_build[0].elapsed_time(ev_build[1])
         return G, st
@@ -242,6 +311,7 @@ def run_dfgt(args, rank, world, local):
         times.append(e0.elapsed_time(e1))
         stats.append(st)
     launches = ctx.launch_count() - launches0
+    tinfo = tinfo[-args.steps:]
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = max_over_ranks(statistics.mean(times), world)
@@ -271,7 +341,8 @@ def run_dfgt(args, rank, world, local):
         e1.synchronize()
         bf_ms.append(e0.elapsed_time(e1))
     bf = statistics.mean(bf_ms)
-    rel = ((G - Gb).abs() / Gb).max().item()
+    ok = Gb > 1e-30
+    rel = ((G - Gb).abs()[ok] / Gb[ok]).max().item()
 
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
     xh = torch.from_numpy(x).pin_memory().numpy()
@@ -296,7 +367,7 @@ def run_dfgt(args, rank, world, local):
     achieved = inter / (base_ms / 1e3) if base_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": "k_base (DFGTBase exact sums)", "achieved": achieved,
             "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
-            "traffic": K_BASE_TRAFFIC.get(args.workload),
+            "traffic": base_traffic(args.workload),
             "peak_source": f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz (measured: "
                            "independent ex2.approx chains retired 31.4 ex2/clk/SM)"}
     cpu_rate, cpu_desc, cores = (None, None, None)
@@ -324,6 +395,7 @@ def run_dfgt(args, rank, world, local):
                  "base_pairs": mean("n_base"), "base_interactions": inter,
                  "base_expanded": mean("base_expanded"), "rounds": mean("rounds")},
         "roofline": roof,
+        "roofline_by_kernel": roofline_by_kernel(stats, tinfo, N, D, nh, sm_clk, peaks.get("hbm_gbs", 6800.0)),
         "cpu_baseline": None if cpu_rate is None else
         {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cpu_desc},
         "e2e": {"value": pairs_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),

@@ -84,6 +84,11 @@ typedef struct {
   double ms_f2l;                /* device time of every far-to-local translation launch */
   long long base_expanded;      /* part of base_interactions summed in the expanded form
                                    (FMA pipe for D <= 5, tensor cores for D >= 6) */
+  long long farfield_terms;     /* sum over far-field pairs of |Q| p^D (terms evaluated) */
+  long long local_terms;        /* sum over direct local pairs of |R| p^D (terms accumulated) */
+  long long f2l_terms;          /* sum over far-to-local pairs of p^{2D} (coefficient products) */
+  long long log_queries;        /* dfgt_sum_log: (bandwidth, query) pairs summed in log space */
+  double ms_log;                /* dfgt_sum_log: device time of the log-space pass */
 } dfgt_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
@@ -105,6 +110,19 @@ void dfgt_destroy(dfgt_ctx* ctx);
 /* Number of CUDA kernels this context has launched since it was created
  * (tree builds, sums, brute force); -1 for a NULL context. */
 long long dfgt_launch_count(const dfgt_ctx* ctx);
+
+/* Test switch for the error path of the bounded device-side waits (no
+ * counterpart in the paper).  The tree build and the traversal each run as
+ * one cooperative launch whose blocks meet at grid barriers; every wait
+ * there polls at most 2^25 times (about a second), then the block records a
+ * timeout in the call's status word and returns, and the call returns
+ * DFGT_ETIMEOUT.  With on = 1 every such barrier of this context waits for
+ * one arrival more than the grid has and gives up after 4096 polls, so each
+ * block leaves at its first barrier and dfgt_build / dfgt_sum return
+ * DFGT_ETIMEOUT within milliseconds, with no kernel left running and the
+ * context still usable.  on = 0 restores the normal waits.  Nothing traps or
+ * faults; other values of `on` give DFGT_EINVAL. */
+dfgt_status dfgt_test_wait_timeout(dfgt_ctx* ctx, int on);
 
 /* Message of the last failure on this context ("" if none).  The string
  * belongs to the context and lives until the next call on it. */
@@ -209,10 +227,30 @@ void dfgt_tree_destroy(dfgt_tree* tree);
  *            caller's original query order; unnormalised sums of Eq. 5
  *   stats  : optional work counters (host), may be NULL
  * The guarantee holds for every query whose exact sum is above ~1e-30
- * (float32 range of the exact leaf sums). */
+ * (float32 range of the exact leaf sums); dfgt_sum_log extends it to every
+ * query. */
 dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree,
                      const double* h_host, int nh, double eps, double* G_dev,
                      dfgt_stats* stats);
+
+/* dfgt_sum with log G beside G, so that the guarantee of Definition 1.2
+ * holds for every query, including queries whose sum (Eq. 5) lies below
+ * the float32 or even the float64 range (far from every reference, small
+ * h, large D).  Runs dfgt_sum, then every (bandwidth, query) whose estimate
+ * is below 1e-20 is summed again in log space: with x_j = |q - r_j|^2/2h^2
+ * and the shift m = min_j x_j, log G = -m + log sum_j exp(-(x_j - m)),
+ * from a depth-first walk of the reference tree with double-float squared
+ * distances; nodes whose every point is exp(-T) below the nearest one,
+ * T = log(|R| / (eps/4)) + 1, are skipped (at most eps/4 of G in all).
+ *   G_dev    : float64 [nh][nq] as for dfgt_sum (underflows to 0 where G does)
+ *   logG_dev : float64 [nh][nq] (device, caller-owned), caller order: log G~
+ * Guarantee: |exp(logG~ - log G) - 1| <= eps for every query.
+ * stats (may be NULL) also receives log_queries and ms_log.  Arguments and
+ * errors as dfgt_sum; DFGT_ECAPACITY if the reference tree is too deep for
+ * the walk's stack (not reachable with the build's 128-level limit). */
+dfgt_status dfgt_sum_log(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree,
+                         const double* h_host, int nh, double eps, double* G_dev, double* logG_dev,
+                         dfgt_stats* stats);
 
 /* Exact G(q_i) by the all-pairs sum of Algorithm 1 (NaiveKDE, without its
  * normalisation) for nh bandwidths; float32 distances and exponentials,
@@ -239,12 +277,15 @@ dfgt_status dfgt_kde_host(dfgt_ctx* ctx, const float* q_host, int64_t nq, const 
  * and loops where an allocation's implicit synchronisation is not
  * acceptable.  The paper has no counterpart; this is a library service.
  *
- * No context is needed and nothing is allocated: the references are split
- * into slices whose float64 partial sums live in a 16 MiB static device
- * array that every GPU loading the library reserves until the process
- * exits.  Limit: nh * nq <= 1,048,576 (partials of two slices must fit);
- * larger requests return DFGT_ECAPACITY before anything is launched.
- *   q_dev, r_dev : float32 [n][d] on the current device (caller-owned)
+ * No context is needed and nothing is allocated.  A query set large enough
+ * to fill the GPU is summed in one pass straight into G_dev; a smaller one
+ * splits the references into slices whose float64 partial sums live in a
+ * 16 MiB static device array that every GPU loading the library reserves
+ * until the process exits.  Limit of the split case: nh * nq <= 1,048,576
+ * (partials of two slices must fit); larger split requests return
+ * DFGT_ECAPACITY before anything is launched.
+ *   q_dev, r_dev : float32 [n][d] on the current device (caller-owned,
+ *                  contiguous rows)
  *   h_host       : nh finite bandwidths > 0 (host), 1 <= nh <= 1024
  *   G_dev        : float64 [nh][nq] on the current device (caller-owned)
  *   cuda_stream  : cudaStream_t to run on (NULL = the legacy default stream)
@@ -252,10 +293,13 @@ dfgt_status dfgt_kde_host(dfgt_ctx* ctx, const float* q_host, int64_t nq, const 
  * stream reaches that point.  All calls share the static array: calls whose
  * kernels overlap on the GPU (different streams, or several host threads)
  * race on it and corrupt each other's results; calls on one stream are
- * ordered and safe.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress, which may load the module); make
- * that first call before any stream capture.  Errors: DFGT_EINVAL for bad
- * arguments, DFGT_ECAPACITY past the limit, DFGT_ECUDA if a launch fails. */
+ * ordered and safe.  The first split call on a device looks up the array's
+ * device address (cudaGetSymbolAddress, which may load the module) and
+ * keeps it for the life of the process; make that first call before any
+ * stream capture, and do not use this entry point after a device reset
+ * (cudaDeviceReset), which leaves the kept address stale.  Errors:
+ * DFGT_EINVAL for bad arguments, DFGT_ECAPACITY past the limit, DFGT_ECUDA
+ * if a launch fails. */
 dfgt_status dfgt_sum_bruteforce_static(const float* q_dev, int64_t nq, const float* r_dev,
                                        int64_t nr, int d, const double* h_host, int nh,
                                        double* G_dev, void* cuda_stream);
@@ -271,8 +315,14 @@ typedef struct {
   int leaf_size;
   int p_max;       /* storage radix of the coefficient tables */
   int n_coeff;     /* p_max^d coefficients per node */
+  double ms_levels;   /* device time of the build up to the end of its level build
+                         (root set-up and the cooperative level launch) */
+  double ms_moments;  /* device time of the moment pass (Eq. far_field_moments and
+                         Lemma 3.5 translations; it runs on the context's side stream) */
 } dfgt_tree_info;
 
+/* Sizes of a tree and the device times of its build; waits for the build's
+ * moment pass to finish. */
 dfgt_status dfgt_tree_get_info(const dfgt_tree* tree, dfgt_tree_info* out);
 
 /* Copy the tree to caller-owned HOST buffers; any pointer may be NULL.

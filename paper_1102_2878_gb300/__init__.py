@@ -69,6 +69,12 @@ class Context:
         """Kernels this context launched so far."""
         return int(self.lib.dfgt_launch_count(self.h))
 
+    def test_wait_timeout(self, on: bool):
+        """Make every grid-barrier wait of this context's cooperative launches
+        run out (on) or restore the normal waits (off); see
+        dfgt_test_wait_timeout in include/dfgt.h."""
+        self.check(self.lib.dfgt_test_wait_timeout(self.h, 1 if on else 0), "dfgt_test_wait_timeout")
+
     def order_after_torch(self):
         torch = _torch()
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
@@ -156,6 +162,22 @@ def kde_sum(ctx: Context, qtree: Tree, rtree: Tree, hs, eps: float, out=None):
                           C.byref(stats))
     ctx.check(st, "dfgt_sum")
     return out, stats.as_dict()
+
+
+def kde_sum_log(ctx: Context, qtree: Tree, rtree: Tree, hs, eps: float):
+    """dfgt_sum_log: G~ and log G~ [nh, nq] float64 (CUDA) with
+    |exp(log G~ - log G) - 1| <= eps for every query, including sums below
+    the float range, and work stats."""
+    torch = _torch()
+    ha, hp = _hs(hs)
+    out = torch.empty((len(ha), qtree.n), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    lout = torch.empty_like(out)
+    stats = _lib.Stats()
+    ctx.order_after_torch()
+    st = ctx.lib.dfgt_sum_log(ctx.h, qtree.h, rtree.h, hp, len(ha), float(eps), C.c_void_p(out.data_ptr()),
+                              C.c_void_p(lout.data_ptr()), C.byref(stats))
+    ctx.check(st, "dfgt_sum_log")
+    return out, lout, stats.as_dict()
 
 
 def kde_sum_loo(ctx: Context, tree: Tree, hs, eps: float, out=None):
@@ -292,17 +314,29 @@ def kde_sum_bruteforce_static(q, r, hs, out, stream=None):
     """Exact G [nh, nq] into a preallocated float64 CUDA tensor `out`,
     without any device allocation by the library (static scratch; see
     dfgt_sum_bruteforce_static in include/dfgt.h for the limit and the
-    rule that overlapping calls race).  Runs on `stream` (a torch CUDA
-    stream, default: the current one) and returns without waiting."""
+    rule that overlapping calls race).  q and r must be contiguous float32
+    CUDA tensors [n, d] on one device (no copy is made: a copy would be an
+    allocation, and one on another stream could be freed while the kernels
+    still read it).  Runs on `stream` (a torch CUDA stream, default: the
+    current one) and returns without waiting."""
     torch = _torch()
     lib = _lib.load()
+    for name, t in (("q", q), ("r", r)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2):
+            raise ValueError(f"{name} must be a float32 CUDA tensor [n, d]")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if q.shape[1] != r.shape[1] or q.device != r.device:
+        raise ValueError("q and r must have the same dimension and device")
     ha, hp = _hs(hs)
-    q = q.contiguous()
-    r = r.contiguous()
-    stream = torch.cuda.current_stream(q.device) if stream is None else stream
-    st = lib.dfgt_sum_bruteforce_static(C.c_void_p(q.data_ptr()), q.shape[0], C.c_void_p(r.data_ptr()),
-                                        r.shape[0], q.shape[1], hp, len(ha), C.c_void_p(out.data_ptr()),
-                                        C.c_void_p(stream.cuda_stream))
+    if not (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+            and tuple(out.shape) == (len(ha), q.shape[0]) and out.device == q.device):
+        raise ValueError("out must be a contiguous float64 CUDA tensor [len(hs), nq] on q's device")
+    with torch.cuda.device(q.device):
+        stream = torch.cuda.current_stream(q.device) if stream is None else stream
+        st = lib.dfgt_sum_bruteforce_static(C.c_void_p(q.data_ptr()), q.shape[0], C.c_void_p(r.data_ptr()),
+                                            r.shape[0], q.shape[1], hp, len(ha), C.c_void_p(out.data_ptr()),
+                                            C.c_void_p(stream.cuda_stream))
     if st != 0:
         raise DFGTError(st, "dfgt_sum_bruteforce_static failed")
     return out

@@ -32,7 +32,9 @@ class Stats(C.Structure):
                 ("ms_traverse", C.c_double), ("ms_classify", C.c_double), ("ms_actions", C.c_double),
                 ("ms_post", C.c_double),
                 ("ms_base", C.c_double), ("ms_farfield", C.c_double), ("ms_local", C.c_double),
-                ("ms_f2l", C.c_double), ("base_expanded", C.c_longlong)]
+                ("ms_f2l", C.c_double), ("base_expanded", C.c_longlong),
+                ("farfield_terms", C.c_longlong), ("local_terms", C.c_longlong),
+                ("f2l_terms", C.c_longlong), ("log_queries", C.c_longlong), ("ms_log", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -41,7 +43,8 @@ class Stats(C.Structure):
 class TreeInfo(C.Structure):
     _fields_ = [("n_points", C.c_int64), ("d", C.c_int), ("n_nodes", C.c_int),
                 ("n_leaves", C.c_int), ("depth", C.c_int), ("leaf_size", C.c_int),
-                ("p_max", C.c_int), ("n_coeff", C.c_int)]
+                ("p_max", C.c_int), ("n_coeff", C.c_int), ("ms_levels", C.c_double),
+                ("ms_moments", C.c_double)]
 
 
 # name -> (restype, argtypes)
@@ -51,11 +54,14 @@ SIGNATURES = {
     "dfgt_set_capacity": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64]),
     "dfgt_last_error": (C.c_char_p, [C.c_void_p]),
     "dfgt_launch_count": (C.c_longlong, [C.c_void_p]),
+    "dfgt_test_wait_timeout": (C.c_int, [C.c_void_p, C.c_int]),
     "dfgt_build": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.POINTER(Opts),
                              C.POINTER(C.c_void_p)]),
     "dfgt_tree_destroy": (None, [C.c_void_p]),
     "dfgt_sum": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int,
                            C.c_double, C.c_void_p, C.POINTER(Stats)]),
+    "dfgt_sum_log": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int,
+                               C.c_double, C.c_void_p, C.c_void_p, C.POINTER(Stats)]),
     "dfgt_sum_bruteforce": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                       C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p]),
     "dfgt_sum_bruteforce_static": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int,

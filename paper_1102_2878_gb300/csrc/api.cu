@@ -300,7 +300,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_traverse(Q, R, b, ctx->frontier[0].as<Pair>(), ctx->frontier[1].as<Pair>(), (int)capf,
                        ctx->list_far.as<Action>(), ctx->list_loc.as<Action>(), ctx->list_f2l.as<Action>(),
-                       ctx->list_base.as<Pair>(), (int)ctx->cap_lists, dctr, dtc, dbar, max_rounds,
+                       ctx->list_base.as<Pair>(), (int)ctx->cap_lists, dctr, dtc, dbar, ctx->wait, max_rounds,
                        ctx->trav_grid, s));
     ++ctx->launches;
     CK(cudaEventRecord(ctx->ev[7], s));
@@ -352,6 +352,9 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     st->n_f2l = lists[3].total;
     st->base_interactions = (long long)hc->base_inter;
     st->base_expanded = (long long)hc->base_exp;
+    st->farfield_terms = (long long)hc->far_terms;
+    st->local_terms = (long long)hc->loc_terms;
+    st->f2l_terms = (long long)hc->f2l_terms;
     st->rounds = rounds;
     st->list_flushes = flushes;
     float ms = 0.f;
@@ -435,7 +438,8 @@ void dfgt_destroy(dfgt_ctx* ctx) {
                     &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,
-                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes, &ctx->cv_buf, &ctx->grad_buf};
+                    &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes, &ctx->cv_buf, &ctx->grad_buf,
+                    &ctx->log_items, &ctx->log_ctr};
   for (DevBuf* b : bufs) b->release();
   if (ctx->tpool) {
     // trees that outlive the context return their arenas in default-stream order
@@ -453,6 +457,16 @@ void dfgt_destroy(dfgt_ctx* ctx) {
 }
 
 long long dfgt_launch_count(const dfgt_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+dfgt_status dfgt_test_wait_timeout(dfgt_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return DFGT_EINVAL;
+  ctx->wait = BarrierCfg{};
+  if (on) {
+    ctx->wait.limit = 4096;  // a few milliseconds of polling
+    ctx->wait.extra = 1;     // one arrival more than the grid has: no block passes
+  }
+  return DFGT_OK;
+}
 
 const char* dfgt_last_error(const dfgt_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
@@ -500,6 +514,40 @@ dfgt_status dfgt_sum(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtr
   ctx->err.clear();
   if (stats) std::memset(stats, 0, sizeof(*stats));
   return run_sum(ctx, qtree, rtree, h_host, nh, eps, G_dev, stats);
+}
+
+dfgt_status dfgt_sum_log(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree, const double* h_host,
+                         int nh, double eps, double* G_dev, double* logG_dev, dfgt_stats* stats) {
+  if (!ctx) return DFGT_EINVAL;
+  if (!logG_dev) return fail(ctx, DFGT_EINVAL, "dfgt_sum_log: need a log G output");
+  dfgt_status rc = dfgt_sum(ctx, qtree, rtree, h_host, nh, eps, G_dev, stats);
+  if (rc != DFGT_OK) return rc;
+  cudaStream_t s = ctx->stream;
+  CK(cudaEventRecord(ctx->ev[4], s));
+  CK(wait_ready(s, rtree));
+  CK(ctx->log_ctr.ensure(64));
+  int* ictr = ctx->log_ctr.as<int>();
+  unsigned long long* nflag = reinterpret_cast<unsigned long long*>(ctx->log_ctr.as<char>() + 8);
+  int* status = ictr + 4;
+  CK(cudaMemsetAsync(ctx->log_ctr.p, 0, 64, s));
+  // dfgt_sum left the bandwidths in ctx->hvals
+  int n_items = 0;
+  CK(launch_log_pass(qtree->view(), rtree->view(), ctx->hvals.as<double>(), nh, eps, kLogFlag, G_dev, logG_dev,
+                     ctx->log_items, ictr, nflag, status, s, &ctx->launches, &n_items));
+  struct { unsigned long long flagged; int status; } h{};
+  CK(cudaMemcpyAsync(&h.flagged, nflag, sizeof(h.flagged), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&h.status, status, sizeof(h.status), cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev[5], s));
+  CK(cudaStreamSynchronize(s));
+  if (h.status & kStOverflow) return fail(ctx, DFGT_ECAPACITY, "dfgt_sum_log: reference tree too deep for the walk");
+  if (stats) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]);
+    stats->ms_log = ms;
+    stats->log_queries = (long long)h.flagged;
+    stats->kernel_launches += 3;
+  }
+  return DFGT_OK;
 }
 
 dfgt_status dfgt_sum_loo(dfgt_ctx* ctx, const dfgt_tree* tree, const double* h_host, int nh, double eps,
@@ -702,6 +750,12 @@ dfgt_status dfgt_tree_get_info(const dfgt_tree* t, dfgt_tree_info* out) {
   out->leaf_size = t->leaf;
   out->p_max = t->pm;
   out->n_coeff = t->P;
+  out->ms_levels = out->ms_moments = -1.0;
+  if (cudaSetDevice(t->device) != cudaSuccess) return DFGT_ECUDA;
+  if (t->ready && cudaEventSynchronize(t->ready) != cudaSuccess) return DFGT_ECUDA;
+  float ms = 0.f;
+  if (t->tev[0] && t->tev[1] && cudaEventElapsedTime(&ms, t->tev[0], t->tev[1]) == cudaSuccess) out->ms_levels = ms;
+  if (t->tev[2] && t->tev[3] && cudaEventElapsedTime(&ms, t->tev[2], t->tev[3]) == cudaSuccess) out->ms_moments = ms;
   return DFGT_OK;
 }
 

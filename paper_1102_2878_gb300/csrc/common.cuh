@@ -50,6 +50,11 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 constexpr double kLog2e = 1.4426950408889634073599246810018921;
 
+// Estimates below this go through the log-space pass of dfgt_sum_log: above
+// it the dual-tree pass's float32 exact sums and its fixed-point lower
+// bounds resolve the sum with room to spare (they need G >= ~1e-30).
+constexpr double kLogFlag = 1e-20;
+
 __host__ __device__ inline double fact_d(int n) {
   double f = 1.0;
   for (int i = 2; i <= n; ++i) f *= (double)i;
@@ -252,6 +257,16 @@ enum : int {
 // ------------------------------------------------------- grid barrier
 constexpr long long kSpinLimit = 1LL << 25;  // barrier polls before giving up (~1 s)
 
+// How the grid barriers of one cooperative launch wait.  `limit` is the
+// number of polls before a wait gives up.  `extra` > 0 makes every barrier
+// wait for that many arrivals more than the grid has: no block can pass,
+// so each one gives up at the first barrier, sets kStTimeout and returns
+// (the error path of a wait that runs out, injected from the host).
+struct BarrierCfg {
+  long long limit = kSpinLimit;
+  unsigned extra = 0;
+};
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -261,19 +276,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // Grid barrier of a cooperative launch on a monotone arrival counter:
 // every block passes the same sequence of barriers, so the k-th barrier
 // opens when the counter reaches k * gridDim.x (`target`, kept by each
-// block).  The wait is bounded: a block that polls kSpinLimit times sets
+// block).  The wait is bounded: a block that polls cfg.limit times sets
 // kStTimeout and leaves; every block returns false from then on, as it does
 // once a non-finite coordinate has been seen.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, unsigned& target) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* status, unsigned& target,
+                                             const BarrierCfg& cfg) {
   __shared__ int s_ok;
   __syncthreads();
-  target += gridDim.x;
+  target += gridDim.x + cfg.extra;
   if (threadIdx.x == 0) {
     __threadfence();
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
     long long it = 0;
     while ((int)(ld_acquire(bar) - target) < 0) {
-      if (++it > kSpinLimit) {
+      if (++it > cfg.limit) {
         atomicOr(status, kStTimeout);
         break;
       }

@@ -70,6 +70,9 @@ struct RoundCounters {
   unsigned long long n_prune;        // cumulative prune count
   unsigned long long base_inter;     // cumulative sum |Q||R| over base pairs
   unsigned long long base_exp;       // base interactions summed in the expanded form
+  unsigned long long far_terms;      // sum |Q| p^D over far-field actions
+  unsigned long long loc_terms;      // sum |R| p^D over direct local actions
+  unsigned long long f2l_terms;      // sum p^{2D} over far-to-local actions
 };
 
 struct dfgt_ctx {
@@ -96,6 +99,8 @@ struct dfgt_ctx {
   DevBuf bf_partials;       // brute-force slice partials
   DevBuf cv_buf;            // cross-validation normalisers, partials and scores
   DevBuf grad_buf;          // exact CV gradient sums (S, A, P, Y, partials)
+  DevBuf log_items;         // (query, bandwidth chunk) items of the log-space pass
+  DevBuf log_ctr;           // item count, flagged count and status of the log-space pass
   DevBuf bscratch;          // tree-build per-point scratch
   DevBuf bnodes;            // tree-build per-node scratch (left counts, prefixes, split ranks)
   std::shared_ptr<TreePool> tpool;
@@ -104,6 +109,7 @@ struct dfgt_ctx {
   int trav_grid[6] = {};      // blocks of the cooperative traversal per dimension template
   DevBuf trav_ctl;            // TravControl and the traversal's grid-barrier counter
   int mom_grid[6] = {};       // blocks of the cooperative moment pass per dimension (0: D >= 6)
+  dfgt::BarrierCfg wait;      // grid-barrier waits of the cooperative launches
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned
@@ -113,6 +119,7 @@ struct dfgt_ctx {
 struct dfgt_tree {
   int device = 0;
   cudaEvent_t ready = nullptr;  // moments and float node data written (recorded on the building context's side stream)
+  cudaEvent_t tev[4] = {};      // build start, after the (last) level build; around the (last) moment pass
   int64_t n = 0;
   int d = 0, dp = 0, leaf = 32, pm = 1, P = 1, p_limit = 1;
   long long base_block = 0;
@@ -164,6 +171,16 @@ cudaError_t launch_bruteforce_split(const float* q, int nq, const float* r, int 
 cudaError_t launch_bruteforce(const float* q, int nq, const float* r, int nr, int d,
                               const double* h_host, int nh, double* G, DevBuf& scratch,
                               cudaStream_t s, long long* launches);
+
+// logsum.cu: log G (and G) of every (bandwidth, query) whose estimate in G
+// (float64 [nh][nq], caller order) is below `flag`, by a depth-first walk
+// of the reference tree with double-float distances and a per-query shift;
+// log of the estimate elsewhere.  counters: one int (item count);
+// n_flagged: listed (bandwidth, query) pairs; status: kSt* bits.
+cudaError_t launch_log_pass(const TreeView& Q, const TreeView& R, const double* h_dev, int nh, double eps,
+                            double flag, double* G, double* logG, DevBuf& items_buf, int* counters,
+                            unsigned long long* n_flagged, int* status, cudaStream_t s, long long* launches,
+                            int* n_items_host);
 
 // cv.cu: cross-validation scores from the sums G [2 nh][n] at h and sqrt(2) h;
 // part holds nh * nblk * 4 doubles, out nh * 4 (CV_LK, bound, CV_LS, bound).
@@ -224,8 +241,8 @@ enum : int { kTravDone = 0, kTravRoom = 1, kTravRounds = 2, kTravOverflow = 3 };
 
 cudaError_t launch_traverse(const TreeView& Q, const TreeView& R, const TravBuffers& b, Pair* F0, Pair* F1,
                             int cap_front, Action* far, Action* loc, Action* f2l, Pair* base, int cap_lists,
-                            RoundCounters* ctr, TravControl* tc, unsigned* bar, int max_rounds, int* grid,
-                            cudaStream_t s);
+                            RoundCounters* ctr, TravControl* tc, unsigned* bar, const BarrierCfg& wait,
+                            int max_rounds, int* grid, cudaStream_t s);
 cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s);
 
 // Scratch of the base-case grouping (counting sort by bandwidth and query node).

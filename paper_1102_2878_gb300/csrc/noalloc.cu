@@ -26,7 +26,9 @@ double* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
 // Device address of the array on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached for the life of the process;
+// a device reset (cudaDeviceReset or a primary-context reset) leaves the
+// cached address stale, so the entry point must not be used after one.
 cudaError_t static_scratch(int device, double** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
@@ -50,22 +52,28 @@ extern "C" dfgt_status dfgt_sum_bruteforce_static(const float* q_dev, int64_t nq
     return DFGT_EINVAL;
   for (int i = 0; i < nh; ++i)
     if (!(h_host[i] > 0.0) || !(h_host[i] < INFINITY)) return DFGT_EINVAL;
-  // the partials of at least two slices must fit the static array
+  long long launches = 0;
+  const cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+  int slices = dfgt::bruteforce_slices((int)nq, (int)nr);
+  if (slices <= 1) {
+    // enough queries to fill the GPU: one pass writes G_dev directly and
+    // needs no scratch, so the array's limit does not apply
+    const cudaError_t e = dfgt::launch_bruteforce_split(q_dev, (int)nq, r_dev, (int)nr, d, h_host, nh, G_dev,
+                                                        1, nullptr, stream, &launches);
+    return e == cudaSuccess ? DFGT_OK : DFGT_ECUDA;
+  }
+  // split references: the partials of at least two slices must fit the array
   const size_t per_slice = (size_t)nh * (size_t)nq;
   if (2 * per_slice > kStaticScratchDoubles) return DFGT_ECAPACITY;
   int device = 0;
   if (cudaGetDevice(&device) != cudaSuccess) return DFGT_ECUDA;
   double* scratch = nullptr;
   if (static_scratch(device, &scratch) != cudaSuccess) return DFGT_ECUDA;
-  int slices = dfgt::bruteforce_slices((int)nq, (int)nr);
-  if (slices < 2) slices = 2;
   const size_t fit = kStaticScratchDoubles / per_slice;
   if ((size_t)slices > fit) slices = (int)fit;
-  long long launches = 0;
   // every partial that the reduction reads is written by its slice in this
   // call, so nothing needs clearing between calls
-  cudaError_t e = dfgt::launch_bruteforce_split(q_dev, (int)nq, r_dev, (int)nr, d, h_host, nh, G_dev,
-                                                slices, scratch, static_cast<cudaStream_t>(cuda_stream),
-                                                &launches);
+  const cudaError_t e = dfgt::launch_bruteforce_split(q_dev, (int)nq, r_dev, (int)nr, d, h_host, nh, G_dev,
+                                                      slices, scratch, stream, &launches);
   return e == cudaSuccess ? DFGT_OK : DFGT_ECUDA;
 }

@@ -80,6 +80,13 @@ __device__ int order_t(float r, float nR, int D, float tau, int plim) {
   return plim;
 }
 
+// b^e for small non-negative integers (b^e < 2^64)
+__device__ __forceinline__ unsigned long long ipow_u(int b, int e) {
+  unsigned long long r = 1;
+  for (int i = 0; i < e; ++i) r *= (unsigned long long)b;
+  return r;
+}
+
 // Block-wide sum added with one atomic (every thread of the block calls it;
 // scratch holds one word per warp).
 __device__ __forceinline__ void warp_add_u64_block(unsigned long long* counter, unsigned long long v,
@@ -152,7 +159,7 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
   const int P = Q.P;
   const int stride = gridDim.x * kT;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  unsigned long long my_prune = 0, my_inter = 0;
+  unsigned long long my_prune = 0, my_inter = 0, my_fterms = 0, my_dterms = 0, my_tterms = 0;
   for (int i0 = blockIdx.x * kT; i0 < nF; i0 += stride) {
     const int i = i0 + threadIdx.x;
     // kind: -1 none, 0 prune, 1 F, 2 D, 3 T, 4 base, 5 recurse
@@ -235,6 +242,11 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
           kind = 5; nchild = 2; split = kSplitROnly;
         }
       }
+      // algorithmic work of the summaries: |Q| p^D far-field terms, |R| p^D
+      // local-moment terms, p^{2D} far-to-local terms
+      if (kind == 1) my_fterms += (u64)cQ * (u64)ipow_u(order, d);
+      else if (kind == 2) my_dterms += (u64)cR * (u64)ipow_u(order, d);
+      else if (kind == 3) my_tterms += (u64)ipow_u(order, 2 * d);
       if (kind <= 4) {
         const u64 f = to_fix_f(nRo, Ku, b.fix_scale_dn);
         if (f) atomicAdd(&b.incr[hq], f);
@@ -309,6 +321,9 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
   // totals: one atomic per block
   warp_add_u64_block(&ctr->n_prune, my_prune, sWarp);
   warp_add_u64_block(&ctr->base_inter, my_inter, sWarp);
+  warp_add_u64_block(&ctr->far_terms, my_fterms, sWarp);
+  warp_add_u64_block(&ctr->loc_terms, my_dterms, sWarp);
+  warp_add_u64_block(&ctr->f2l_terms, my_tterms, sWarp);
 }
 
 // Every round of the traversal in one cooperative launch: fold, lower
@@ -328,6 +343,7 @@ struct TravArgs {
   RoundCounters* ctr;
   TravControl* tc;
   unsigned* bar;
+  BarrierCfg wait;
   int max_rounds;
 };
 
@@ -353,13 +369,13 @@ __global__ void __launch_bounds__(kT) k_traverse(TravArgs A) {
       break;
     }
     fold_phase(b, total);
-    if (!grid_barrier(A.bar, &ctr->status, target)) return;
+    if (!grid_barrier(A.bar, &ctr->status, target, A.wait)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&ctr->n_next, 0);
     lb_phase<D>(A.Q, A.R, b, A.F[cur], nF);
-    if (!grid_barrier(A.bar, &ctr->status, target)) return;
+    if (!grid_barrier(A.bar, &ctr->status, target, A.wait)) return;
     classify_phase<D>(A.Q, A.R, b, A.F[cur], nF, A.F[cur ^ 1], 4 * nF, A.far, A.loc, A.f2l, A.base,
                       A.cap_lists, ctr, sWarp, sBase);
-    if (!grid_barrier(A.bar, &ctr->status, target)) return;
+    if (!grid_barrier(A.bar, &ctr->status, target, A.wait)) return;
     visited += nF;
     ++rounds;
     cur ^= 1;
@@ -404,8 +420,8 @@ cudaError_t launch_init_frontier(Pair* F, int nh, cudaStream_t s) {
 
 cudaError_t launch_traverse(const TreeView& Q, const TreeView& R, const TravBuffers& b, Pair* F0, Pair* F1,
                             int cap_front, Action* far, Action* loc, Action* f2l, Pair* base, int cap_lists,
-                            RoundCounters* ctr, TravControl* tc, unsigned* bar, int max_rounds, int* grid,
-                            cudaStream_t s) {
+                            RoundCounters* ctr, TravControl* tc, unsigned* bar, const BarrierCfg& wait,
+                            int max_rounds, int* grid, cudaStream_t s) {
   TravArgs A;
   A.Q = Q;
   A.R = R;
@@ -421,6 +437,7 @@ cudaError_t launch_traverse(const TreeView& Q, const TreeView& R, const TravBuff
   A.ctr = ctr;
   A.tc = tc;
   A.bar = bar;
+  A.wait = wait;
   A.max_rounds = max_rounds;
   switch (Q.d) {  // grid[d]: the cooperative grid of each dimension's kernel
     case 1: return traverse_d<1>(A, grid + 1, s);

@@ -142,6 +142,7 @@ struct LevelArgs {
   int* lv;                          // level table: [3L] first node, [3L+1] end, [3L+2] splits
   int* ctl;                         // [0] status, [1] point buffer, [2] level, [3] leaves, [4] done, [5] nodes needed
   unsigned* bar;                    // grid barrier counter (zero at launch)
+  BarrierCfg wait;                  // how its waits are bounded
   int n, d, dp, leaf, cap, init_from, max_levels;
 };
 
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
       A.hi[j * d + k] = -INFINITY;
     }
   }
-  if (!grid_barrier(A.bar, A.ctl, target)) return;
+  if (!grid_barrier(A.bar, A.ctl, target, A.wait)) return;
 
   if (A.init_from == 0) {
     // the root: padded copies of the points and its box
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
       }
       __syncthreads();
     }
-    if (!grid_barrier(A.bar, A.ctl, target)) return;
+    if (!grid_barrier(A.bar, A.ctl, target, A.wait)) return;
   }
 
   for (;;) {
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
       block_exclusive_scan(nflag, tot, sw);
       if (tid == 0) A.bcnt[b] = tot;
     }
-    if (!grid_barrier(A.bar, A.ctl, target)) return;
+    if (!grid_barrier(A.bar, A.ctl, target, A.wait)) return;
 
     // phase 2: left ranks of the points (and of each node's first point),
     // decisions of the nodes
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
         A.bcnt[2 * G + b] = nl;
       }
     }
-    if (!grid_barrier(A.bar, A.ctl, target)) return;
+    if (!grid_barrier(A.bar, A.ctl, target, A.wait)) return;
 
     // phase 3: children, leaves, scatter
     grid_prefix(A.bcnt + G, G, sPre[0], sw);
@@ -496,7 +497,7 @@ __global__ void __launch_bounds__(kBT, 1) k_build_levels(LevelArgs A) {
         }
       }
     }
-    if (!grid_barrier(A.bar, A.ctl, target)) return;
+    if (!grid_barrier(A.bar, A.ctl, target, A.wait)) return;
     cur ^= 1;
     nleaves += NL;
     ++level;
@@ -870,6 +871,11 @@ void free_tree(dfgt_tree* t) {
   }
   if (t->ready) cudaEventDestroy(t->ready);
   t->ready = nullptr;
+  for (cudaEvent_t& e : t->tev)
+    if (e) {
+      cudaEventDestroy(e);
+      e = nullptr;
+    }
   t->arena = nullptr;
   t->tpool.reset();
   t->chi = t->clo = t->whalf = t->mnorm = nullptr;
@@ -923,6 +929,8 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
   // the previous build's moment pass may still read the build scratch
   TRY(cudaStreamWaitEvent(s, ctx->moments_done, 0));
   TRY(cudaEventCreateWithFlags(&t->ready, cudaEventDisableTiming));
+  for (cudaEvent_t& e : t->tev) TRY(cudaEventCreate(&e));
+  TRY(cudaEventRecord(t->tev[0], s));
   for (int pass = 0; pass < 2; ++pass) {
     cv.off = 0;
     pbuf[0] = cv.take<float>(np * t->dp);
@@ -979,6 +987,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       A.lo = t->lo; A.hi = t->hi; A.beg = t->beg; A.cnt = t->cnt; A.left = t->left; A.parent = t->parent;
       A.nleft = ns.nleft; A.arrive = ns.arrive; A.lp0 = ns.lp0; A.sloc = ns.sloc; A.leaves = t->leaves;
       A.lv = lv; A.ctl = ctl; A.bar = bar;
+      A.wait = ctx->wait;
       A.n = n; A.d = d; A.dp = t->dp; A.leaf = t->leaf;
       A.cap = (int)std::min<size_t>(cap, INT32_MAX);
       A.init_from = init_from;
@@ -986,10 +995,12 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       void* args[] = {&A};
       TRY(cudaLaunchCooperativeKernel((const void*)k_build_levels, dim3(ctx->build_grid), dim3(kBT), args, 0, s));
       ++*L;
+      TRY(cudaEventRecord(t->tev[1], s));
       // the moment pass runs on the side stream after the level build; the
       // next call on the context overlaps it (readers wait on t->ready)
       TRY(cudaEventRecord(ctx->ev[4], s));
       TRY(cudaStreamWaitEvent(ctx->side, ctx->ev[4], 0));
+      TRY(cudaEventRecord(t->tev[2], ctx->side));
       MomArgs M;
       M.pbuf0 = pbuf[0]; M.pbuf1 = pbuf[1];
       M.lo = t->lo; M.hi = t->hi; M.beg = t->beg; M.cnt = t->cnt; M.left = t->left; M.leaves = t->leaves;
@@ -1005,6 +1016,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
         default: TRY(launch_moments<0>(ctx, M, ctx->side)); break;
       }
       ++*L;
+      TRY(cudaEventRecord(t->tev[3], ctx->side));
       TRY(cudaEventRecord(ctx->moments_done, ctx->side));
       TRY(cudaMemcpyAsync(h_ctl, ctl, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
       TRY(cudaMemcpyAsync(lvh.data(), lv, lvh.size() * sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -59,11 +59,14 @@ def test_bichromatic(dev, orc, D):
     q = datagen.isotropic_mixture(3333, D, 6, 0.05, seed=700 + D)
     hs = [0.01, 0.05, 0.3]
     qt, rt = dfgt.Tree(dev, to_cuda(q)), dfgt.Tree(dev, to_cuda(r), leaf_size=16)
-    G, _ = dfgt.kde_sum(dev, qt, rt, hs, 1e-2)
-    G = G.cpu().numpy()
+    G, L, _ = dfgt.kde_sum_log(dev, qt, rt, hs, 1e-2)
+    G, L = G.cpu().numpy(), L.cpu().numpy()
     for i, h in enumerate(hs):
-        ref = orc.naive_kde(q.astype(np.float64), r.astype(np.float64), h)
-        ok = ref > 1e-30  # float32 range of the exact leaf sums
+        # every query, in log form (the sums of far queries lie below float range)
+        ref_log = orc.log_naive_kde(q.astype(np.float64), r.astype(np.float64), h)
+        assert np.abs(np.expm1(L[i] - ref_log)).max() <= 1e-2
+        ref = np.exp(ref_log)
+        ok = ref > 1e-300
         rel = np.abs(G[i][ok] - ref[ok]) / ref[ok]
         assert rel.max() <= 1e-2
 

@@ -53,3 +53,36 @@ def test_float_allowance_rule(dev):
         dfgt.kde_sum(dev, t, te, [0.1], 4e-4)
     G, _ = dfgt.kde_sum(dev, t, te, [0.1], 1e-3)
     assert np.isfinite(G.cpu().numpy()).all()
+
+
+def test_bounded_waits_report_timeout_and_context_recovers(dev):
+    # Every grid barrier of the cooperative launches waits for one arrival
+    # that never comes (a host-side switch, nothing faults): each block gives
+    # up after its poll limit, records the timeout and returns, so the build
+    # and the sum come back with DFGT_ETIMEOUT instead of hanging.
+    import time
+
+    from paper_1102_2878_gb300 import datagen
+
+    x = datagen.anisotropic_mixture(3000, 3, 4, 1e-4, 1e-2, seed=11)
+    pts = to_cuda(x)
+    t = dfgt.Tree(dev, pts)
+    want, _ = dfgt.kde_sum(dev, t, t, [0.02, 0.2], 1e-2)
+    try:
+        dev.test_wait_timeout(True)
+        t0 = time.perf_counter()
+        with pytest.raises(dfgt.DFGTError, match="ETIMEOUT"):
+            dfgt.Tree(dev, pts)
+        with pytest.raises(dfgt.DFGTError, match="ETIMEOUT"):
+            dfgt.kde_sum(dev, t, t, [0.02, 0.2], 1e-2)
+        assert time.perf_counter() - t0 < 30.0  # the calls came back, the waits did run out
+    finally:
+        dev.test_wait_timeout(False)
+    # the context serves the next normal calls, with the same results
+    t2 = dfgt.Tree(dev, pts)
+    got, _ = dfgt.kde_sum(dev, t2, t2, [0.02, 0.2], 1e-2)
+    rel = np.abs(got.cpu().numpy() - want.cpu().numpy()) / want.cpu().numpy()
+    assert rel.max() <= 2e-2
+    assert dfgt._lib.load().dfgt_test_wait_timeout(dev.h, 2) == 1  # DFGT_EINVAL
+    t.close()
+    t2.close()

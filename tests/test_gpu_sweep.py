@@ -44,16 +44,19 @@ def test_random_configuration(dev, orc, k):
     D, x, q, leaf, eps, hs = config(k)
     rtree = dfgt.Tree(dev, to_cuda(x), leaf_size=leaf)
     qtree = rtree if q is None else dfgt.Tree(dev, to_cuda(q), leaf_size=leaf)
-    G, _ = dfgt.kde_sum(dev, qtree, rtree, hs, eps)
-    G = G.cpu().numpy()
+    G, L, _ = dfgt.kde_sum_log(dev, qtree, rtree, hs, eps)
+    G, L = G.cpu().numpy(), L.cpu().numpy()
     qx = (x if q is None else q).astype(np.float64)
     for i, h in enumerate(hs):
-        ref = orc.naive_kde(qx, x.astype(np.float64), h)
-        ok = ref > TINY
+        # every query, in log form (Definition 1.2 for sums below any float range too)
+        ref_log = orc.log_naive_kde(qx, x.astype(np.float64), h)
+        err = np.abs(np.expm1(L[i] - ref_log))
+        assert err.max(initial=0.0) <= eps, (k, D, len(x), leaf, eps, h, float(err.max(initial=0.0)))
+        ref = np.exp(ref_log)
+        ok = ref > 1e-300
         rel = np.abs(G[i][ok] - ref[ok]) / ref[ok]
         assert rel.max(initial=0.0) <= eps, (k, D, len(x), leaf, eps, h, float(rel.max(initial=0.0)))
-        # below the float32 range the guarantee is absolute, not relative
-        assert np.all(np.isfinite(G[i])) and np.all(np.abs(G[i][~ok] - ref[~ok]) <= 1e-20)
+        assert np.all(np.isfinite(G[i])) and np.all(np.isfinite(L[i]))
     if q is None and len(x) >= 2:
         S, _ = dfgt.kde_sum_loo(dev, rtree, hs, eps)
         S = S.cpu().numpy()
