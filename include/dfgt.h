@@ -54,7 +54,8 @@ typedef struct {
                       (Section 3.6: 6 for D=2, 4 for D=3, 2 for D=4,5, 1 for D>=6;
                       8 for D=1); a smaller positive value lowers it */
   double eps_fp;   /* part of eps reserved for float32 rounding in exact sums;
-                      0 -> chosen per sum: 1% of eps, within [2e-5, 1e-4]
+                      0 -> chosen per sum: 1% of eps within [2e-5, 1e-4] for
+                      d <= 5, 20% of eps within [2e-5, 2e-3] for d >= 6
                       (a sum takes the larger of its two trees' values);
                       must be < eps */
   long long base_block; /* a node pair that no summary can take is summed exactly,
@@ -89,6 +90,7 @@ typedef struct {
   long long f2l_terms;          /* sum over far-to-local pairs of p^{2D} (coefficient products) */
   long long log_queries;        /* dfgt_sum_log: (bandwidth, query) pairs summed in log space */
   double ms_log;                /* dfgt_sum_log: device time of the log-space pass */
+  double ms_base_tc;            /* part of ms_base spent in the tensor-core exact sums (D >= 6) */
 } dfgt_stats;
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a
@@ -221,7 +223,7 @@ void dfgt_tree_destroy(dfgt_tree* tree);
  * dual-tree traversal of Section 3.6 (DFGTMain).
  *   h_host : nh finite values > 0 (host); 1 <= nh <= 1024
  *   eps    : 0 < eps < 1, above the trees' float allowance eps_fp (with
- *            eps_fp = 0 that is 1% of eps within [2e-5, 1e-4], so
+ *            eps_fp = 0 that is a share of eps with a floor of 2e-5, so
  *            eps > 2e-5); else DFGT_EINVAL
  *   G_dev  : float64 [nh][nq] (device, caller-owned), written in the
  *            caller's original query order; unnormalised sums of Eq. 5
@@ -333,9 +335,13 @@ dfgt_status dfgt_tree_get_info(const dfgt_tree* tree, dfgt_tree_info* out);
  *   moments float64[n_nodes][n_coeff] raw moments m_alpha = sum_r (r-c)^alpha/alpha!
  *           about the box center c, multi-index alpha at position
  *           sum_d alpha[d] p_max^(d_count-1-d) (last dimension least significant);
- *           the h-scaled moments of Eq. far_field_moments are m_alpha (2h^2)^(-|alpha|/2). */
+ *           the h-scaled moments of Eq. far_field_moments are m_alpha (2h^2)^(-|alpha|/2).
+ *   radius  float32[n_nodes]    radius of the node's points about the float box centre
+ *           0.5f (lo + hi), rounded up (the ball that tightens the distance bounds for
+ *           d >= 6). */
 dfgt_status dfgt_tree_export(const dfgt_tree* tree, int32_t* perm, float* lo, float* hi,
-                             int32_t* begin, int32_t* count, int32_t* left, double* moments);
+                             int32_t* begin, int32_t* count, int32_t* left, double* moments,
+                             float* radius);
 
 /* Actions of Summarize / DFGTBase applied to explicit node pairs. */
 enum {
@@ -352,11 +358,14 @@ enum {
  * (float64 [nq], caller order).  qnode/rnode/action/order are host arrays
  * of length n (order in 1..p_max, ignored for prune and base).  This runs
  * the same kernels as dfgt_sum on a caller-chosen pair list; it exists so
- * each operator can be checked against a reference. */
+ * each operator can be checked against a reference.  The exact sums take
+ * the trees' float allowance eps_fp (2e-5 where both leave it 0).  stats
+ * (may be NULL) receives base_interactions and base_expanded of the listed
+ * exact sums. */
 dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qtree, const dfgt_tree* rtree,
                              const int32_t* qnode_host, const int32_t* rnode_host,
                              const int32_t* action_host, const int32_t* order_host, int n,
-                             double h, double* G_dev);
+                             double h, double* G_dev, dfgt_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -127,8 +127,9 @@ class Tree:
         out = {"perm": np.empty(self.n, np.int32), "lo": np.empty((nn, d), np.float32),
                "hi": np.empty((nn, d), np.float32), "begin": np.empty(nn, np.int32),
                "count": np.empty(nn, np.int32), "left": np.empty(nn, np.int32),
-               "moments": np.empty((nn, P), np.float64)}
-        ptr = [C.c_void_p(out[k].ctypes.data) for k in ("perm", "lo", "hi", "begin", "count", "left", "moments")]
+               "moments": np.empty((nn, P), np.float64), "radius": np.empty(nn, np.float32)}
+        ptr = [C.c_void_p(out[k].ctypes.data) for k in ("perm", "lo", "hi", "begin", "count", "left", "moments",
+                                                         "radius")]
         self.ctx.check(self.ctx.lib.dfgt_tree_export(self.h, *ptr), "dfgt_tree_export")
         out["info"] = inf
         return out
@@ -361,15 +362,18 @@ def kde_host(ctx: Context, q: np.ndarray, r: np.ndarray | None, hs, eps: float, 
     return out, stats.as_dict()
 
 
-def apply_pairs(ctx: Context, qtree: Tree, rtree: Tree, qnode, rnode, action, order, h: float, out=None):
-    """Contributions of explicit (Q, R, action, order) items for one bandwidth."""
+def apply_pairs(ctx: Context, qtree: Tree, rtree: Tree, qnode, rnode, action, order, h: float, out=None,
+                with_stats: bool = False):
+    """Contributions of explicit (Q, R, action, order) items for one bandwidth
+    (and, with with_stats, the exact sums' work counters)."""
     torch = _torch()
     arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.int32)) for a in (qnode, rnode, action, order)]
     n = len(arrs[0])
     if out is None:
         out = torch.empty(qtree.n, dtype=torch.float64, device=f"cuda:{ctx.device}")
     ctx.order_after_torch()
+    stats = _lib.Stats()
     st = ctx.lib.dfgt_apply_pairs(ctx.h, qtree.h, rtree.h, *[C.c_void_p(a.ctypes.data) for a in arrs], n,
-                                  float(h), C.c_void_p(out.data_ptr()))
+                                  float(h), C.c_void_p(out.data_ptr()), C.byref(stats))
     ctx.check(st, "dfgt_apply_pairs")
-    return out
+    return (out, stats.as_dict()) if with_stats else out

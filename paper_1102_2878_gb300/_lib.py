@@ -34,7 +34,8 @@ class Stats(C.Structure):
                 ("ms_base", C.c_double), ("ms_farfield", C.c_double), ("ms_local", C.c_double),
                 ("ms_f2l", C.c_double), ("base_expanded", C.c_longlong),
                 ("farfield_terms", C.c_longlong), ("local_terms", C.c_longlong),
-                ("f2l_terms", C.c_longlong), ("log_queries", C.c_longlong), ("ms_log", C.c_double)]
+                ("f2l_terms", C.c_longlong), ("log_queries", C.c_longlong), ("ms_log", C.c_double),
+                ("ms_base_tc", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,9 +71,9 @@ SIGNATURES = {
                                 C.POINTER(C.c_double), C.c_int, C.c_double, C.POINTER(Opts),
                                 C.c_void_p, C.POINTER(Stats)]),
     "dfgt_tree_get_info": (C.c_int, [C.c_void_p, C.POINTER(TreeInfo)]),
-    "dfgt_tree_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 7),
+    "dfgt_tree_export": (C.c_int, [C.c_void_p] + [C.c_void_p] * 8),
     "dfgt_apply_pairs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p] + [C.c_void_p] * 4 +
-                         [C.c_int, C.c_double, C.c_void_p]),
+                         [C.c_int, C.c_double, C.c_void_p, C.POINTER(Stats)]),
     "dfgt_cv_scores": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int, C.c_double,
                                  C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(Stats)]),

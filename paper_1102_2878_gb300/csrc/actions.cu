@@ -716,8 +716,9 @@ constexpr int kHdWarps = 8;
 template <int DM>
 __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                                 const int* __restrict__ ksorted, int n,
-                                                const float* __restrict__ c2v, const float* __restrict__ inv2h2_up,
-                                                double* __restrict__ gacc, float exp_err) {
+                                                const float* __restrict__ c2v,
+                                                const unsigned char* __restrict__ tcflag,
+                                                double* __restrict__ gacc) {
   constexpr int TP = HdShape<DM>::TP, PS = HdShape<DM>::PS;
   __shared__ __align__(16) float sT[kHdWarps][TP * PS];
   __shared__ int sOff[kHdWarps][kEntryChunk + 1], sRb[kHdWarps][kEntryChunk];
@@ -740,8 +741,6 @@ __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView 
     qbeg = Q.beg[q];
     qcnt = Q.cnt[q];
   }
-  float rho2 = 0.f, far2 = 0.f;  // for the choice of form (base_hd_forms.cuh)
-  if (lane < m) hd_entry_bounds(Q, R, key % Q.nn, rsorted[i0 + lane] & kNodeMask, rho2, far2);
   const int keyp = __shfl_up_sync(FULL, key, 1);
   const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
   float* T = sT[wib];
@@ -769,17 +768,11 @@ __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView 
     const float c2 = c2v[hidx];
     const float2 c2p = make_float2(c2, c2);
     const bool loo = __any_sync(FULL, lane >= t && lane < e && self);
-    {
-      // a run of the tensor form is summed by k_base_hd_tc
-      const float rq2 = __shfl_sync(FULL, rho2, t);
-      const float f2 = __uint_as_float(
-          __reduce_max_sync(FULL, (lane >= t && lane < e) ? __float_as_uint(far2) : 0u));
-      HtScale sc;
-      if (hd_tensor_form(Q.d, ht_chunks(DM), rq2, f2, inv2h2_up[hidx], c2, loo, qn, exp_err, &sc)) {
-        __syncwarp();
-        t = e;
-        continue;
-      }
+    if (tcflag[i0 + t]) {
+      // a run of the tensor form (k_tc_plan) is summed by k_base_tc
+      __syncwarp();
+      t = e;
+      continue;
     }
     __syncwarp();
     for (int qs = 0; qs < qn; qs += 32 * kHdQBlocks) {
@@ -1613,17 +1606,27 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
     DISPATCH_D(Q.d, k_base<DD><<<g, kBaseWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up,
                                                               b.gacc, b.base_exp, b.exp_err));
   } else {
+    // which runs take the tensor form, then the direct-form runs (SIMT), then
+    // the tensor-form runs
+    const unsigned char* tcflag = nullptr;
+    // after the scatter, off[key] is the end of the key's entries
+    if ((e = launch_tc_plan(Q, R, b, rsorted, sc.cnt->as<int>(), sc.off->as<int>(), b.nh * Q.nn, n, *sc.plan,
+                            &tcflag, s, launches)) != cudaSuccess)
+      return e;
     const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kHdWarps - 1) / kHdWarps);
     if (Q.dp <= 8)
-      k_base_hd<8><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.exp_err);
+      k_base_hd<8><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc);
     else if (Q.dp <= 16)
-      k_base_hd<16><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.exp_err);
+      k_base_hd<16><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc);
     else
-      k_base_hd<32><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, b.inv2h2_up, b.gacc, b.exp_err);
+      k_base_hd<32><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ++*launches;
-    return launch_base_hd_tc(Q, R, b, rsorted, ksorted, n, s, launches);
+    if (sc.tc0 && (e = cudaEventRecord(sc.tc0, s)) != cudaSuccess) return e;
+    if ((e = launch_tc_sums(Q, R, b, rsorted, n, *sc.plan, s, launches)) != cudaSuccess) return e;
+    if (sc.tc1 && (e = cudaEventRecord(sc.tc1, s)) != cudaSuccess) return e;
+    return cudaSuccess;
   }
   ++*launches;
   return cudaGetLastError();

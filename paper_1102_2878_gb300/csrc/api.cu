@@ -79,10 +79,14 @@ dfgt_status post(dfgt_ctx* ctx, const dfgt_tree* qt, const TravBuffers& b, doubl
 
 // Part of eps reserved for float32 rounding in exact sums: the larger of
 // the trees' eps_fp, or, where both leave it 0, 1% of eps within
-// [2e-5, 1e-4].
+// [2e-5, 1e-4] for D <= 5, 20% of eps within [2e-5, 2e-3] for D >= 6
+// (where p_max = 1 leaves most of the work to exact sums, whose tensor
+// form needs the room, and little to the expansions that eps - eps_fp
+// budgets).
 double float_allowance(const dfgt_tree* a, const dfgt_tree* b, double eps) {
   const double v = std::max(a->eps_fp, b->eps_fp);
-  return v > 0.0 ? v : std::min(1e-4, std::max(2e-5, 0.01 * eps));
+  if (v > 0.0) return v;
+  return a->d >= 6 ? std::min(2e-3, std::max(2e-5, 0.2 * eps)) : std::min(1e-4, std::max(2e-5, 0.01 * eps));
 }
 
 // Zeroed per-call state; returns the traversal buffers.
@@ -138,6 +142,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->c2 = fl + 3 * nh;
   b->sf = fl + 4 * nh;
   b->base_exp = &ctx->counters.as<RoundCounters>()->base_exp;
+  b->status = &ctx->counters.as<RoundCounters>()->status;
   b->ku = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
@@ -174,14 +179,18 @@ struct ListState {
   int count = 0;
   long long total = 0;
   double ms = 0.0;       // device time of this list's kernel, all launches
+  double ms_tc = 0.0;    // of which the tensor-core exact sums (D >= 6)
   bool timed = false;    // a launch is bracketed by its events, not yet read
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool timed_tc = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, t0 = nullptr, t1 = nullptr;
   void collect() {
     if (!timed) return;
     float t = 0.f;
     cudaEventElapsedTime(&t, e0, e1);
     ms += t;
     timed = false;
+    if (timed_tc && cudaEventElapsedTime(&t, t0, t1) == cudaSuccess) ms_tc += t;
+    timed_tc = false;
   }
 };
 
@@ -203,14 +212,19 @@ dfgt_status drain(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, const
   }
   CK(cudaEventRecord(ls.e0, s));
   if (which == 0) {
-    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp, &ctx->tc_plan};
+    if (qt->d >= 6) {
+      sc.tc0 = ls.t0;
+      sc.tc1 = ls.t1;
+      ls.timed_tc = true;
+    }
     CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), ls.count, sc, s, &ctx->launches));
   }
   else if (which == 1) {
-    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp, &ctx->tc_plan};
     CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), ls.count, sc, s, &ctx->launches));
   } else if (which == 2) {
-    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+    BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp, &ctx->tc_plan};
     CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), ls.count, sc, s, &ctx->launches));
   } else {
     CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), ls.count, s));
@@ -246,9 +260,15 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     lists[w].e0 = ctx->ev[8 + 2 * w];
     lists[w].e1 = ctx->ev[9 + 2 * w];
   }
+  lists[0].t0 = ctx->ev[16];
+  lists[0].t1 = ctx->ev[17];
   int flushes = 0;
   double ms_classify = 0.0;
   CK(cudaEventRecord(ctx->ev[0], s));
+  if (qt->d >= 6) {  // the bounds take the nodes' point radii, written by the moment pass
+    CK(wait_ready(s, qt));
+    CK(wait_ready(s, rt));
+  }
   CK(launch_init_frontier(ctx->frontier[0].as<Pair>(), nh, s));
   ++ctx->launches;
   int cur = 0, nF = nh, rounds = 0;
@@ -342,6 +362,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
   CK(cudaEventRecord(ctx->ev[2], s));
   rc = post(ctx, qt, b, G_dev, st);
   if (rc != DFGT_OK) return rc;
+  if (hc->status & kStTimeout) return fail(ctx, DFGT_ETIMEOUT, "dfgt_sum: an exact-sum wait timed out");
   for (int w = 0; w < 4; ++w) lists[w].collect();
   if (st) {
     st->pairs_visited = visited;
@@ -364,6 +385,7 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]);
     st->ms_actions = ms;
     st->ms_base = lists[0].ms;
+    st->ms_base_tc = lists[0].ms_tc;
     st->ms_farfield = lists[1].ms;
     st->ms_local = lists[2].ms;
     st->ms_f2l = lists[3].ms;
@@ -408,7 +430,7 @@ dfgt_status dfgt_create(dfgt_ctx** out, int device, void* cuda_stream) {
     }
     ctx->tpool->stream = ctx->stream;
   }
-  for (int i = 0; i < 16 && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
+  for (int i = 0; i < kCtxEvents && e == cudaSuccess; ++i) e = cudaEventCreate(&ctx->ev[i]);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->moments_done, cudaEventDisableTiming);
   if (e != cudaSuccess) {
@@ -435,7 +457,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->side) cudaStreamSynchronize(ctx->side);
   DevBuf* bufs[] = {&ctx->scan_tmp, &ctx->counters, &ctx->hvals, &ctx->frontier[0], &ctx->frontier[1],
-                    &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->kus,
+                    &ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->tc_plan, &ctx->kus,
                     &ctx->list_far, &ctx->list_loc, &ctx->list_f2l, &ctx->list_base, &ctx->node_state,
                     &ctx->lmom, &ctx->pused, &ctx->gacc, &ctx->io_q, &ctx->io_r, &ctx->io_g,
                     &ctx->bf_partials, &ctx->bscratch, &ctx->bnodes, &ctx->cv_buf, &ctx->grad_buf,
@@ -448,7 +470,7 @@ void dfgt_destroy(dfgt_ctx* ctx) {
   }
   ctx->tpool.reset();
   if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
-  for (int i = 0; i < 16; ++i)
+  for (int i = 0; i < kCtxEvents; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -760,7 +782,7 @@ dfgt_status dfgt_tree_get_info(const dfgt_tree* t, dfgt_tree_info* out) {
 }
 
 dfgt_status dfgt_tree_export(const dfgt_tree* t, int32_t* perm, float* lo, float* hi,
-                             int32_t* begin, int32_t* count, int32_t* left, double* moments) {
+                             int32_t* begin, int32_t* count, int32_t* left, double* moments, float* radius) {
   if (!t) return DFGT_EINVAL;
   if (cudaSetDevice(t->device) != cudaSuccess) return DFGT_ECUDA;
   if (t->ready && cudaEventSynchronize(t->ready) != cudaSuccess) return DFGT_ECUDA;
@@ -772,6 +794,7 @@ dfgt_status dfgt_tree_export(const dfgt_tree* t, int32_t* perm, float* lo, float
       {count, t->cnt, (size_t)t->nn * sizeof(int)},
       {left, t->left, (size_t)t->nn * sizeof(int)},
       {moments, t->mom, (size_t)t->nn * t->P * sizeof(double)},
+      {radius, t->rad, (size_t)t->nn * sizeof(float)},
   };
   for (const Item& it : items)
     if (it.dst && cudaMemcpy(it.dst, it.src, it.bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -781,7 +804,7 @@ dfgt_status dfgt_tree_export(const dfgt_tree* t, int32_t* perm, float* lo, float
 
 dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
                              const int32_t* qnode, const int32_t* rnode, const int32_t* action,
-                             const int32_t* order, int n, double h, double* G_dev) {
+                             const int32_t* order, int n, double h, double* G_dev, dfgt_stats* stats) {
   if (!ctx) return DFGT_EINVAL;
   if (!qt || !rt || !G_dev || qt->d != rt->d || n < 0 || (n > 0 && (!qnode || !rnode || !action)))
     return fail(ctx, DFGT_EINVAL, "dfgt_apply_pairs: bad arguments");
@@ -826,13 +849,27 @@ dfgt_status dfgt_apply_pairs(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree
   CK(up(ctx->list_f2l, f2l.data(), f2l.size() * sizeof(Action)));
   const TreeView Q = qt->view(), R = rt->view();
   CK(launch_prune_apply(Q, R, b, ctx->frontier[0].as<Pair>(), (int)prune.size(), s));
-  BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp};
+  BaseScratch sc{&ctx->grp_cnt, &ctx->grp_off, &ctx->grp_r, &ctx->scan_tmp, &ctx->tc_plan};
   CK(launch_base(Q, R, b, ctx->list_base.as<Pair>(), (int)base.size(), sc, s, &ctx->launches));
   CK(launch_farfield(Q, R, b, ctx->list_far.as<Action>(), (int)far.size(), sc, s, &ctx->launches));
   CK(launch_local(Q, R, b, ctx->list_loc.as<Action>(), (int)loc.size(), sc, s, &ctx->launches));
   CK(launch_f2l(Q, R, b, ctx->list_f2l.as<Action>(), (int)f2l.size(), s));
   CK(cudaEventRecord(ctx->ev[2], s));
-  return post(ctx, qt, b, G_dev, nullptr);
+  rc = post(ctx, qt, b, G_dev, nullptr);
+  if (rc != DFGT_OK) return rc;
+  if (ctx->h_counters->status & kStTimeout) return fail(ctx, DFGT_ETIMEOUT, "dfgt_apply_pairs: an exact-sum wait timed out");
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    long long inter = 0;
+    std::vector<int> qc(qt->nn), rc2(rt->nn);
+    CK(cudaMemcpy(qc.data(), qt->cnt, qc.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(rc2.data(), rt->cnt, rc2.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (const Pair& p : base) inter += (long long)qc[p.q] * rc2[p.r];
+    stats->n_base = (long long)base.size();
+    stats->base_interactions = inter;
+    stats->base_expanded = (long long)ctx->h_counters->base_exp;
+  }
+  return DFGT_OK;
 }
 
 dfgt_status dfgt_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n, int d, const double* h_host, int nh,

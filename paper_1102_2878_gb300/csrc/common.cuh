@@ -37,6 +37,7 @@ struct TreeView {
   const float* clo;
   const float* whalf;  // [nn] largest half side w of the box (1 for a point)
   const float* mnorm;  // [nn][P] normalised moments m_alpha / w^|alpha| (|m~| <= |R|)
+  const float* rad;    // [nn] radius of the node's points about its float box centre 0.5f (lo + hi), rounded up
   int n, d, dp, nn, pm, P;
 };
 
@@ -190,10 +191,19 @@ __device__ __forceinline__ void atomic_max_f(float* a, float v) {
 // kernel value and every truncation bound derived from them stays on the
 // safe side.  (x + |x|)/2 summed over the two orderings of Eq. (6) is
 // max(rl - qu, ql - ru, 0).
+// For D >= 6 (the generic D = 0 instance with d >= 6) the bounds are
+// tightened by the nodes' balls about their box centres c (radius r of the
+// points, Q.rad / R.rad): every pair of points is at least |c_Q - c_R| -
+// r_Q - r_R and at most |c_Q - c_R| + r_Q + r_R apart.  In many dimensions
+// a kd box is much wider than the points it holds, and the box bound alone
+// separates almost no pair; any valid pair of bounds serves the traversal
+// (Theorem 3.3 needs only that the distances lie between them).
 template <int D>
 __device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const TreeView& R, int r,
                                              float& dl2, float& du2, float& sideQ, float& sideR) {
   const int d = D > 0 ? D : Q.d;
+  const bool ball = D == 0 && d >= 6;
+  float c2dn = 0.f, c2up = 0.f;
   dl2 = du2 = sideQ = sideR = 0.f;
   for (int k = 0; k < d; ++k) {
     const float ql = Q.lo[(size_t)q * d + k], qu = Q.hi[(size_t)q * d + k];
@@ -204,6 +214,20 @@ __device__ __forceinline__ void box_geometry(const TreeView& Q, int q, const Tre
     du2 = __fmaf_ru(far, far, du2);
     sideQ = fmaxf(sideQ, __fsub_ru(qu, ql));
     sideR = fmaxf(sideR, __fsub_ru(ru, rl));
+    if (ball) {
+      const float cq = 0.5f * (ql + qu), cr = 0.5f * (rl + ru);
+      const float dn = cq >= cr ? __fsub_rd(cq, cr) : __fsub_rd(cr, cq);
+      const float up = cq >= cr ? __fsub_ru(cq, cr) : __fsub_ru(cr, cq);
+      c2dn = __fmaf_rd(dn, dn, c2dn);
+      c2up = __fmaf_ru(up, up, c2up);
+    }
+  }
+  if (ball) {
+    const float rr = __fadd_ru(Q.rad[q], R.rad[r]);
+    const float lo = __fsub_rd(__fsqrt_rd(c2dn), rr);
+    if (lo > 0.f) dl2 = fmaxf(dl2, __fmul_rd(lo, lo));
+    const float hi = __fadd_ru(__fsqrt_ru(c2up), rr);
+    du2 = fminf(du2, __fmul_ru(hi, hi));
   }
 }
 

@@ -75,6 +75,8 @@ struct RoundCounters {
   unsigned long long f2l_terms;      // sum p^{2D} over far-to-local actions
 };
 
+constexpr int kCtxEvents = 18;  // [16], [17]: around the tensor-core exact sums
+
 struct dfgt_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -90,6 +92,7 @@ struct dfgt_ctx {
   DevBuf kus;            // float lower bound on K(d^u) per frontier pair
   DevBuf frontier[2];    // Pair
   DevBuf grp_cnt, grp_off, grp_r;  // base-case grouping scratch
+  DevBuf tc_plan;        // tensor-core plan of the exact sums (D >= 6)
   DevBuf list_far, list_loc, list_f2l, list_base;  // Action / Pair
   DevBuf node_state;     // u64 inherited/decided/incr/lbsum
   DevBuf lmom;           // double local moments [nh][nn][P]
@@ -113,7 +116,7 @@ struct dfgt_ctx {
   size_t cap_frontier = 1 << 20;
   size_t cap_lists = 1 << 22;
   RoundCounters* h_counters = nullptr;  // pinned
-  cudaEvent_t ev[16] = {};
+  cudaEvent_t ev[kCtxEvents] = {};
 };
 
 struct dfgt_tree {
@@ -142,11 +145,12 @@ struct dfgt_tree {
   float* clo = nullptr;
   float* whalf = nullptr;
   float* mnorm = nullptr;
+  float* rad = nullptr;       // radius of each node's points about its box centre
   dfgt::TreeView view() const {
     dfgt::TreeView v;
     v.pts = pts; v.perm = perm; v.lo = lo; v.hi = hi; v.beg = beg; v.cnt = cnt;
     v.left = left; v.parent = parent; v.mom = mom;
-    v.chi = chi; v.clo = clo; v.whalf = whalf; v.mnorm = mnorm;
+    v.chi = chi; v.clo = clo; v.whalf = whalf; v.mnorm = mnorm; v.rad = rad;
     v.n = (int)n; v.d = d; v.dp = dp; v.nn = nn; v.pm = pm; v.P = P;
     return v;
   }
@@ -214,6 +218,7 @@ struct TravBuffers {
   const float* c2;       // [nh] -log2(e)/(2h^2) as float, the exp2 scale of exact sums
   const float* sf;       // [nh] 1/sqrt(2h^2) as float, the expansion scale
   unsigned long long* base_exp;  // device counter of expanded-form base interactions
+  int* status;           // device status word of the call (kSt* bits)
   float tau_scale_dn;    // eps_eff / (fix_scale |R_total|) as float, rounded down
   float* ku;        // [frontier] lower bound on K(d^u) of each pending pair
   int nh;
@@ -251,12 +256,20 @@ struct BaseScratch {
   DevBuf* off;
   DevBuf* rsorted;
   DevBuf* scan_tmp;
+  DevBuf* plan;         // D >= 6: the tensor-core plan (items and per-entry flags)
+  cudaEvent_t tc0 = nullptr, tc1 = nullptr;  // recorded around the tensor-core exact sums (D >= 6) if set
 };
 cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                         const Pair* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
-// base_hd_tc.cu: the tensor-core runs of a sorted base list (D >= 6).
-cudaError_t launch_base_hd_tc(const TreeView& Q, const TreeView& R, const TravBuffers& b, const int* rsorted,
-                              const int* ksorted, int n, cudaStream_t s, long long* launches);
+// base_tc.cu: the tensor-core runs of a sorted base list (D >= 6): the plan
+// (which runs take the tensor form; tcflag[i] = 1 for their entries) and
+// their sums.
+// cnt[key] entries of key (bandwidth, query node) end at end[key] in the sorted list.
+cudaError_t launch_tc_plan(const TreeView& Q, const TreeView& R, const TravBuffers& b, const int* rsorted,
+                           const int* cnt, const int* end, int nkeys, int n, DevBuf& plan,
+                           const unsigned char** tcflag, cudaStream_t s, long long* launches);
+cudaError_t launch_tc_sums(const TreeView& Q, const TreeView& R, const TravBuffers& b, const int* rsorted, int n,
+                           DevBuf& plan, cudaStream_t s, long long* launches);
 cudaError_t launch_farfield(const TreeView& Q, const TreeView& R, const TravBuffers& b,
                             const Action* list, int n, BaseScratch& sc, cudaStream_t s, long long* launches);
 cudaError_t launch_local(const TreeView& Q, const TreeView& R, const TravBuffers& b,

@@ -528,7 +528,7 @@ struct MomArgs {
   const float *lo, *hi;
   const int *beg, *cnt, *left, *parent, *leaves;
   double* mom;                 // [nodes][P] raw moments
-  float *chi, *clo, *whalf, *mnorm;
+  float *chi, *clo, *whalf, *mnorm, *rad;
   int* arrive;                 // [nodes] children finished (zero at launch)
   const int* ctl;
   int n, d, dp, pm, P;
@@ -693,7 +693,7 @@ __device__ void f2f_node(const MomArgs& M, int w, MomSmem<D, PM, P>& sm) {
 // the scaled moments M_alpha = m~_alpha (w s)^|alpha| are formed in float32
 // without range problems.  Computed in float64 once per tree; the node's
 // moments were written by this warp or are visible to it.
-__device__ void node_float_data(const MomArgs& M, int j) {
+__device__ void node_float_data(const MomArgs& M, const float* pin, int j) {
   const int d = M.d, lane = threadIdx.x & 31;
   double hw = 0.0;
   for (int k = lane; k < d; k += 32) {
@@ -706,6 +706,52 @@ __device__ void node_float_data(const MomArgs& M, int j) {
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) hw = fmax(hw, __shfl_xor_sync(0xffffffffu, hw, o));
+  // radius of the node's points about the float box centre 0.5f (lo + hi)
+  // (the centre the distance bounds take), rounded up: a leaf from its
+  // points, a parent from its children (|c - c_child| + r_child) or the box's
+  // half diagonal, whichever is smaller
+  float r2 = 0.f;
+  const int left = M.left[j];
+  if (left < 0) {
+    const int b = M.beg[j], c = M.cnt[j];
+    for (int i = lane; i < c; i += 32) {
+      const float* p = pin + (size_t)(b + i) * M.dp;
+      float s = 0.f;
+      for (int k = 0; k < d; ++k) {
+        const float ck = 0.5f * (M.lo[(size_t)j * d + k] + M.hi[(size_t)j * d + k]);
+        const float v = p[k];
+        const float df = v >= ck ? __fsub_ru(v, ck) : __fsub_ru(ck, v);
+        s = __fmaf_ru(df, df, s);
+      }
+      r2 = fmaxf(r2, s);
+    }
+  } else {
+    if (lane < 2) {
+      const int ch = left + lane;
+      float s = 0.f;
+      for (int k = 0; k < d; ++k) {
+        const float ck = 0.5f * (M.lo[(size_t)j * d + k] + M.hi[(size_t)j * d + k]);
+        const float cc = 0.5f * (M.lo[(size_t)ch * d + k] + M.hi[(size_t)ch * d + k]);
+        const float df = cc >= ck ? __fsub_ru(cc, ck) : __fsub_ru(ck, cc);
+        s = __fmaf_ru(df, df, s);
+      }
+      const float r = __fadd_ru(__fsqrt_ru(s), __ldcg(M.rad + ch));
+      r2 = __fmul_ru(r, r);
+    }
+  }
+  // the box's half diagonal bounds it too
+  float hd2 = 0.f;
+  for (int k = lane; k < d; k += 32) {
+    const float ck = 0.5f * (M.lo[(size_t)j * d + k] + M.hi[(size_t)j * d + k]);
+    const float w = fmaxf(__fsub_ru(M.hi[(size_t)j * d + k], ck), __fsub_ru(ck, M.lo[(size_t)j * d + k]));
+    hd2 = __fmaf_ru(w, w, hd2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    hd2 = __fadd_ru(hd2, __shfl_xor_sync(0xffffffffu, hd2, o));
+  }
+  if (lane == 0) M.rad[j] = fminf(__fsqrt_ru(r2), __fsqrt_ru(hd2));
   float wf = (float)hw;
   if (!(wf > 0.f)) wf = 1.f;
   if (lane == 0) M.whalf[j] = wf;
@@ -746,7 +792,7 @@ __global__ void __launch_bounds__(kMT) k_moments(MomArgs M) {
       if (lane == 0) M.mom[w] = (double)M.cnt[w];
     }
     __syncwarp();
-    node_float_data(M, w);
+    node_float_data(M, pin, w);
     for (;;) {
       const int par = M.parent[w];
       if (par < 0) break;
@@ -763,7 +809,7 @@ __global__ void __launch_bounds__(kMT) k_moments(MomArgs M) {
         if (lane == 0) M.mom[par] = (double)M.cnt[par];
       }
       __syncwarp();
-      node_float_data(M, par);
+      node_float_data(M, pin, par);
       w = par;
     }
   }
@@ -794,6 +840,7 @@ void carve_tree(Carver& ca, dfgt_tree* t, size_t np, size_t cap) {
   t->clo = ca.take<float>(cap * d);
   t->whalf = ca.take<float>(cap);
   t->mnorm = ca.take<float>(cap * P);
+  t->rad = ca.take<float>(cap);
 }
 
 cudaError_t alloc_tree(dfgt_ctx* ctx, dfgt_tree* t, size_t np, size_t cap) {
@@ -878,7 +925,7 @@ void free_tree(dfgt_tree* t) {
     }
   t->arena = nullptr;
   t->tpool.reset();
-  t->chi = t->clo = t->whalf = t->mnorm = nullptr;
+  t->chi = t->clo = t->whalf = t->mnorm = t->rad = nullptr;
   t->pts = nullptr; t->perm = nullptr; t->lo = t->hi = nullptr;
   t->beg = t->cnt = t->left = t->parent = t->leaves = nullptr; t->mom = nullptr;
 }
@@ -1004,7 +1051,7 @@ dfgt_status build_tree(dfgt_ctx* ctx, const float* pts_dev, int64_t n64, int d,
       MomArgs M;
       M.pbuf0 = pbuf[0]; M.pbuf1 = pbuf[1];
       M.lo = t->lo; M.hi = t->hi; M.beg = t->beg; M.cnt = t->cnt; M.left = t->left; M.leaves = t->leaves;
-      M.mom = t->mom; M.chi = t->chi; M.clo = t->clo; M.whalf = t->whalf; M.mnorm = t->mnorm;
+      M.mom = t->mom; M.chi = t->chi; M.clo = t->clo; M.whalf = t->whalf; M.mnorm = t->mnorm; M.rad = t->rad;
       M.parent = t->parent; M.arrive = ns.arrive; M.ctl = ctl;
       M.n = n; M.d = d; M.dp = t->dp; M.pm = t->pm; M.P = t->P;
       switch (d) {

@@ -64,22 +64,80 @@ def test_forms_partition_the_interactions(dev):
     assert rel.max().item() <= 2e-2
 
 
-@pytest.mark.parametrize("D,side,h,efp", [(6, 0.2, 0.3, 0.0), (7, 0.2, 0.3, 0.0), (7, 1.0, 0.5, 1e-3),
-                                          (8, 0.2, 0.3, 0.0), (12, 0.15, 0.3, 0.0), (16, 0.1, 0.25, 0.0),
-                                          (16, 1.0, 0.5, 1e-3), (20, 0.08, 0.3, 0.0), (32, 0.05, 0.2, 0.0),
-                                          (32, 1.0, 0.9, 1e-3)])
-def test_whole_node_exact_sum_high_dimension(dev, orc, D, side, h, efp):
-    # D >= 6: one base entry (root, root) whose expansion bound puts it in
-    # the tensor-core form; each term's error is then at most eps_fp / 4
-    # (plus ex2.approx's 2^-21 and the float32 summation)
+U = 2.0 ** -24
+
+
+def tc_kappa(D):
+    """kappa of the tensor form's bound (base_hd_forms.cuh): 26 + 4 KC, KC
+    the chained K16 steps of DM = 8, 16 or 32 padded coordinates."""
+    dm = 8 if D <= 8 else 16 if D <= 16 else 32
+    return 26 + 4 * ((3 * dm + 2 + 15) // 16)
+
+
+def tc_tolerance(X, Q, h, e1, D):
+    """Relative error allowed to one query's exact sum in the tensor form:
+    2^-21 (ex2) + E1 + 2 kappa u xbar (xbar the kernel-weighted mean
+    exponent, natural units) + 2^-20 for the float32 summation."""
+    tol = np.empty(len(Q))
+    for i, q in enumerate(Q):
+        x = ((X - q) ** 2).sum(1) / (2 * h * h)
+        K = np.exp(-x)
+        tol[i] = 2.0 ** -21 + e1 + 2 * tc_kappa(D) * U * (K * x).sum() / K.sum() + 2.0 ** -20
+    return tol
+
+
+@pytest.mark.parametrize("D,side,h", [(6, 0.3, 0.3), (7, 1.0, 0.6), (8, 0.3, 0.3), (12, 0.3, 0.3),
+                                      (16, 0.25, 0.3), (16, 1.0, 0.9), (20, 0.2, 0.3), (32, 0.2, 0.4),
+                                      (32, 1.0, 1.5)])
+def test_whole_node_exact_sum_high_dimension(dev, orc, D, side, h):
+    # D >= 6: one base entry (root, root) of 2000 queries against 2000
+    # references in the tensor-core form (float allowance 1e-3: E1 =
+    # 8 kappa u rho^2 / 2h^2 <= eps_fp / 4 for these boxes), within the
+    # form's bound of the oracle's float64 sums
     rng = np.random.default_rng(60 + D)
     X = (side * rng.random((2000, D))).astype(np.float32)
+    efp = 1e-3
     t = dfgt.Tree(dev, to_cuda(X), eps_fp=efp)
-    G = dfgt.apply_pairs(dev, t, t, [0], [0], [_lib.ACT_BASE], [1], h).cpu().numpy()
-    want = orc.naive_kde(X.astype(np.float64), X.astype(np.float64), h)
+    G, st = dfgt.apply_pairs(dev, t, t, [0], [0], [_lib.ACT_BASE], [1], h, with_stats=True)
+    assert st["base_expanded"] == st["base_interactions"] == 2000 * 2000, st
+    G = G.cpu().numpy()
+    X64 = X.astype(np.float64)
+    want = orc.naive_kde(X64, X64, h)
     rel = np.abs(G - want) / want
-    allowance = efp if efp > 0 else 2e-5
-    assert rel.max() <= allowance / 4 + 2e-6, (D, rel.max())
+    lo, hi = X.min(0).astype(np.float64), X.max(0).astype(np.float64)
+    rho2 = (((hi - lo) / 2) ** 2).sum()
+    e1 = 8 * tc_kappa(D) * U * rho2 / (2 * h * h)
+    assert e1 <= efp / 4
+    sample = rng.choice(2000, size=300, replace=False)
+    tol = tc_tolerance(X64, X64[sample], h, e1, D)
+    assert np.all(rel[sample] <= tol), (D, float((rel[sample] / tol).max()))
+    assert rel.max() <= efp, (D, rel.max())
+    # the same sum forced onto the direct form agrees within both bounds
+    td = dfgt.Tree(dev, to_cuda(X), eps_fp=1e-7)
+    Gd, sd = dfgt.apply_pairs(dev, td, td, [0], [0], [_lib.ACT_BASE], [1], h, with_stats=True)
+    assert sd["base_expanded"] == 0
+    assert (np.abs(Gd.cpu().numpy() - want) / want).max() <= efp
+
+
+@pytest.mark.parametrize("D", [8, 16, 32])
+def test_tensor_form_ragged_runs(dev, orc, D):
+    # many base entries of one query node: reference tiles that end part
+    # way (ragged 128-column tiles), query blocks past 128 rows, and runs
+    # spanning several 32-entry chunks
+    rng = np.random.default_rng(90 + D)
+    X = (0.3 * rng.random((3001, D))).astype(np.float32)
+    Y = (0.3 * rng.random((1777, D))).astype(np.float32)
+    qt = dfgt.Tree(dev, to_cuda(Y), eps_fp=1e-3, leaf_size=200)
+    rt = dfgt.Tree(dev, to_cuda(X), eps_fp=1e-3, leaf_size=7)
+    rinfo = rt.export()
+    leaves = np.flatnonzero(rinfo["left"] < 0)
+    h = 0.35
+    G, st = dfgt.apply_pairs(dev, qt, rt, [0] * len(leaves), list(leaves), [_lib.ACT_BASE] * len(leaves),
+                             [1] * len(leaves), h, with_stats=True)
+    assert st["base_expanded"] == st["base_interactions"] == 1777 * 3001, st
+    want = orc.naive_kde(Y.astype(np.float64), X.astype(np.float64), h)
+    rel = np.abs(G.cpu().numpy() - want) / want
+    assert rel.max() <= 1e-3, rel.max()
 
 
 @pytest.mark.parametrize("eps", [1e-2, 1e-3])

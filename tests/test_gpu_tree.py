@@ -37,6 +37,17 @@ def check_tree(x, t, leaf):
         assert cnt[j] > leaf
     leaves = np.where(left < 0)[0]
     assert cnt[leaves].sum() == n
+    # the node's ball about the float box centre holds every point of it, and
+    # is no wider than the box's half diagonal allows (plus float rounding)
+    rad = t["radius"].astype(np.float64)
+    for j in range(nn):
+        pts = xp[beg[j]:beg[j] + cnt[j]].astype(np.float64)
+        c = (np.float32(0.5) * (lo[j] + hi[j])).astype(np.float64)
+        dmax = np.sqrt(((pts - c) ** 2).sum(1).max())
+        assert dmax <= rad[j], (j, dmax, rad[j])
+        half_diag = np.sqrt((np.maximum(hi[j] - c, c - lo[j]) ** 2).sum())
+        # (float32 squares of sides below 1e-19 are subnormal: an absolute slack)
+        assert rad[j] <= half_diag * (1 + 1e-5) + 1e-20, (j, rad[j], half_diag)
 
 
 @pytest.mark.parametrize("D,n,leaf", [(1, 1000, 8), (2, 5000, 32), (3, 20011, 32), (5, 3000, 16),
