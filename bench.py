@@ -33,7 +33,8 @@ from paper_1102_2878_gb300 import datagen  # noqa: E402
 
 METRIC = "effective query-ref pairs/s (|Q|·|R|/time) at ε=1e-2, DFGT vs GPU brute force"
 UNIT = "pairs/s"
-DEFAULT_WORKLOAD = "kde3d_n2e5_sweep10"
+# the largest single-GPU configuration: D = 16, 1e6 points, 8 bandwidths
+DEFAULT_WORKLOAD = "kde16d_n1e6_sweep8"
 # GB300: 152 SMs.  A loop of eight independent ex2.approx chains per thread
 # on every SM retired 31.4 ex2 per clock per SM at the sampled 1987 MHz, and
 # the profiler puts the exact-sum kernel's XU pipe at 43% while it runs 12.8
@@ -186,9 +187,17 @@ def roofline_by_kernel(stats, tinfo, N, D, nh, sm_clk, hbm_gbs):
         out[kernel] = {"units_per_step": units, "unit": unit, "ms_per_step": ms, "bound": bound,
                        "achieved": rate, "peak": peak, "peak_unit": peak_unit, "frac": rate / peak}
 
-    base_name = "k_base" if D <= 5 else "k_base_hd + k_base_hd_tc"
-    put(base_name, mean("base_interactions"), "pair interactions", mean("ms_base"), "alu",
-        ex2_peak, "ex2/s (SFU)")
+    if D <= 5:
+        put("k_base", mean("base_interactions"), "pair interactions", mean("ms_base"), "alu", ex2_peak,
+            "ex2/s (SFU)")
+    else:
+        # tensor form: one ex2 per interaction on the SFU (the binding unit);
+        # direct form (SIMT): 2D + 2 FMA-pipe operations per interaction
+        put("k_base_tc", mean("base_expanded"), "pair interactions", mean("ms_base_tc"), "alu", ex2_peak,
+            "ex2/s (SFU)")
+        direct = mean("base_interactions") - mean("base_expanded")
+        put("k_base_hd", direct * (2 * D + 2), "FMA-pipe operations (2D + 2 per interaction)",
+            mean("ms_base") - mean("ms_base_tc"), "alu", fma_peak, "FMA/s")
     put("k_farfield", mean("farfield_terms"), "series terms |Q| p^D", mean("ms_farfield"), "alu",
         fma_peak, "FMA/s")
     put("k_local", mean("local_terms"), "series terms |R| p^D", mean("ms_local"), "alu", fma_peak, "FMA/s")
@@ -357,15 +366,27 @@ def run_dfgt(args, rank, world, local):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel (the exact sums): one ex2 per pair
-    # interaction, bounded by the SFU ex2 issue rate
-    inter = statistics.mean(s["base_interactions"] for s in stats)
-    base_ms = statistics.mean(s["ms_base"] for s in stats)
+    # roofline of the dominant kernel: the exact sums (DFGTBase), one ex2 per
+    # pair interaction, bounded by the SFU ex2 issue rate; for D >= 6 the
+    # tensor-core kernel if it takes the larger share of their time
     peaks = measured_peaks()
     sm_clk = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak = SM_COUNT * SFU_EX2_PER_CLK_PER_SM * sm_clk * 1e6
-    achieved = inter / (base_ms / 1e3) if base_ms > 0 else 0.0
-    roof = {"bound": "alu", "kernel": "k_base (DFGTBase exact sums)", "achieved": achieved,
+    inter = statistics.mean(s["base_interactions"] for s in stats)
+    roof_units = inter
+    roof_ms = statistics.mean(s["ms_base"] for s in stats)
+    kernel = "k_base (DFGTBase exact sums)"
+    if D >= 6:
+        tc_ms = statistics.mean(s["ms_base_tc"] for s in stats)
+        expanded = statistics.mean(s["base_expanded"] for s in stats)
+        if tc_ms >= roof_ms - tc_ms:
+            roof_units, roof_ms = expanded, tc_ms
+            kernel = "k_base_tc (DFGTBase exact sums, tcgen05 tensor form)"
+        else:
+            roof_units, roof_ms = inter - expanded, roof_ms - tc_ms
+            kernel = "k_base_hd (DFGTBase exact sums, direct form)"
+    achieved = roof_units / (roof_ms / 1e3) if roof_ms > 0 else 0.0
+    roof = {"bound": "alu", "kernel": kernel, "achieved": achieved,
             "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
             "traffic": base_traffic(args.workload),
             "peak_source": f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz (measured: "
@@ -388,6 +409,7 @@ def run_dfgt(args, rank, world, local):
         "max_rel_err_vs_bruteforce": rel,
         "breakdown_ms": {"build": mean("ms_build"), "classify": mean("ms_classify"),
                          "traverse": mean("ms_traverse"), "base": mean("ms_base"),
+                         "base_tensor_form": mean("ms_base_tc"),
                          "farfield": mean("ms_farfield"), "local": mean("ms_local"),
                          "f2l": mean("ms_f2l"), "post": mean("ms_post")},
         "work": {"pairs_visited": mean("pairs_visited"), "prune": mean("n_prune"),

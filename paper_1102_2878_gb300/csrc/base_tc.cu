@@ -390,8 +390,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
       const unsigned norm_a = h2u(__floats2half2_rn(pow2i(item.s), pow2i(item.s)));
       const int ne = item.ne;
       // this thread's reference row of the next tile, loaded one tile ahead
-      // so the global reads overlap the tile before
-      float rv[DM];
+      // so the global reads overlap the tile before (raw: nothing uses the
+      // loaded values until the row is staged)
+      float4 rv4[DM / 4];
       bool r_ok = false;
       int ent = 0;  // entry of this thread's reference in the last fetched tile
       auto fetch = [&](int tile) {
@@ -413,14 +414,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
           ent = lo;
           const float* src = R.pts + (size_t)(sRb[lo] + J - sOff[lo]) * R.dp;
 #pragma unroll
-          for (int k4 = 0; k4 < DM / 4; ++k4) {
-            float4 a4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (4 * k4 < R.dp) a4 = __ldg(reinterpret_cast<const float4*>(src) + k4);
-            rv[4 * k4] = a4.x - mloc[4 * k4];
-            rv[4 * k4 + 1] = a4.y - mloc[4 * k4 + 1];
-            rv[4 * k4 + 2] = a4.z - mloc[4 * k4 + 2];
-            rv[4 * k4 + 3] = a4.w - mloc[4 * k4 + 3];
-          }
+          for (int k4 = 0; k4 < DM / 4; ++k4)
+            rv4[k4] = 4 * k4 < R.dp ? __ldg(reinterpret_cast<const float4*>(src) + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       };
       bool ok = true;
@@ -466,6 +461,14 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
           }
           unsigned char* tB = tB0 + b * SH::TILE;
           if (r_ok) {
+            float rv[DM];
+#pragma unroll
+            for (int k4 = 0; k4 < DM / 4; ++k4) {
+              rv[4 * k4] = rv4[k4].x - mloc[4 * k4];
+              rv[4 * k4 + 1] = rv4[k4].y - mloc[4 * k4 + 1];
+              rv[4 * k4 + 2] = rv4[k4].z - mloc[4 * k4 + 2];
+              rv[4 * k4 + 3] = rv4[k4].w - mloc[4 * k4 + 3];
+            }
             unsigned rh[DM / 2], rl[DM / 2];
 #pragma unroll
             for (int k = 0; k < DM; k += 2) split2(rv[k] * sr, rv[k + 1] * sr, rh[k / 2], rl[k / 2]);
