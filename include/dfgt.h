@@ -198,17 +198,21 @@ dfgt_status dfgt_grad(dfgt_ctx* ctx, const float* x_dev, int64_t n, int d, const
 
 /* Choose the tree options that make a dual-tree sum of these points
  * fastest on this GPU.  No counterpart in the paper (its leaf size is
- * unstated): the leaf size and the exact-sum threshold base_block trade
- * traversal work against exact-sum work, and the best pair depends on the
- * data, the bandwidths and eps.  Builds a tree over points_dev (float32
- * [n][d], device, caller-owned, not modified) for each candidate
- * (leaf_size 32, 64, 96, 128, 160, 192; base_block 2048, 4096, 8192), runs
- * dfgt_sum(tree, tree, h_host[0..nh), eps) trials + 1 times and keeps the
- * fastest of the last `trials` runs (build and sum, CUDA events on the
- * context's stream).  `best` is read for p_max and eps_fp, which are kept,
- * and receives the chosen options; best_ms (may be NULL) the time of one
- * build and sum with them.  1 <= trials <= 16.  Results of the trial sums
- * are discarded.  Errors as for dfgt_build and dfgt_sum. */
+ * unstated, and its p_max table is an upper limit, Section 3.6): the leaf
+ * size, the exact-sum block base_block and the expansion order limit trade
+ * traversal work, series work and exact-sum work, and the best choice
+ * depends on the data, the bandwidths and eps.  Builds a tree over
+ * points_dev (float32 [n][d], device, caller-owned, not modified) for each
+ * candidate (leaf_size 32, 64, 96, 128, 160, 192; base_block 2048, 4096,
+ * 8192; p_max the paper's table value and one below it, or the caller's
+ * best->p_max alone if it is > 0), runs dfgt_sum(tree, tree,
+ * h_host[0..nh), eps) trials + 1 times and keeps the fastest of the last
+ * `trials` runs (build and sum, CUDA events on the context's stream).
+ * `best` is read for p_max and eps_fp (eps_fp is kept) and receives the
+ * chosen options; best_ms (may be NULL) the time of one build and sum
+ * with them.  1 <= trials <= 16.  Results of the trial sums are discarded;
+ * every candidate keeps the guarantee of Definition 1.2.  Errors as for
+ * dfgt_build and dfgt_sum. */
 dfgt_status dfgt_autotune(dfgt_ctx* ctx, const float* points_dev, int64_t n, int d,
                           const double* h_host, int nh, double eps, int trials,
                           dfgt_opts* best, double* best_ms);

@@ -278,8 +278,9 @@ def cv_likelihood(ctx: Context, points, log_h):
 
 
 def autotune(ctx: Context, points, hs, eps: float, trials: int = 2, p_max: int = 0, eps_fp: float = 0.0):
-    """dfgt_autotune: the leaf size and exact-sum threshold that make a
-    build + sum of these points fastest; returns (options dict, ms)."""
+    """dfgt_autotune: the leaf size, exact-sum threshold and expansion order
+    limit that make a build + sum of these points fastest; returns (options
+    dict, ms).  p_max > 0 fixes the order instead of searching it."""
     torch = _torch()
     if not (isinstance(points, torch.Tensor) and points.is_cuda and points.dtype == torch.float32
             and points.dim() == 2):

@@ -675,18 +675,27 @@ dfgt_status dfgt_autotune(dfgt_ctx* ctx, const float* points_dev, int64_t n, int
   if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, DFGT_EINVAL, "dfgt_autotune: need 0 < eps < 1");
   CK(cudaSetDevice(ctx->device));
   CK(ctx->io_g.ensure((size_t)nh * n * sizeof(double)));
-  // candidates: leaf sizes and exact-sum thresholds
+  // candidates: leaf sizes, exact-sum thresholds (the block |Q| |R| of one
+  // exact sum) and, unless the caller fixed it, the expansion order limit
+  // p_max and one below it (fewer coefficients per node against fewer
+  // pairs that a series can take)
   const int leaves[] = {32, 64, 96, 128, 160, 192};
   const long long blocks[] = {2048, 4096, 8192};
   dfgt_opts start = *best;
+  const int pm_table = pmax_of(d);
+  int orders[2] = {start.p_max > 0 ? std::min(start.p_max, pm_table) : pm_table, 0};
+  int norders = 1;
+  if (start.p_max <= 0 && pm_table > 1) orders[norders++] = pm_table - 1;
   double best_t = 1e300;
   dfgt_opts chosen = start;
+  for (int oi = 0; oi < norders; ++oi)
   for (int leaf : leaves) {
     if (leaf > kMaxLeaf) continue;
     for (long long bb : blocks) {
       dfgt_opts o = start;
       o.leaf_size = leaf;
       o.base_block = bb;
+      o.p_max = orders[oi];
       double tmin = 1e300;
       for (int rep = 0; rep <= trials; ++rep) {  // the first run warms up and is not counted
         CK(cudaEventRecord(ctx->ev[4], ctx->stream));

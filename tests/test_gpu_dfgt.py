@@ -154,11 +154,25 @@ def test_autotune_picks_a_candidate_and_stays_exact(dev, orc):
     opts, ms = dfgt.autotune(dev, pts, hs, eps, trials=1)
     assert opts["leaf_size"] in (32, 64, 96, 128, 160, 192)
     assert opts["base_block"] in (2048, 4096, 8192)
+    assert opts["p_max"] in (6, 5)  # D = 2: the paper's p_max = 6, or one below it
     assert ms > 0
-    t = dfgt.Tree(dev, pts, leaf_size=opts["leaf_size"], base_block=opts["base_block"])
+    t = dfgt.Tree(dev, pts, leaf_size=opts["leaf_size"], base_block=opts["base_block"], p_max=opts["p_max"])
     G, _ = dfgt.kde_sum(dev, t, t, hs, eps)
     ref = orc.naive_kde(x.astype(np.float64), x.astype(np.float64), hs[0])
     assert np.all(np.abs(G.cpu().numpy()[0] - ref) <= eps * ref)
+
+
+def test_autotune_keeps_a_fixed_order_and_each_order_stays_exact(dev, orc):
+    # a caller's p_max is kept; every order the search tries keeps eps
+    x, hs, eps = datagen.workload("kde2d_n1e4")
+    pts = to_cuda(x)
+    opts, _ = dfgt.autotune(dev, pts, hs, eps, trials=1, p_max=4)
+    assert opts["p_max"] == 4
+    ref = orc.naive_kde(x.astype(np.float64), x.astype(np.float64), hs[0])
+    for p in (6, 5, 4):
+        t = dfgt.Tree(dev, pts, p_max=p)
+        G, st = dfgt.kde_sum(dev, t, t, hs, eps)
+        assert np.all(np.abs(G.cpu().numpy()[0] - ref) <= eps * ref), p
 
 
 def test_query_batches_match_single_calls(dev):

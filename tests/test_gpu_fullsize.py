@@ -46,5 +46,44 @@ def test_kde5d_n5e5(dev, orc):
     run_workload(dev, orc, "kde5d_n5e5", 64)
 
 
-def test_kde16d_manifold(dev, orc):
-    run_workload(dev, orc, "kde16d_n1e6_sweep8", 24, n=200_000)
+def test_kde16d_n1e6_sweep8(dev, orc):
+    # the benchmark's default workload at its full size (D = 16, 1e6 points,
+    # 8 bandwidths): tensor-core and direct exact sums both take part
+    st = run_workload(dev, orc, "kde16d_n1e6_sweep8", 48)
+    assert 0 < st["base_expanded"] < st["base_interactions"]
+
+
+@pytest.mark.parametrize("eps_index", [0, 1])
+def test_kde32d_r1e6_batches(dev, orc, eps_index):
+    # the bichromatic D = 32 recipe at its full reference size (1e6 points):
+    # the smallest, a middle and the largest of the 64 uneven query batches,
+    # all 16 bandwidths, every sampled query against the oracle's log G
+    # (Definition 1.2 in log form: most small-bandwidth sums underflow)
+    refs, batches, hs, eps_list = datagen.bichromatic("kde32d_r1e6_q64batches")
+    eps = eps_list[eps_index]
+    sizes = np.array([len(b) for b in batches])
+    order = np.argsort(sizes)
+    pick = [order[0], order[len(order) // 2], order[-1]] if eps_index == 0 else [order[len(order) // 2]]
+    # at eps = 1e-3 the trees reserve 5e-4 for float32 rounding, as the
+    # reduced-size bichromatic test does: far queries' exact sums carry
+    # exponents of 30..60, whose rounding the default 20% of eps would not cover
+    efp = 0.0 if eps_index == 0 else 5e-4
+    rt = dfgt.Tree(dev, to_cuda(refs), eps_fp=efp)
+    r64 = refs.astype(np.float64)
+    rng = np.random.default_rng(99 + eps_index)
+    underflow = 0
+    for bi in pick:
+        qx = batches[bi]
+        qt = dfgt.Tree(dev, to_cuda(qx), eps_fp=efp)
+        G, L, st = dfgt.kde_sum_log(dev, qt, rt, hs, eps)
+        G, L = G.cpu().numpy(), L.cpu().numpy()
+        assert np.all(np.isfinite(L))
+        sample = rng.choice(len(qx), size=min(len(qx), 12), replace=False)
+        q64 = qx.astype(np.float64)[sample]
+        for i, h in enumerate(hs):
+            ref_log = orc.log_naive_kde(q64, r64, h)
+            err = np.abs(np.expm1(L[i][sample] - ref_log))
+            assert np.all(err <= eps), (bi, h, float(err.max()))
+            underflow += int((ref_log < np.log(1e-30)).sum())
+        qt.close()
+    assert underflow > 0
