@@ -8,10 +8,13 @@
 // tensor form, marks its entries (k_base_hd skips them) and lists it as
 // work items of up to kItemEntries entries with its scales.
 //
-// k_base_tc is persistent: each CTA takes work items in turn.  Four
-// producer warps stage the operands in shared memory and one of their
-// threads issues the MMAs; four consumer warps read the results back from
-// tensor memory and sum the exponentials.  Per item and block of up to 128
+// k_base_tc is persistent: each CTA takes a contiguous range of work items
+// of about equal cost (the plan's one packed atomic per run gives every item
+// its index and the summed cost before it).  Four producer warps stage the
+// operands in shared memory; the producer that stages a tile's last row
+// (counted by an acquire-release shared counter) issues its MMAs, so no
+// producer waits for another.  Four consumer warps read the results back
+// from tensor memory and sum the exponentials.  Per item and block of up to 128
 // queries, producer thread p stages query row p of A: the float16 splits
 // of W_q 2^a = Wh + Wl (W_q = -2c q~) laid out as Wh | Wh | Wl | 2^s 2^s
 // along K; per tile of 128 references it stages reference row p of B:
@@ -145,22 +148,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
   return false;
 }
 
-__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
-}
-
 __device__ __forceinline__ void kahan(float& S, float& C, float v) {
   const float y = v - C;
   const float t = S + y;
@@ -237,8 +224,25 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// barrier of the four producer warps only
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Shared-memory counter increment with acquire-release order at block scope:
+// each producer's staged row (made visible to the async proxy before) is
+// ordered before the MMAs of whichever producer sees the count complete.
+__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* c) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], 1;" : "=r"(old) : "r"(smem_addr(c)) : "memory");
+  return old;
+}
+
+// barrier of the four producer warps only, returning the AND of v over them
+__device__ __forceinline__ bool producers_sync_and(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.b32 p, %1, 0;\nbar.red.and.pred q, 1, 128, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
 
 constexpr int kItemEntries = 256;  // base entries per work item at most
 
@@ -248,8 +252,23 @@ struct TcItem {
   int hidx, qnode;   // bandwidth, query node
   int qb, qn, tot;   // first query, queries, references of the item
   int a, b, s;       // scales (the run's)
-  int pad[2];
+  int pad;
+  unsigned long long cpre;  // summed cost of the items before this one
 };
+
+// Work of an item in tile units: each 128-query block streams the item's
+// reference tiles, plus about one tile of setup.
+__device__ __forceinline__ unsigned long long item_cost(int qn, int tot) {
+  return (unsigned long long)((qn + kTcRows - 1) / kTcRows) * (unsigned long long)((tot + kTcRows - 1) / kTcRows + 1);
+}
+
+// The plan's counter packs the item count (low kItemCountBits; lists hold at
+// most 2^28 entries) and the summed cost of the items (the rest, 2^35 tile
+// units), so that one atomic gives an item both its index and its cost prefix,
+// in the same order. A sum that would pass 2^35 sets the plan's overflow word
+// and the CTAs then take the items in turn instead.
+constexpr int kItemCountBits = 29;
+constexpr unsigned long long kItemCountMask = (1ull << kItemCountBits) - 1;
 
 // Plan: one warp per key (bandwidth, query node) of the counting sort; the
 // key's entries are [end - cnt, end).
@@ -258,7 +277,7 @@ __global__ void __launch_bounds__(256) k_tc_plan(TreeView Q, TreeView R, const i
                                                  const int* __restrict__ cnt, const int* __restrict__ end, int nkeys,
                                                  const float* __restrict__ c2v, const float* __restrict__ inv2h2_up,
                                                  float exp_err, unsigned char* __restrict__ tcflag,
-                                                 TcItem* __restrict__ items, int* __restrict__ n_items,
+                                                 TcItem* __restrict__ items, unsigned long long* __restrict__ plan_ctr,
                                                  unsigned long long* __restrict__ tc_ctr) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -292,27 +311,56 @@ __global__ void __launch_bounds__(256) k_tc_plan(TreeView Q, TreeView R, const i
   for (int i = lane; i < c; i += 32) tcflag[b0 + i] = tc ? 1 : 0;
   if (!tc) return;
   const int nparts = (c + kItemEntries - 1) / kItemEntries;
-  int k = 0;
-  if (lane == 0) {
-    k = atomicAdd(n_items, nparts);
-    atomicAdd(tc_ctr, (unsigned long long)qn * (unsigned long long)tot);
-  }
-  k = __shfl_sync(FULL, k, 0);
-  const int qb = Q.beg[q];
-  for (int j = 0; j < nparts; ++j) {
+  // the parts' references: counted once for the summed cost, again for the items
+  auto part_refs = [&](int j) {
     const int i0 = b0 + j * kItemEntries, ne = min(kItemEntries, c - j * kItemEntries);
     int pt = 0;
     for (int i = lane; i < ne; i += 32) pt += R.cnt[rsorted[i0 + i] & kNodeMask];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) pt += __shfl_xor_sync(FULL, pt, o);
-    if (lane == 0) items[k + j] = TcItem{i0, ne, hidx, q, qb, qn, pt, sc.a, sc.b, sc.s, {0, 0}};
+    return pt;
+  };
+  unsigned long long cost = 0;
+  for (int j = 0; j < nparts; ++j) cost += item_cost(qn, part_refs(j));
+  unsigned long long old = 0;
+  if (lane == 0) {
+    old = atomicAdd(plan_ctr, (cost << kItemCountBits) | (unsigned long long)nparts);
+    if ((old >> kItemCountBits) + cost >= (1ull << (64 - kItemCountBits)) || cost >= (1ull << (64 - kItemCountBits)))
+      atomicOr(reinterpret_cast<unsigned int*>(plan_ctr + 1), 1u);
+    atomicAdd(tc_ctr, (unsigned long long)qn * (unsigned long long)tot);
   }
+  old = __shfl_sync(FULL, old, 0);
+  const int k = (int)(old & kItemCountMask);
+  unsigned long long cpre = old >> kItemCountBits;
+  const int qb = Q.beg[q];
+  for (int j = 0; j < nparts; ++j) {
+    const int i0 = b0 + j * kItemEntries, ne = min(kItemEntries, c - j * kItemEntries);
+    const int pt = part_refs(j);
+    if (lane == 0) items[k + j] = TcItem{i0, ne, hidx, q, qb, qn, pt, sc.a, sc.b, sc.s, 0, cpre};
+    cpre += item_cost(qn, pt);
+  }
+}
+
+// Items [first, last) of CTA c of G: those whose cost interval has its middle
+// in [c T / G, (c + 1) T / G), T the summed cost (items are in prefix order,
+// so each CTA takes a contiguous range of about T / G).
+__device__ __forceinline__ int items_owner(const TcItem& it, unsigned long long T, int G) {
+  const unsigned long long mid2 = 2 * it.cpre + item_cost(it.qn, it.tot);
+  return (int)(mid2 * (unsigned long long)G / (2 * T));
+}
+__device__ int items_lower_bound(const TcItem* items, int n, unsigned long long T, int G, int c) {
+  int lo = 0, hi = n;  // first item whose owner is >= c
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (items_owner(items[mid], T, G) < c) lo = mid + 1; else hi = mid;
+  }
+  return lo;
 }
 
 template <int DM>
 __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     k_base_tc(TreeView Q, TreeView R, const int* __restrict__ rsorted, const TcItem* __restrict__ items,
-              const int* __restrict__ n_items_p, const float* __restrict__ c2v, double* __restrict__ gacc,
+              const unsigned long long* __restrict__ plan_ctr, const float* __restrict__ c2v, double* __restrict__ gacc,
               int* __restrict__ status) {
   using SH = TcShape<DM>;
   extern __shared__ __align__(1024) unsigned char dsm[];
@@ -320,16 +368,24 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
   unsigned char* const tB0 = dsm + SH::TILE;
   __shared__ int sOff[kItemEntries], sRb[kItemEntries];
   __shared__ int sAbort;   // a wait ran out: every role leaves at its next check
-  __shared__ int sProdOk[2];  // the producers' thread 0 saw its wait complete; read by all producers
-                              // after their named barrier, so they decide alike (two slots used in
-                              // turn: a slot is written again only after every producer passed the
-                              // barrier that follows its last read)
   __shared__ uint32_t sTmem;
   __shared__ __align__(8) uint64_t sDone[2], sFree[2];  // mma_done, acc_free
+  __shared__ uint32_t sArr[2];  // producer rows staged into B buffer 0 / 1 (all tiles so far)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const unsigned FULL = 0xffffffffu;
-  const int n_items = *n_items_p;
-  if ((int)blockIdx.x >= n_items) return;
+  const unsigned long long ctr = *plan_ctr;
+  const int n_items = (int)(ctr & kItemCountMask);
+  const unsigned long long T = ctr >> kItemCountBits;
+  const bool in_turn = *reinterpret_cast<const unsigned int*>(plan_ctr + 1) != 0;
+  if (n_items == 0) return;
+  __shared__ int sRange[2];
+  if (tid < 2)
+    sRange[tid] = in_turn ? 0 : items_lower_bound(items, n_items, T, gridDim.x, blockIdx.x + tid);
+  __syncthreads();
+  // a contiguous range of about T / G, or (after an overflow) every G-th item
+  const int it0 = in_turn ? (int)blockIdx.x : sRange[0], it1 = in_turn ? n_items : sRange[1];
+  const int istep = in_turn ? (int)gridDim.x : 1;
+  if (it0 >= it1) return;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&sTmem)),
@@ -343,6 +399,7 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&sFree[1])), "r"(kTcCons));
     asm volatile("fence.mbarrier_init.release.cluster;");
     sAbort = 0;
+    sArr[0] = sArr[1] = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -350,10 +407,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
   const uint32_t tmem = sTmem;
   const bool producer = warp >= 4;
   const int p = tid - kTcCons;  // producer row
-  uint32_t g = 0;               // tiles so far (both roles count alike)
-  uint32_t pub = 0;             // producers: outcomes published through sProdOk
+  uint32_t g = 0;               // tiles so far (every role counts alike)
+  bool pdead = false;           // producers: a wait of this thread ran out
 
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  for (int it = it0; it < it1; it += istep) {
     const TcItem item = items[it];
     const float c2 = c2v[item.hidx];
     const int ntiles = (item.tot + kTcRows - 1) / kTcRows;
@@ -385,7 +442,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
           base += __shfl_sync(FULL, incl, 31);
         }
       }
-      producers_sync();
+      // every producer reaches this barrier once per item; it also decides,
+      // for all of them alike, whether to go on after a wait has run out
+      if (!producers_sync_and(!pdead && !sAbort)) break;
       const float sw = pow2i(item.a), sr = pow2i(item.b), sbr = pow2i(item.a + item.b - item.s);
       const unsigned norm_a = h2u(__floats2half2_rn(pow2i(item.s), pow2i(item.s)));
       const int ne = item.ne;
@@ -418,15 +477,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
             rv4[k4] = 4 * k4 < R.dp ? __ldg(reinterpret_cast<const float4*>(src) + k4) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       };
-      bool ok = true;
-      for (int qs = 0; qs < item.qn && ok; qs += kTcRows) {
+      for (int qs = 0; qs < item.qn && !pdead; qs += kTcRows) {
         const int qcnt = min(kTcRows, item.qn - qs);
-        // A is read by every MMA of the previous block: thread 0 waits for
-        // the last one, the others learn the outcome at the named barrier
-        if (p == 0) sProdOk[pub & 1] = (g == 0 || mbar_wait(&sDone[(g - 1) & 1], ((g - 1) >> 1) & 1u)) && !sAbort;
-        producers_sync();
-        if (!sProdOk[pub++ & 1]) {
-          ok = false;
+        // A is read by every MMA of the previous block: each producer waits
+        // for the last one before it rewrites its row
+        if (g > 0 && !mbar_wait(&sDone[(g - 1) & 1], ((g - 1) >> 1) & 1u)) {
+          pdead = true;
           break;
         }
         if (p < qcnt) {
@@ -450,14 +506,11 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
         fetch(0);
         for (int i = 0; i < ntiles; ++i, ++g) {
           const int b = g & 1;
-          // accumulator b and B buffer b are free once the consumers are done with tile g - 2
-          if (g >= 2) {
-            if (p == 0) sProdOk[pub & 1] = mbar_wait(&sFree[b], ((g >> 1) - 1) & 1u) && !sAbort;
-            producers_sync();
-            if (!sProdOk[pub++ & 1]) {
-              ok = false;
-              break;
-            }
+          // accumulator b and B buffer b are free once the consumers are done
+          // with tile g - 2; each producer waits itself before writing its row
+          if (g >= 2 && !mbar_wait(&sFree[b], ((g >> 1) - 1) & 1u)) {
+            pdead = true;
+            break;
           }
           unsigned char* tB = tB0 + b * SH::TILE;
           if (r_ok) {
@@ -479,9 +532,11 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
           } else {
             zero_row<DM>(tB, p);
           }
+          // the row (and, on the block's first tile, the A row) is handed to
+          // the tensor cores' proxy; the producer that stages the tile's last
+          // row issues its MMAs, so no producer waits for another
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          producers_sync();
-          if (p == 0) {
+          if ((atom_add_acq_rel(&sArr[b]) & (kTcRows - 1)) == kTcRows - 1) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_addr(tA), b0 = smem_addr(tB);
             const uint32_t dcol = tmem + (uint32_t)(b * kTcRows);
@@ -501,14 +556,9 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
           if (i + 1 < ntiles) fetch(i + 1);
         }
       }
-      if (!ok) {
-        if (p == 0) {
-          atomicOr(status, kStTimeout);
-          sAbort = 1;
-          // let the last issued MMA finish (bounded) before tensor memory is freed
-          if (g > 0) mbar_wait(&sDone[(g - 1) & 1], ((g - 1) >> 1) & 1u);
-        }
-        break;
+      if (pdead) {
+        atomicOr(status, kStTimeout);
+        sAbort = 1;
       }
     } else {
       // ---- consumers: row tid of each query block
@@ -579,7 +629,8 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcCols));
 }
 
-// The plan buffer: the item count, the items, then one flag per entry.
+// The plan buffer: the packed counter and the overflow word (256 bytes kept),
+// the items, then one flag per entry.
 size_t plan_items_offset() { return 256; }
 size_t plan_flags_offset(int n) { return (256 + (size_t)n * sizeof(TcItem) + 255) & ~(size_t)255; }
 
@@ -589,7 +640,7 @@ void plan_d(const TreeView& Q, const TreeView& R, const TravBuffers& b, const in
   k_tc_plan<DM><<<(nkeys + 7) / 8, 256, 0, s>>>(
       Q, R, rsorted, cnt, end, nkeys, b.c2, b.inv2h2_up, b.exp_err,
       reinterpret_cast<unsigned char*>(base + plan_flags_offset(n)),
-      reinterpret_cast<TcItem*>(base + plan_items_offset()), reinterpret_cast<int*>(base), b.base_exp);
+      reinterpret_cast<TcItem*>(base + plan_items_offset()), reinterpret_cast<unsigned long long*>(base), b.base_exp);
 }
 
 template <int DM>
@@ -604,7 +655,8 @@ cudaError_t sums_d(const TreeView& Q, const TreeView& R, const TravBuffers& b, c
   const int per_sm = smem <= 110 * 1024 ? kTcCtasPerSm : 1;
   const int grid = (int)std::min<long>((long)per_sm * b.sms, (long)n);
   k_base_tc<DM><<<grid, kTcThreads, smem, s>>>(Q, R, rsorted, reinterpret_cast<const TcItem*>(base + plan_items_offset()),
-                                               reinterpret_cast<const int*>(base), b.c2, b.gacc, b.status);
+                                               reinterpret_cast<const unsigned long long*>(base), b.c2, b.gacc,
+                                               b.status);
   return cudaGetLastError();
 }
 
@@ -616,7 +668,8 @@ cudaError_t launch_tc_plan(const TreeView& Q, const TreeView& R, const TravBuffe
   cudaError_t e = plan.ensure(plan_flags_offset(n) + (size_t)n + 256);
   if (e != cudaSuccess) return e;
   char* base = plan.as<char>();
-  if ((e = cudaMemsetAsync(base, 0, sizeof(int), s)) != cudaSuccess) return e;
+  // the packed counter and the overflow word
+  if ((e = cudaMemsetAsync(base, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
   if (Q.dp <= 8) plan_d<8>(Q, R, b, rsorted, cnt, end, nkeys, n, base, s);
   else if (Q.dp <= 16) plan_d<16>(Q, R, b, rsorted, cnt, end, nkeys, n, base, s);
   else plan_d<32>(Q, R, b, rsorted, cnt, end, nkeys, n, base, s);
