@@ -30,10 +30,12 @@
 // natural-log units), its scales fit, it has at least kHtMinQ queries and
 // holds no self entry (leave-one-out runs take the direct form, which
 // leaves the self interaction out exactly).  A term's relative error is
-// then at most 2^-21 + eps_fp / 4 + 2 kappa u x; for the exact sums of a
-// query to stay within eps_fp that needs its kernel-weighted mean exponent
-// x~ = sum K x / sum K below (3/4 eps_fp - 2^-21) / (2 kappa u), as for the
-// direct form's (D+3) u x (the self term K = 1 keeps x~ small when Q = R).
+// then at most 2^-21 + eps_fp / 4 + 2 kappa u x, and the float32 row sums
+// of positive terms add at most 9u (seven rounding levels per 64-column
+// part, Kahan across parts); for the exact sums of a query to stay within
+// eps_fp that needs its kernel-weighted mean exponent x~ = sum K x / sum K
+// below (3/4 eps_fp - 2^-21 - 9u) / (2 kappa u), as for the direct form's
+// (D+3) u x (the self term K = 1 keeps x~ small when Q = R).
 #pragma once
 
 #include "common.cuh"

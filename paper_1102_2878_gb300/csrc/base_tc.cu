@@ -25,7 +25,7 @@
 // 8-row groups, 2048 bytes between K groups of 8); D is float32 in tensor
 // memory, lane = query row, column = reference.  Two accumulators and two
 // B buffers alternate: the MMA of tile g + 1 runs while the consumers read
-// tile g (tcgen05.ld, 32 columns at a time) and add 2^(D 2^-(a+b) + A_q)
+// tile g (tcgen05.ld, 64 columns at a time) and add 2^(D 2^-(a+b) + A_q)
 // with ex2.approx into Kahan-compensated row sums.  mbarriers order the
 // roles: mma_done[b] (tcgen05.commit) tells the consumers a tile is in
 // accumulator b, acc_free[b] (128 consumer arrivals) tells the producers
@@ -600,21 +600,20 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const int tn = min(kTcRows, item.tot - i * kTcRows);
           const uint32_t base = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(b * kTcRows);
-          // the next 32 columns load while these are summed
+          // 64 columns per step: both 32-column loads in flight together,
+          // then two independent chunk sums into one Kahan update
           uint32_t ra[32], rb[32];
-          tc_ld32_async(base, ra);
-          tc_wait32(ra);
           for (int c0 = 0; c0 < tn; c0 += 64) {
             const bool more = c0 + 32 < tn;
+            tc_ld32_async(base + c0, ra);
             if (more) tc_ld32_async(base + c0 + 32, rb);
-            if (row_ok) kahan(acc, comp, ex2_sum32(ra, sout, Aq, tn - c0));
-            if (!more) break;
-            tc_wait32(rb);
-            const bool more2 = c0 + 64 < tn;
-            if (more2) tc_ld32_async(base + c0 + 64, ra);
-            if (row_ok) kahan(acc, comp, ex2_sum32(rb, sout, Aq, tn - c0 - 32));
-            if (!more2) break;
             tc_wait32(ra);
+            tc_wait32(rb);
+            if (row_ok) {
+              float part = ex2_sum32(ra, sout, Aq, tn - c0);
+              if (more) part += ex2_sum32(rb, sout, Aq, tn - c0 - 32);
+              kahan(acc, comp, part);
+            }
           }
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           mbar_arrive(&sFree[b]);
