@@ -2,7 +2,10 @@
 
 One step = one full dual-tree sum of the workload: build the kd-tree and
 raw moments of the points (Q = R), then dfgt_sum over every bandwidth of
-the workload at eps.  The metric is effective query-reference pairs per
+the workload at eps.  For a bichromatic workload (a reference set and
+uneven query batches) a step builds the reference tree and one query tree
+over all batches and sums them in log form (dfgt_sum_log: every query
+within eps, including sums below the float range) at the first eps.  The metric is effective query-reference pairs per
 second, |Q| |R| n_h / time, next to the GPU brute force on the same data.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dfgt|reference]
@@ -41,6 +44,10 @@ DEFAULT_WORKLOAD = "kde16d_n1e6_sweep8"
 # ex2 per clock per SM: the unit takes 32 ex2 per clock per SM (8 per
 # sub-partition)
 SM_COUNT, SFU_EX2_PER_CLK_PER_SM = 152, 32
+# queries per query tree of a bichromatic workload's batch groups (the
+# frontier of a larger group could pass 2^28 node pairs at the large
+# bandwidths of D = 32, where nothing prunes)
+GROUP_QUERIES = 200_000
 
 
 def dist_env():
@@ -218,7 +225,33 @@ def roofline_by_kernel(stats, tinfo, N, D, nh, sm_clk, hbm_gbs):
     return out
 
 
-def cpu_oracle_rate(x, hs, target_s, seed=0):
+def load_problem(name, n):
+    """(queries, references or None for Q = R, bandwidths, eps, query batch
+    sizes or None) of a named workload; ``n`` gives a smaller case (points,
+    or references of a bichromatic workload)."""
+    if name in datagen.BICHROMATIC:
+        refs, batches, hs, eps_list = datagen.bichromatic(name, nr=n)
+        return (np.ascontiguousarray(np.concatenate(batches)), refs, hs, eps_list[0],
+                [len(b) for b in batches])
+    x, hs, eps = datagen.workload(name, n)
+    return x, None, hs, eps, None
+
+
+def query_groups(sizes, limit):
+    """Query index spans [a, b) of consecutive batches holding at most
+    ``limit`` queries each (a larger batch is a span of its own)."""
+    spans, a, b = [], 0, 0
+    for m in sizes:
+        if b > a and b - a + m > limit:
+            spans.append((a, b))
+            a = b
+        b += m
+    if b > a:
+        spans.append((a, b))
+    return spans
+
+
+def cpu_oracle_rate(x, hs, target_s, seed=0, r=None):
     """Time the FP64 oracle's exact sums on a bounded query sample (all
     references, all bandwidths), in batches grown until about target_s of
     work is done; returns (pairs/s, sample description, cores, seconds)."""
@@ -226,35 +259,36 @@ def cpu_oracle_rate(x, hs, target_s, seed=0):
 
     oracle.build()
     x64 = x.astype(np.float64)
+    r64 = x64 if r is None else r.astype(np.float64)
     rng = np.random.default_rng(seed)
     order = rng.permutation(len(x))
-    oracle.naive_kde(x64[order[:16]], x64, hs[0])  # thread pool and pages warm
-    done, spent, batch = 0, 0.0, 64
+    oracle.naive_kde(x64[order[:16]], r64, hs[0])  # thread pool and pages warm
+    done, spent, batch = 0, 0.0, 16
     while done < len(x) and spent < target_s:
         sel = x64[order[done:done + batch]]
         t0 = time.perf_counter()
         for h in hs:
-            oracle.naive_kde(sel, x64, h)
+            oracle.naive_kde(sel, r64, h)
         dt = time.perf_counter() - t0
         spent += dt
         done += len(sel)
         per_query = dt / len(sel)
-        batch = int(max(64, min(len(x) - done, (target_s - spent) / max(per_query, 1e-9))))
-    pairs = done * len(x) * len(hs)
+        batch = int(max(16, min(len(x) - done, (target_s - spent) / max(per_query, 1e-9))))
+    pairs = done * len(r64) * len(hs)
     cores = oracle.num_threads()
-    desc = f"{done} of {len(x)} queries x all {len(x)} references x {len(hs)} bandwidths, {spent:.1f} s"
+    desc = f"{done} of {len(x)} queries x all {len(r64)} references x {len(hs)} bandwidths, {spent:.1f} s"
     return pairs / spent, desc, cores, spent
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    x, hs, eps = datagen.workload(args.workload, args.n)
+    x, r, hs, eps, _ = load_problem(args.workload, args.n)
     vals, secs = [], []
     desc, cores = "", 0
     per_step = max(2.0, min(12.0, 150.0 / max(1, args.steps + args.warmup)))
     for i in range(args.warmup + args.steps):
-        v, desc, cores, sec = cpu_oracle_rate(x, hs, per_step, seed=i)
+        v, desc, cores, sec = cpu_oracle_rate(x, hs, per_step, seed=i, r=r)
         if i >= args.warmup:
             vals.append(v)
             secs.append(sec)
@@ -264,7 +298,8 @@ def run_reference(args, rank, world):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "D": x.shape[1], "N": len(x), "nh": len(hs),
-                       "eps": eps, "q_eq_r": True},
+                       "eps": eps, "q_eq_r": r is None,
+                       **({} if r is None else {"n_ref": len(r)})},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": desc + " per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -278,11 +313,13 @@ def run_dfgt(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dfgt.build()
-    x, hs, eps = datagen.workload(args.workload, args.n)
+    x, r, hs, eps, sizes = load_problem(args.workload, args.n)
     x = replica_points(x, rank)  # independent replica per rank (weak scaling)
     N, D, nh = x.shape[0], x.shape[1], len(hs)
+    NR = N if r is None else r.shape[0]
     ctx = dfgt.Context(local)
     pts = torch.from_numpy(x).to(f"cuda:{local}")
+    rpts = pts if r is None else torch.from_numpy(r).to(f"cuda:{local}")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     torch.cuda.synchronize()
 
@@ -291,6 +328,16 @@ def run_dfgt(args, rank, world, local):
 
     def step():
         ev_build[0].record(ctx.stream)
+        if r is not None:
+            # the reference tree, then the batches in groups of query trees
+            rtree = dfgt.Tree(ctx, rpts)
+            ev_build[1].record(ctx.stream)
+            outs, st = dfgt.kde_sum_batches(ctx, list(torch.split(pts, sizes)), rtree, hs, eps,
+                                            max_queries=GROUP_QUERIES, log=True)
+            tinfo.append(rtree.info())
+            rtree.close()
+            st["ms_build"] = ev_build[0].elapsed_time(ev_build[1])
+            return torch.cat([g for g, _ in outs], dim=1), st
         tree = dfgt.Tree(ctx, pts)
         ev_build[1].record(ctx.stream)
         G, st = dfgt.kde_sum(ctx, tree, tree, hs, eps)
@@ -329,25 +376,25 @@ def run_dfgt(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    pairs_step = N * N * nh
+    pairs_step = N * NR * nh
     value = world * pairs_step / (ms / 1e3)
 
     if args.only_dfgt:
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": world * N * N * nh / (ms / 1e3), "unit": UNIT,
+            print(json.dumps({"metric": METRIC, "value": world * pairs_step / (ms / 1e3), "unit": UNIT,
                               "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
                               "config": {"workload": args.workload, "N": N}, "note": "dual-tree steps only"}))
         ctx.close()
         return
     # GPU brute force on the same data (the comparison named by the metric)
-    Gb = dfgt.kde_sum_bruteforce(ctx, pts, pts, hs)
+    Gb = dfgt.kde_sum_bruteforce(ctx, pts, rpts, hs)
     bf_ms = []
     for _ in range(max(2, min(args.steps, 3))):
         with torch.cuda.stream(ctx.stream):
             flush.fill_(1.0)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(ctx.stream)
-        dfgt.kde_sum_bruteforce(ctx, pts, pts, hs, out=Gb)
+        dfgt.kde_sum_bruteforce(ctx, pts, rpts, hs, out=Gb)
         e1.record(ctx.stream)
         e1.synchronize()
         bf_ms.append(e0.elapsed_time(e1))
@@ -358,11 +405,21 @@ def run_dfgt(args, rank, world, local):
     # end to end through the host-buffer C-ABI call (copies inside the timed region)
     xh = torch.from_numpy(x).pin_memory().numpy()
     Gh = torch.empty((nh, N), dtype=torch.float64).pin_memory().numpy()
-    dfgt.kde_host(ctx, xh, None, hs, eps, out=Gh)
+    rh = None if r is None else torch.from_numpy(r).pin_memory().numpy()
+    # a bichromatic workload goes through the host call once per batch group
+    spans = [(0, N)] if r is None else query_groups(sizes, GROUP_QUERIES)
+    Gparts = [Gh] if r is None else [torch.empty((nh, b - a), dtype=torch.float64).pin_memory().numpy()
+                                     for a, b in spans]
+
+    def host_step():
+        for (a, b), out in zip(spans, Gparts):
+            dfgt.kde_host(ctx, xh[a:b], rh, hs, eps, out=out)
+
+    host_step()
     e2e_t = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        dfgt.kde_host(ctx, xh, None, hs, eps, out=Gh)
+        host_step()
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_t)
 
@@ -387,22 +444,31 @@ def run_dfgt(args, rank, world, local):
         else:
             roof_units, roof_ms = inter - expanded, roof_ms - tc_ms
             kernel = "k_base_hd (DFGTBase exact sums, direct form)"
+    unit, source = "pair-interactions/s", (f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz "
+                                           "(measured: independent ex2.approx chains retired 31.4 ex2/clk/SM)")
+    if kernel.startswith("k_base_hd"):
+        # the direct form is bound by the FMA pipe: 2D + 2 operations per interaction
+        roof_units *= 2 * D + 2
+        peak = SM_COUNT * FMA_PER_CLK_PER_SM * sm_clk * 1e6
+        unit, source = "FMA-pipe operations/s", (f"2D + 2 FMA-pipe operations per interaction: 152 SMs x 128 "
+                                                  f"FP32 lanes x {sm_clk:.0f} MHz")
     achieved = roof_units / (roof_ms / 1e3) if roof_ms > 0 else 0.0
     roof = {"bound": "alu", "kernel": kernel, "achieved": achieved,
-            "peak": peak, "unit": "pair-interactions/s", "frac": achieved / peak,
-            "traffic": base_traffic(args.workload),
-            "peak_source": f"one ex2 per interaction: 152 SMs x 32 ex2/clk x {sm_clk:.0f} MHz (measured: "
-                           "independent ex2.approx chains retired 31.4 ex2/clk/SM)"}
+            "peak": peak, "unit": unit, "frac": achieved / peak,
+            "traffic": base_traffic(args.workload), "peak_source": source}
     cpu_rate, cpu_desc, cores = (None, None, None)
     if not args.no_cpu_baseline:
-        cpu_rate, cpu_desc, cores, _ = cpu_oracle_rate(x, hs, args.cpu_seconds)
+        cpu_rate, cpu_desc, cores, _ = cpu_oracle_rate(x, hs, args.cpu_seconds, r=r)
     mean = lambda k: statistics.mean(s[k] for s in stats)  # noqa: E731
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "D": D, "N": N, "nh": nh,
-                   "h": [float(v) for v in hs], "eps": eps, "q_eq_r": True,
+                   "h": [float(v) for v in hs], "eps": eps, "q_eq_r": r is None,
+                   **({} if r is None else {"n_ref": NR, "query_batches": f"grouped into query trees of at most "
+                                                                          f"{GROUP_QUERIES} queries",
+                                            "sum": "dfgt_sum_log (e2e: dfgt_kde_host, plain G)"}),
                    "step": "kd-tree build + moments + dual-tree sum over all bandwidths",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -422,7 +488,8 @@ def run_dfgt(args, rank, world, local):
         "roofline_by_kernel": roofline_by_kernel(stats, tinfo, N, D, nh, sm_clk, peaks.get("hbm_gbs", 6800.0)),
         "cpu_baseline": None if cpu_rate is None else
         {"value": cpu_rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cpu_desc},
-        "e2e": {"value": pairs_step / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(x.nbytes),
+        "e2e": {"value": pairs_step / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(x.nbytes) + (0 if r is None else int(r.nbytes)),
                 "d2h_bytes_per_step": int(Gh.nbytes)},
         "clocks": clocks,
         "gpu_launches": int(launches),
@@ -437,7 +504,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["dfgt", "reference"], default="dfgt")
-    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(datagen.WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(datagen.WORKLOADS) + sorted(datagen.BICHROMATIC))
     ap.add_argument("--n", type=int, default=None,
                     help="points drawn from the workload's recipe (default: its own count); for small profiling cases")
     ap.add_argument("--no-cpu-baseline", action="store_true")

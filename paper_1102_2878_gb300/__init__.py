@@ -197,18 +197,56 @@ def kde_sum_loo(ctx: Context, tree: Tree, hs, eps: float, out=None):
 
 
 def kde_sum_batches(ctx: Context, query_batches, rtree: Tree, hs, eps: float, leaf_size: int = 0,
-                    base_block: int = 0, eps_fp: float = 0.0):
+                    base_block: int = 0, eps_fp: float = 0.0, max_queries: int = 1 << 18, log: bool = False):
     """Sums for several query batches against one reference tree.  A query's
-    sum does not depend on the other queries, so the batches are
-    concatenated into one query tree and summed in one call; returns one
-    [nh, n_b] float64 tensor per batch and the call's statistics."""
+    sum does not depend on the other queries, so consecutive batches are
+    concatenated into groups of at most ``max_queries`` queries (a larger
+    batch is a group of its own), each group into one query tree summed in
+    one call; a group whose frontier would pass the context's capacity
+    (DFGT_ECAPACITY) is halved and retried.  Returns one [nh, n_b] float64
+    tensor per batch (with ``log``: (G, log G) pairs from dfgt_sum_log) and
+    the summed work statistics."""
     torch = _torch()
     sizes = [int(b.shape[0]) for b in query_batches]
-    q = torch.cat([b.contiguous() for b in query_batches], dim=0)
-    qt = Tree(ctx, q, leaf_size=leaf_size, base_block=base_block, eps_fp=eps_fp)
-    G, st = kde_sum(ctx, qt, rtree, hs, eps)
-    qt.close()
-    return list(torch.split(G, sizes, dim=1)), st
+    groups, cur, cnt = [], [], 0
+    for i, m in enumerate(sizes):
+        if cur and cnt + m > max_queries:
+            groups.append(cur)
+            cur, cnt = [], 0
+        cur.append(i)
+        cnt += m
+    if cur:
+        groups.append(cur)
+    outs = [None] * len(sizes)
+    total = {}
+
+    def run(idx):
+        q = torch.cat([query_batches[i].contiguous() for i in idx], dim=0)
+        qt = Tree(ctx, q, leaf_size=leaf_size, base_block=base_block, eps_fp=eps_fp)
+        try:
+            if log:
+                G, L, st = kde_sum_log(ctx, qt, rtree, hs, eps)
+            else:
+                G, st = kde_sum(ctx, qt, rtree, hs, eps)
+        except DFGTError as e:
+            qt.close()
+            if e.status != "DFGT_ECAPACITY" or len(idx) == 1:
+                raise
+            run(idx[: len(idx) // 2])
+            run(idx[len(idx) // 2:])
+            return
+        qt.close()
+        parts = torch.split(G, [sizes[i] for i in idx], dim=1)
+        lparts = torch.split(L, [sizes[i] for i in idx], dim=1) if log else [None] * len(idx)
+        for i, g, lg in zip(idx, parts, lparts):
+            outs[i] = (g, lg) if log else g
+        for k, v in st.items():
+            if isinstance(v, (int, float)):
+                total[k] = total.get(k, 0) + v
+
+    for idx in groups:
+        run(idx)
+    return outs, total
 
 
 def cv_scores(ctx: Context, tree: Tree, hs, eps: float):

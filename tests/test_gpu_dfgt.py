@@ -175,17 +175,22 @@ def test_autotune_keeps_a_fixed_order_and_each_order_stays_exact(dev, orc):
         assert np.all(np.abs(G.cpu().numpy()[0] - ref) <= eps * ref), p
 
 
-def test_query_batches_match_single_calls(dev):
-    # batches concatenated into one query tree give the same sums as each
-    # batch summed on its own (both within eps of the brute force)
+def test_query_batches_match_single_calls(dev, orc):
+    # batches grouped into query trees (one per batch here) give every query's
+    # log-form sum within eps of the oracle's log G, underflowing sums included
     refs, batches, hs, _ = datagen.bichromatic("kde32d_r1e6_q64batches", nr=20_000, nbatch=4, batch_hi=4_000)
     rt = dfgt.Tree(dev, to_cuda(refs), eps_fp=5e-4)
     eps = 1e-2
-    outs, st = dfgt.kde_sum_batches(dev, [to_cuda(b) for b in batches], rt, hs[::4], eps, eps_fp=5e-4)
-    assert len(outs) == len(batches)
-    for b, Gb in zip(batches, outs):
-        ref = dfgt.kde_sum_bruteforce(dev, to_cuda(b), to_cuda(refs), hs[::4]).cpu().numpy()
-        Gb = Gb.cpu().numpy()
-        assert Gb.shape == ref.shape
-        big = ref >= 1e-30
-        assert np.all(np.abs(Gb[big] - ref[big]) <= (eps + 5e-4) * ref[big])
+    sizes = [len(b) for b in batches]
+    outs, st = dfgt.kde_sum_batches(dev, [to_cuda(b) for b in batches], rt, hs[::4], eps, eps_fp=5e-4,
+                                    max_queries=max(sizes) + 1, log=True)
+    assert len(outs) == len(batches) and st["rounds"] > 0
+    r64 = refs.astype(np.float64)
+    rng = np.random.default_rng(7)
+    for b, (G, L) in zip(batches, outs):
+        assert G.shape == L.shape == (len(hs[::4]), len(b))
+        L = L.cpu().numpy()
+        pick = rng.choice(len(b), size=min(len(b), 64), replace=False)
+        for i, h in enumerate(hs[::4]):
+            ref = orc.log_naive_kde(b.astype(np.float64)[pick], r64, h)
+            assert np.all(np.abs(np.expm1(L[i][pick] - ref)) <= eps), h
