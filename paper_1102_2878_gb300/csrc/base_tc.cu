@@ -233,6 +233,9 @@ __device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* c) {
   return old;
 }
 
+// barrier of the four producer warps only
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 // barrier of the four producer warps only, returning the AND of v over them
 __device__ __forceinline__ bool producers_sync_and(bool v) {
   uint32_t r;
@@ -419,7 +422,10 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
 #pragma unroll
       for (int k = 0; k < DM; ++k)
         mloc[k] = k < Q.d ? 0.5f * (Q.lo[(size_t)item.qnode * Q.d + k] + Q.hi[(size_t)item.qnode * Q.d + k]) : 0.f;
-      // ---- the item's reference table (warp 4), then the tiles
+      // ---- the item's reference table (warp 4), then the tiles; every
+      // producer is past its last read of the previous item's table (the
+      // fetches of its tiles) before warp 4 rewrites it
+      producers_sync();
       if (warp == 4) {
         int base = 0;
         for (int c0 = 0; c0 < item.ne; c0 += 32) {
@@ -480,8 +486,12 @@ __global__ void __launch_bounds__(kTcThreads, kTcCtasPerSm)
       for (int qs = 0; qs < item.qn && !pdead; qs += kTcRows) {
         const int qcnt = min(kTcRows, item.qn - qs);
         // A is read by every MMA of the previous block: each producer waits
-        // for the last one before it rewrites its row
-        if (g > 0 && !mbar_wait(&sDone[(g - 1) & 1], ((g - 1) >> 1) & 1u)) {
+        // for its last two tiles (a commit tracks only its own thread's
+        // MMAs, and the two tiles may have had different issuers; every
+        // earlier tile was consumed before these two were staged) before it
+        // rewrites its row
+        if ((g > 0 && !mbar_wait(&sDone[(g - 1) & 1], ((g - 1) >> 1) & 1u)) ||
+            (g > 1 && !mbar_wait(&sDone[g & 1], ((g - 2) >> 1) & 1u))) {
           pdead = true;
           break;
         }
