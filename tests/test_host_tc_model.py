@@ -3,7 +3,8 @@ D >= 6 (base_hd_forms.cuh), checked with numpy's float16 on the host: a
 float32 value scaled below 2^13 splits into float16 hi + lo with at most
 2^-22 of it left over while lo is normal, and the three products
 Wh rh + Wh rl + Wl rh miss W r by at most 12u of |W r| (u = 2^-24); an
-emulation of the whole form stays inside the bound the kernels use."""
+emulation of the whole form (operands, K layout, K16 steps, the
+consumers' fma) stays inside the bound the kernels use."""
 import numpy as np
 
 U = 2.0 ** -24
@@ -55,53 +56,80 @@ def f32(a):
     return np.asarray(a, dtype=np.float32)
 
 
-def emulate_exponent(q, r, m, c, a, b):
-    """The tensor form's exponent less A_q (base_hd_forms.cuh), emulated:
-    float32 set-up as on the device, float16 splits of W 2^a and r~ 2^b,
-    exact products, float32 accumulation onto C = B_r 2^(a+b) (the tensor
-    core's own accumulation is allowed 8u per step in the bound; plain
-    float32 additions stand in for it here), times 2^-(a+b)."""
-    qt = f32(q - m)                       # q~, rounded as on the device
-    rt = f32(r - m)                       # r~
-    w = f32(f32(-2.0 * c) * qt)           # W_q
-    b2 = np.float32(0.0)
-    for v in rt:                          # B_r = c |r~|^2 by an fma chain
-        b2 = np.float32(np.float64(v) * np.float64(v) + np.float64(b2))
-    acc = np.float32(np.float32(c) * b2) * np.float32(2.0 ** (a + b))
-    wh, wl = split(f32(w * np.float32(2.0 ** a)))
+def pairwise_sumsq(v, dm):
+    """|v|^2 as the kernels form it: float32 squares, then pairwise float32
+    additions over the padded dimension dm."""
+    t = [np.float32(np.float32(x) * np.float32(x)) for x in v] + [np.float32(0.0)] * (dm - len(v))
+    while len(t) > 1:
+        w = len(t) // 2
+        t = [np.float32(t[k] + t[k + w]) for k in range(w)]
+    return t[0]
+
+
+def scales(c2, rho, rmax, f2):
+    """The operands' power-of-two scales (hd_tensor_form)."""
+    a = 13 - int(np.frexp(2.0 * abs(c2) * rho)[1])
+    b = 13 - int(np.frexp(rmax)[1])
+    s = int(np.frexp(abs(c2) * f2)[1]) + a + b - 14
+    if s > 15:
+        x = s - 15
+        a -= (x + 1) // 2
+        b -= x // 2
+        s = 15
+    return a, b, max(s, 0)
+
+
+def emulate_exponent(q, r, m, c2, a, b, s, dm):
+    """The tensor form's exponent of one (query, reference) pair, in log2
+    units (base_hd_forms.cuh, base_tc.cu), emulated: float32 set-up as on
+    the device, float16 splits of W_q 2^a (W_q = -2c q~), r~ 2^b and
+    c|r~|^2 2^(a+b-s), exact products summed per K16 step and rounded once
+    into the float32 accumulator per step (the model the bound allows 4u
+    for), then D 2^-(a+b) + c|q~|^2 with one fma."""
+    qt = f32(q - m)
+    rt = f32(r - m)
+    c2 = np.float32(c2)
+    wh, wl = split(f32(f32(np.float32(-2.0) * c2 * qt) * np.float32(2.0 ** a)))
     rh, rl = split(f32(rt * np.float32(2.0 ** b)))
-    for k in range(len(q)):
-        for x, y in ((wh[k], rh[k]), (wh[k], rl[k]), (wl[k], rh[k])):
-            acc = np.float32(np.float64(acc) + np.float64(x) * np.float64(y))
-    return np.float64(acc) * 2.0 ** -(a + b)
+    bn = f32(np.float32(c2 * pairwise_sumsq(rt, dm)) * np.float32(2.0 ** (a + b - s)))
+    bh, bl = split(np.array([bn], dtype=np.float32))
+    d = len(q)
+    pad = lambda v: np.concatenate([v.astype(np.float64), np.zeros(dm - d)])  # noqa: E731
+    A = np.concatenate([pad(wh), pad(wh), pad(wl), [2.0 ** s, 2.0 ** s]])
+    B = np.concatenate([pad(rh), pad(rl), pad(rh), [float(bh[0]), float(bl[0])]])
+    kc = (3 * dm + 2 + 15) // 16
+    A = np.concatenate([A, np.zeros(16 * kc - len(A))])
+    B = np.concatenate([B, np.zeros(16 * kc - len(B))])
+    acc = np.float32(0.0)
+    for step in range(kc):
+        sl = slice(16 * step, 16 * step + 16)
+        acc = np.float32(np.float64(acc) + np.dot(A[sl], B[sl]))
+    aq = np.float32(c2 * pairwise_sumsq(qt, dm))
+    return float(np.float32(np.float64(acc) * 2.0 ** -(a + b) + np.float64(aq))), kc
 
 
 def test_bound_covers_the_emulated_form():
-    # kappa u (|q~| + |r~|)^2 / 2h^2 (natural units) bounds the exponent's
-    # error, kappa = max(D+1, 15) + 8 KC; here the set-up and splits are
-    # emulated exactly and the accumulation with float32 additions
+    # kappa u |c| (|q~| + |r~|)^2 (log2 units) bounds the exponent's error,
+    # kappa = 26 + 4 KC
     rng = np.random.default_rng(4)
     log2e = 1.4426950408889634
     worst = 0.0
-    for trial in range(400):
+    for trial in range(300):
         D = int(rng.choice([6, 8, 12, 16, 20, 32]))
-        h = float(np.exp(rng.uniform(np.log(0.05), np.log(1.0))))
-        c = -log2e / (2 * h * h)
+        dm = 8 if D <= 8 else 16 if D <= 16 else 32
         m = f32(rng.random(D))
-        q = f32(m + rng.uniform(-0.1, 0.1, D))
-        r = f32(m + rng.uniform(-0.3, 0.3, D))
+        rho = float(rng.uniform(0.01, 0.2))
+        q = f32(m + rng.uniform(-rho, rho, D) / np.sqrt(D))
+        r = f32(m + rng.uniform(-0.5, 0.5, D))
         qt, rt = (q - m).astype(np.float64), (r - m).astype(np.float64)
-        wmax = 2 * abs(c) * np.linalg.norm(qt) + 1e-30
-        rmax = np.linalg.norm(rt) + 1e-30
-        a = 13 - int(np.frexp(wmax)[1])
-        b = 13 - int(np.frexp(rmax)[1])
-        got = emulate_exponent(q, r, m, np.float32(c), a, b)
-        exact = c * (np.sum(rt * rt) - 2 * np.dot(qt, rt))
-        kc = 3 if D <= 16 else 6  # chained mma steps: DM = 8 or 16 -> 3, DM = 32 -> 6
-        kappa = max(D + 1, 15) + 8 * kc
-        span2 = (np.linalg.norm(qt) + np.linalg.norm(rt)) ** 2
-        bound_log2 = kappa * U * span2 / (2 * h * h) * log2e
-        err = abs(got - exact)
-        worst = max(worst, err / bound_log2)
-        assert err <= bound_log2, (D, h, err, bound_log2)
+        for h in (0.05, 0.2, 1.0):
+            c2 = float(np.float32(-log2e / (2 * h * h)))
+            a, b, s = scales(c2, np.linalg.norm(qt) + 1e-30, np.linalg.norm(rt) + 1e-30, float(rt @ rt) + 1e-30)
+            got, kc = emulate_exponent(q, r, m, c2, a, b, s, dm)
+            exact = c2 * float(np.sum((q.astype(np.float64) - r.astype(np.float64)) ** 2))
+            kappa = 26 + 4 * kc
+            bound = kappa * U * abs(c2) * (np.linalg.norm(qt) + np.linalg.norm(rt)) ** 2
+            err = abs(got - exact)
+            worst = max(worst, err / bound)
+            assert err <= bound, (D, h, err, bound)
     assert worst < 0.5  # the emulated accumulation leaves room for the tensor core's own
