@@ -220,8 +220,20 @@ def kde_sum_batches(ctx: Context, query_batches, rtree: Tree, hs, eps: float, le
     outs = [None] * len(sizes)
     total = {}
 
+    def group_points(idx):
+        # consecutive batches that already lie back to back in one tensor
+        # (e.g. splits of one array) are used in place; others are copied
+        bs = [query_batches[i] for i in idx]
+        if all(b.is_contiguous() and b.dim() == 2 for b in bs) and all(
+                bs[k + 1].data_ptr() == bs[k].data_ptr() + bs[k].numel() * bs[k].element_size()
+                for k in range(len(bs) - 1)):
+            first = bs[0]
+            rows = sum(int(b.shape[0]) for b in bs)
+            return first.as_strided((rows, first.shape[1]), (first.shape[1], 1))
+        return torch.cat([b.contiguous() for b in bs], dim=0)
+
     def run(idx):
-        q = torch.cat([query_batches[i].contiguous() for i in idx], dim=0)
+        q = group_points(idx)
         qt = Tree(ctx, q, leaf_size=leaf_size, base_block=base_block, eps_fp=eps_fp)
         try:
             if log:

@@ -77,3 +77,27 @@ def test_other_errors_are_not_retried(monkeypatch):
     with pytest.raises(dfgt.DFGTError, match="DFGT_ETIMEOUT"):
         dfgt.kde_sum_batches(None, [torch.zeros(2, 1), torch.zeros(2, 1)], None, [1.0], 1e-2)
     assert calls == [4]
+
+
+def test_adjacent_batches_are_used_in_place(monkeypatch):
+    # batches that are consecutive slices of one tensor form their group's
+    # query set without a copy; separate tensors are concatenated
+    seen = []
+
+    def fake_sum(ctx, qt, rt, hs, eps):
+        seen.append((qt.q.data_ptr(), qt.q.shape))
+        return fake_rows(qt.q, hs), {"rounds": 1}
+
+    monkeypatch.setattr(dfgt, "Tree", FakeTree)
+    monkeypatch.setattr(dfgt, "kde_sum", fake_sum)
+    base = torch.arange(24, dtype=torch.float32).reshape(12, 2)
+    parts = list(torch.split(base, [3, 4, 5]))
+    outs, _ = dfgt.kde_sum_batches(None, parts, None, [1.0], 1e-2, max_queries=7)
+    assert seen[0] == (base.data_ptr(), torch.Size([7, 2]))  # batches 0 and 1 in place
+    assert seen[1][1] == torch.Size([5, 2])
+    for b, G in zip(parts, outs):
+        assert torch.equal(G, fake_rows(b, [1.0]))
+    seen.clear()
+    apart = [torch.zeros(3, 2), torch.ones(4, 2)]
+    dfgt.kde_sum_batches(None, apart, None, [1.0], 1e-2)
+    assert seen[0][1] == torch.Size([7, 2]) and seen[0][0] not in (apart[0].data_ptr(), apart[1].data_ptr())
