@@ -55,7 +55,7 @@ typedef struct {
                       8 for D=1); a smaller positive value lowers it */
   double eps_fp;   /* part of eps reserved for float32 rounding in exact sums;
                       0 -> chosen per sum: 1% of eps within [2e-5, 1e-4] for
-                      d <= 5, 20% of eps within [2e-5, 2e-3] for d >= 6
+                      d <= 5, half of eps within [2e-5, 5e-3] for d >= 6
                       (a sum takes the larger of its two trees' values);
                       must be < eps */
   long long base_block; /* a node pair that no summary can take is summed exactly,

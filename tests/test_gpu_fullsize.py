@@ -64,10 +64,10 @@ def test_kde32d_r1e6_batches(dev, orc, eps_index):
     sizes = np.array([len(b) for b in batches])
     order = np.argsort(sizes)
     pick = [order[0], order[len(order) // 2], order[-1]] if eps_index == 0 else [order[len(order) // 2]]
-    # at eps = 1e-3 the trees reserve 5e-4 for float32 rounding, as the
-    # reduced-size bichromatic test does: far queries' exact sums carry
-    # exponents of 30..60, whose rounding the default 20% of eps would not cover
-    efp = 0.0 if eps_index == 0 else 5e-4
+    # the default float allowance at D >= 6 is half of eps (5e-4 at
+    # eps = 1e-3, as the reduced-size bichromatic test sets it): far
+    # queries' exact sums carry exponents of 30..60, whose rounding it covers
+    efp = 0.0
     rt = dfgt.Tree(dev, to_cuda(refs), eps_fp=efp)
     r64 = refs.astype(np.float64)
     rng = np.random.default_rng(99 + eps_index)
