@@ -56,25 +56,42 @@ constexpr int kHtMinQ = 16;  // fewer queries leave too many of the 128 tensor r
 __host__ __device__ constexpr int tc_chunks(int dm) { return ((3 * dm + 2) + 15) / 16; }
 constexpr float kHtUnit = 5.9604645e-08f;  // u = 2^-24
 
-// Squared radius of query node q's points about its box centre (the
-// smaller of the box's half diagonal and the node's point radius) and
-// squared distance from that centre to the farthest corner of reference
-// box r, rounded up.
-__device__ __forceinline__ void hd_entry_bounds(const TreeView& Q, const TreeView& R, int q, int r, float& rho2,
-                                                float& far2) {
-  rho2 = 0.f;
-  far2 = 0.f;
-  for (int k = 0; k < Q.d; ++k) {
-    const float lo = Q.lo[(size_t)q * Q.d + k], hi = Q.hi[(size_t)q * Q.d + k];
-    const float mc = 0.5f * (lo + hi);
-    const float w = fmaxf(__fsub_ru(hi, mc), __fsub_ru(mc, lo));
-    rho2 = __fmaf_ru(w, w, rho2);
-    const float rl = R.lo[(size_t)r * R.d + k], rh = R.hi[(size_t)r * R.d + k];
-    const float f = fmaxf(fabsf(__fsub_ru(rh, mc)), fabsf(__fsub_rd(rl, mc)));
-    far2 = __fmaf_ru(f, f, far2);
+// Bounds of a run (query node q against its entries' reference boxes), all
+// rounded up: the squared radius of q's points about its box centre (the
+// smaller of the box's half diagonal and the node's point radius), and per
+// entry the squared distance from that centre to the farthest corner of
+// reference box r.
+// The query node's part: its box centre (DM slots, zero past d) and rho2.
+template <int DM>
+__device__ __forceinline__ float hd_query_bounds(const TreeView& Q, int q, float (&mc)[DM]) {
+  float rho2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < DM; ++k) {
+    mc[k] = 0.f;
+    if (k < Q.d) {
+      const float lo = Q.lo[(size_t)q * Q.d + k], hi = Q.hi[(size_t)q * Q.d + k];
+      mc[k] = 0.5f * (lo + hi);
+      const float w = fmaxf(__fsub_ru(hi, mc[k]), __fsub_ru(mc[k], lo));
+      rho2 = __fmaf_ru(w, w, rho2);
+    }
   }
   const float rq = Q.rad[q];
-  rho2 = fminf(rho2, __fmul_ru(rq, rq));
+  return fminf(rho2, __fmul_ru(rq, rq));
+}
+
+// An entry's part: far2 from the query box centre mc.
+template <int DM>
+__device__ __forceinline__ float hd_entry_far2(const TreeView& R, int r, const float (&mc)[DM]) {
+  float far2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < DM; ++k) {
+    if (k < R.d) {
+      const float rl = R.lo[(size_t)r * R.d + k], rh = R.hi[(size_t)r * R.d + k];
+      const float f = fmaxf(fabsf(__fsub_ru(rh, mc[k])), fabsf(__fsub_rd(rl, mc[k])));
+      far2 = __fmaf_ru(f, f, far2);
+    }
+  }
+  return far2;
 }
 
 // Scales of a tensor-form run: W_q 2^a, r~ 2^b, B_r 2^(a+b-s) against 2^s.

@@ -290,20 +290,18 @@ __global__ void __launch_bounds__(256) k_tc_plan(TreeView Q, TreeView R, const i
   if (c == 0) return;
   const int b0 = end[key] - c;
   const int hidx = (int)(key / Q.nn), q = (int)(key - (long)hidx * Q.nn);
-  float rho2 = 0.f, f2 = 0.f;
+  float mc[DM];
+  const float rho2 = hd_query_bounds<DM>(Q, q, mc);  // once per run
+  float f2 = 0.f;
   bool self = false;
   long long tot = 0;
   for (int i = lane; i < c; i += 32) {
     const int rv = rsorted[b0 + i];
     const int r = rv & kNodeMask;
     self |= ((rv >> kNodeBits) & kSelfFlag) != 0;
-    float r2, fa2;
-    hd_entry_bounds(Q, R, q, r, r2, fa2);
-    rho2 = r2;
-    f2 = fmaxf(f2, fa2);
+    f2 = fmaxf(f2, hd_entry_far2<DM>(R, r, mc));
     tot += R.cnt[r];
   }
-  rho2 = __shfl_sync(FULL, rho2, 0);
   f2 = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(f2)));
   self = __any_sync(FULL, self);
 #pragma unroll
