@@ -145,7 +145,7 @@ dfgt_status setup_state(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt,
   b->sf = fl + 4 * nh;
   b->base_exp = &ctx->counters.as<RoundCounters>()->base_exp;
   b->status = &ctx->counters.as<RoundCounters>()->status;
-  b->ku = nullptr;
+  b->ku = b->kl = b->sq = b->sr = nullptr;
   b->nh = nh;
   b->eps_eff = eps_eff;
   // the expanded form of exact sums may spend a quarter of the float allowance
@@ -316,8 +316,11 @@ dfgt_status run_sum(dfgt_ctx* ctx, const dfgt_tree* qt, const dfgt_tree* rt, con
     ctx->cap_frontier = capf;
     CK(grow_keep(ctx->frontier[cur], capf * sizeof(Pair), (size_t)nF * sizeof(Pair), s));
     CK(ctx->frontier[cur ^ 1].ensure(capf * sizeof(Pair)));
-    CK(ctx->kus.ensure(capf * sizeof(float)));
+    CK(ctx->kus.ensure(4 * capf * sizeof(float)));
     b.ku = ctx->kus.as<float>();
+    b.kl = b.ku + capf;
+    b.sq = b.ku + 2 * capf;
+    b.sr = b.ku + 3 * capf;
     CK(cudaMemsetAsync(dbar, 0, sizeof(unsigned), s));
     CK(cudaEventRecord(ctx->ev[6], s));
     CK(launch_traverse(Q, R, b, ctx->frontier[0].as<Pair>(), ctx->frontier[1].as<Pair>(), (int)capf,

@@ -89,7 +89,7 @@ struct dfgt_ctx {
   DevBuf scan_tmp;
   DevBuf counters;       // RoundCounters on the device
   DevBuf hvals;          // bandwidths, then 1/(2h^2)
-  DevBuf kus;            // float lower bound on K(d^u) per frontier pair
+  DevBuf kus;            // per frontier pair: K(d^u) lower and K(d^l) upper bounds, box sides
   DevBuf frontier[2];    // Pair
   DevBuf grp_cnt, grp_off, grp_r;  // base-case grouping scratch
   DevBuf tc_plan;        // tensor-core plan of the exact sums (D >= 6)
@@ -221,6 +221,9 @@ struct TravBuffers {
   int* status;           // device status word of the call (kSt* bits)
   float tau_scale_dn;    // eps_eff / (fix_scale |R_total|) as float, rounded down
   float* ku;        // [frontier] lower bound on K(d^u) of each pending pair
+  float* kl;        // [frontier] upper bound on K(d^l), and the two boxes'
+  float* sq;        //   largest sides, from the fold phase's box geometry,
+  float* sr;        //   reused by the classification of the same pair
   int nh;
   double eps_eff;   // eps minus the float allowance for exact sums
   float exp_err;    // exponent error the expanded form of exact sums may take (eps_fp / 4)

@@ -140,7 +140,11 @@ __device__ __forceinline__ void lb_phase(const TreeView& Q, const TreeView& R, c
     float dl2, du2, sq, sr;
     box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sq, sr);
     const float Ku = kernel_lower(du2, b.inv2h2_up[pr.h]);
-    b.ku[i] = Ku;  // reused by the classification of the same pair
+    // reused by the classification of the same pair (no second gather of the boxes)
+    b.ku[i] = Ku;
+    b.kl[i] = kernel_upper(dl2, b.inv2h2_dn[pr.h]);
+    b.sq[i] = sq;
+    b.sr[i] = sr;
     // leave-one-out: a node meeting Q holds at most |R| - 1 other points for some query
     const int nr = R.cnt[pr.r] - ((b.loo && ranges_meet(Q, pr.q, R, pr.r)) ? 1 : 0);
     const u64 f = to_fix_f((float)nr, Ku, b.fix_scale_dn);
@@ -181,10 +185,8 @@ __device__ __forceinline__ void classify_phase(const TreeView& Q, const TreeView
       const bool holds = meet && range_holds(R, pr.r, Q, pr.q);
       const bool summarise = !meet || holds;
       const float nRo = meet ? nR - 1.f : nR;
-      float dl2, du2, sideQ, sideR;
-      box_geometry<D>(Q, pr.q, R, pr.r, dl2, du2, sideQ, sideR);
-      const float Kl = kernel_upper(dl2, b.inv2h2_dn[pr.h]);
-      const float Ku = b.ku[i];
+      // the fold phase's box geometry of this pair
+      const float Kl = b.kl[i], Ku = b.ku[i], sideQ = b.sq[i], sideR = b.sr[i];
       const u64 lbf = __ldcg(b.inherited + hq) + __ldcg(b.decided + hq) + __ldcg(b.lbsum + hq);
       // tau = eps |R| G^l(Q) / |R_total| (CanSummarize), rounded down
       const float tau = __fmul_rd(__fmul_rd(b.tau_scale_dn, nRo), u64_to_f_rd(lbf));
