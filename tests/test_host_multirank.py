@@ -79,3 +79,25 @@ def test_dist_env_defaults(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "4")
     monkeypatch.setenv("LOCAL_RANK", "1")
     assert bench.dist_env() == (3, 4, 1)
+
+
+def test_query_groups_spans():
+    import bench
+
+    # consecutive batches up to the limit; a batch above it stands alone
+    assert bench.query_groups([5, 3, 10, 2, 2], 8) == [(0, 8), (8, 18), (18, 22)]
+    assert bench.query_groups([20], 8) == [(0, 20)]
+    assert bench.query_groups([1] * 5, 2) == [(0, 2), (2, 4), (4, 5)]
+    spans = bench.query_groups([7, 1, 9, 4, 4, 30, 2], 12)
+    assert spans[0][0] == 0 and spans[-1][1] == 57
+    assert all(a < b for a, b in spans) and all(spans[k][1] == spans[k + 1][0] for k in range(len(spans) - 1))
+
+
+def test_load_problem_shapes():
+    import bench
+
+    x, r, hs, eps, sizes = bench.load_problem("kde2d_n1e4", 500)
+    assert x.shape == (500, 2) and r is None and sizes is None and eps == 1e-2
+    q, r, hs, eps, sizes = bench.load_problem("kde32d_r1e6_q64batches", 2000)
+    assert r.shape == (2000, 32) and q.shape == (sum(sizes), 32) and len(sizes) == 64 and len(hs) == 16
+    assert eps == 1e-2 and q.dtype == np.float32 and q.flags["C_CONTIGUOUS"]
