@@ -704,15 +704,24 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 20 / kBaseWarps)
 // at most (D+3) u x per term).
 constexpr int kHdQBlocks = 4;  // query blocks of 32 in flight per pass
 
+// Reference pairs per tile, the largest that keeps the blocks per SM that
+// the registers allow (4 at DM = 16, 2 at DM = 32): at DM = 32, 48 pairs ran
+// the direct form 25% faster than 16 and 8% faster than 32 (64 would leave
+// one block per SM); at DM = 16, 40 pairs 1.6% faster than 32, and 64 no
+// faster than 40.
 template <int DM>
 struct HdShape {
-  static constexpr int TP = DM == 8 ? 64 : DM == 16 ? 32 : 16;   // reference pairs per tile
+  static constexpr int TP = DM == 8 ? 64 : DM == 16 ? 40 : 48;   // reference pairs per tile
   static constexpr int PS = 2 * DM + 4;                          // floats per pair slot
 };
 
 // Eight warps per block: one-warp blocks (more registers, no spills) ran
 // the D = 16 direct form 6% slower.
 constexpr int kHdWarps = 8;
+// the block's reference tiles, in dynamic shared memory (past the 48 KB
+// of a static allocation for the larger tiles)
+template <int DM>
+constexpr int hd_smem() { return kHdWarps * HdShape<DM>::TP * HdShape<DM>::PS * (int)sizeof(float); }
 template <int DM>
 __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView R, const int* __restrict__ rsorted,
                                                 const int* __restrict__ ksorted, int n,
@@ -720,7 +729,7 @@ __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView 
                                                 const unsigned char* __restrict__ tcflag,
                                                 double* __restrict__ gacc) {
   constexpr int TP = HdShape<DM>::TP, PS = HdShape<DM>::PS;
-  __shared__ __align__(16) float sT[kHdWarps][TP * PS];
+  extern __shared__ __align__(16) float sHd[];  // kHdWarps tiles of TP * PS floats
   __shared__ int sOff[kHdWarps][kEntryChunk + 1], sRb[kHdWarps][kEntryChunk];
   const unsigned FULL = 0xffffffffu;
   const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -743,7 +752,7 @@ __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView 
   }
   const int keyp = __shfl_up_sync(FULL, key, 1);
   const unsigned starts = __ballot_sync(FULL, lane < m && (lane == 0 || key != keyp));
-  float* T = sT[wib];
+  float* T = sHd + (size_t)wib * TP * PS;
   int t = 0;
   while (t < m) {
     const unsigned later = starts & ~((2u << t) - 1u);
@@ -862,6 +871,18 @@ __global__ void __launch_bounds__(kHdWarps * 32) k_base_hd(TreeView Q, TreeView 
     __syncwarp();
     t = e;
   }
+}
+
+template <int DM>
+cudaError_t launch_base_hd(int g, const TreeView& Q, const TreeView& R, const int* rsorted, const int* ksorted,
+                           int n, const float* c2, const unsigned char* tcflag, double* gacc, cudaStream_t s) {
+  constexpr int smem = hd_smem<DM>();
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_base_hd<DM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_base_hd<DM><<<g, kHdWarps * 32, smem, s>>>(Q, R, rsorted, ksorted, n, c2, tcflag, gacc);
+  return cudaGetLastError();
 }
 
 // Scaled far-field moments M_alpha = m_alpha (2h^2)^(-|alpha|/2) for alpha < p
@@ -1616,12 +1637,12 @@ cudaError_t launch_base(const TreeView& Q, const TreeView& R, const TravBuffers&
     const long warps = (n + kEntryChunk - 1) / kEntryChunk;
     const int g = (int)((warps + kHdWarps - 1) / kHdWarps);
     if (Q.dp <= 8)
-      k_base_hd<8><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc);
+      e = launch_base_hd<8>(g, Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc, s);
     else if (Q.dp <= 16)
-      k_base_hd<16><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc);
+      e = launch_base_hd<16>(g, Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc, s);
     else
-      k_base_hd<32><<<g, kHdWarps * 32, 0, s>>>(Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      e = launch_base_hd<32>(g, Q, R, rsorted, ksorted, n, b.c2, tcflag, b.gacc, s);
+    if (e != cudaSuccess) return e;
     ++*launches;
     if (sc.tc0 && (e = cudaEventRecord(sc.tc0, s)) != cudaSuccess) return e;
     if ((e = launch_tc_sums(Q, R, b, rsorted, n, *sc.plan, s, launches)) != cudaSuccess) return e;
