@@ -366,7 +366,7 @@ __device__ __forceinline__ void load_raw(const float* row, float* a) {
 
 // Two forms of the exponent x = c |q - r|^2, c = -log2(e)/(2h^2):
 //  * direct: differences q - r, D packed add + D packed fma + 1 packed mul
-//    per two interactions; rounding changes a term by at most (D+3) u x
+//    per two interactions; rounding changes a term by at most (D+4) u x
 //    relative (x in natural units from here on);
 //  * expanded about the query node's center m, with q~ = q - m, r~ = r - m:
 //    x = A_q + B_r + sum_k W_qk r~_k, A_q = c|q~|^2, W_q = -2c q~, B_r = c|r~|^2
@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 20 / kBaseWarps)
 // that query.  Per two interactions: DM packed subtractions and FMAs, one
 // packed multiply, two ex2; blocks of 8 steps summed in float32 and added
 // with Kahan compensation (so the rounding is that of the D <= 5 direct form,
-// at most (D+3) u x per term).
+// at most (D+4) u x per term).
 constexpr int kHdQBlocks = 4;  // query blocks of 32 in flight per pass
 
 // Reference pairs per tile, the largest that keeps the blocks per SM that

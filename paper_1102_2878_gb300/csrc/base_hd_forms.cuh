@@ -35,7 +35,7 @@
 // part, Kahan across parts); for the exact sums of a query to stay within
 // eps_fp that needs its kernel-weighted mean exponent x~ = sum K x / sum K
 // below (3/4 eps_fp - 2^-21 - 9u) / (2 kappa u), as for the direct form's
-// (D+3) u x (the self term K = 1 keeps x~ small when Q = R).
+// (D+4) u x (the self term K = 1 keeps x~ small when Q = R).
 #pragma once
 
 #include "common.cuh"

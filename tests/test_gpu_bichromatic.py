@@ -12,9 +12,9 @@ against the oracle on the same sample wherever its float32 terms can hold
 the sum (G >= 1e-30).
 
 Float32 tolerance.  A term exp(-x) computed in float32 from D coordinate
-differences carries about (D+3) u x of relative error (u = 2^-24), so at
+differences carries at most (D+4) u x of relative error (u = 2^-24), so at
 D = 32, where these sums are made of terms with x of 30..60, the brute
-force is checked against sum_r K_r (2^-21 + (D+3) u x_r) + 2^-20 G, and the
+force is checked against sum_r K_r (2^-21 + (D+4) u x_r) + 2^-20 G, and the
 dual-tree trees reserve eps_fp = 5e-4 of eps for float32 rounding (enough
 for a kernel-weighted mean exponent up to ~115).
 """
@@ -39,7 +39,7 @@ def bruteforce_tolerance(q64, r64, h):
     for i, q in enumerate(q64):
         x = ((r64 - q) ** 2).sum(1) / (2 * h * h)
         K = np.exp(-x)
-        tol[i] = (K * (2.0 ** -21 + (D + 3) * U * x)).sum()
+        tol[i] = (K * (2.0 ** -21 + (D + 4) * U * x)).sum()
         G[i] = K.sum()
     return tol + 2.0 ** -20 * G
 

@@ -11,7 +11,7 @@ from paper_1102_2878_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
 
-# Kernel values are float32 (ex2.approx: 2^-21 relative, plus (D+3)u x from
+# Kernel values are float32 (ex2.approx: 2^-21 relative, plus (D+4)u x from
 # the rounding of the exponent) and every sum is float64, so the scores
 # agree with the float64 oracle to ~1e-6 and the gradients to ~1e-6 of the
 # sums of |terms| they are made of; the tolerances leave a factor of 100.

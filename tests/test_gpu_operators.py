@@ -171,7 +171,7 @@ def test_prune_and_base_operators(setup, orc, dev):
         _, Rp = node_points(Y, tr, b)
         want[qi] += orc.naive_kde(Qp, Rp, h)
         # float32 rounding: each term exp(-x) with x = d^2/2h^2 carries the
-        # ex2 error (< 2^-21 relative) and either (D+3)u x (direct form) or
+        # ex2 error (< 2^-21 relative) and either (D+4)u x (direct form) or
         # at most 5e-6 + 2(D+4)u x (expanded form, used only when its bound
         # allows); the run of at most 24 terms is summed in float32
         x = ((Qp[:, None, :] - Rp[None, :, :]) ** 2).sum(2) / (2 * h * h)

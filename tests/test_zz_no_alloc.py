@@ -26,7 +26,7 @@ U = 2.0 ** -24
 
 def float32_tolerance(q64, r64, h):
     """The brute-force tolerance of the other GPU tests: each float32 term
-    exp(-x) carries 2^-21 (ex2) plus (D+3) u x (its exponent from D
+    exp(-x) carries 2^-21 (ex2) plus (D+4) u x (its exponent from D
     coordinate differences), and the compensated sum 2^-20 of G."""
     D = q64.shape[1]
     tol = np.empty(len(q64))
@@ -34,7 +34,7 @@ def float32_tolerance(q64, r64, h):
     for i, q in enumerate(q64):
         x = ((r64 - q) ** 2).sum(1) / (2 * h * h)
         K = np.exp(-x)
-        tol[i] = (K * (2.0 ** -21 + (D + 3) * U * x)).sum()
+        tol[i] = (K * (2.0 ** -21 + (D + 4) * U * x)).sum()
         G[i] = K.sum()
     return tol + 2.0 ** -20 * G
 
