@@ -374,14 +374,18 @@ __device__ __forceinline__ void load_raw(const float* row, float* a) {
 //    packed fma per two interactions and is scaled by 2^A_q once per query
 //    and tile (B_r + W_q . r~ = x - A_q lies between x and |c| |q~|^2, so it
 //    cannot overflow, and it underflows only where 2^x does).  Its error in
-//    x, with the rounding of q~ and r~ taken as a perturbation of the points,
-//    is at most (D+4) u (|q~| + |r~|)^2 / 2h^2.  A run uses it when that is
-//    at most E for the query box and the farthest corner of every reference
-//    box, or when 8 (D+4) u rho_Q^2 / 2h^2 <= E for the query box radius
-//    rho_Q alone: with |r~| <= |q~| + |q - r| and (a + b)^2 <= 2a^2 + 2b^2
-//    the error is then at most E + 2 (D+4) u x per term.  Otherwise the
-//    direct form.  E is a quarter of the float allowance eps_fp, so a term
-//    stays within eps_fp whenever 2^-21 + eps_fp / 4 + 2 (D+4) u x <= eps_fp.
+//    x, with the rounding of q~ and r~ taken as a perturbation of the points
+//    (2u), is at most u ((D+4) (|q~| + |r~|)^2 + D |r~|^2) / 2h^2: A_q and
+//    B_r each take D + 1 roundings and c one, W_q . r~ one per product and
+//    one per step of the chain of D fused multiply-adds, and that chain
+//    starts from B_r, so each of its steps may also round away up to u |B_r|
+//    (hence the D |r~|^2).  A run uses it when that is at most E for the
+//    query box and the farthest corner of every reference box, or when
+//    (10 D + 32) u rho_Q^2 / 2h^2 <= E for the query box radius rho_Q alone:
+//    with |r~| <= |q~| + |q - r| and (a + b)^2 <= 2a^2 + 2b^2 the error is
+//    then at most E + (4 D + 8) u x per term.  Otherwise the direct form.
+//    E is a quarter of the float allowance eps_fp, so a term stays within
+//    eps_fp whenever 2^-21 + eps_fp / 4 + (4 D + 8) u x <= eps_fp.
 
 constexpr int kQCap = 128;  // queries of a run staged at a time
 
@@ -510,11 +514,12 @@ __global__ void __launch_bounds__(kBaseWarps * 32, 20 / kBaseWarps)
       const float f2 = __uint_as_float(
           __reduce_max_sync(FULL, (lane >= t && lane < e) ? __float_as_uint(far2) : 0u));
       const float span = __fadd_ru(__fsqrt_ru(rq2), __fsqrt_ru(f2));
-      const float ui = (float)(D + 4) * 5.9604645e-08f * __shfl_sync(FULL, i2h, t);
+      const float uu = 5.9604645e-08f * __shfl_sync(FULL, i2h, t);
       // a run with a self entry takes the direct form, which leaves the
       // self interaction out exactly
       self_run = __any_sync(FULL, lane >= t && lane < e && self);
-      expanded = !self_run && (ui * span * span <= exp_err || 8.f * ui * rq2 <= exp_err);
+      expanded = !self_run && ((float)(D + 4) * uu * span * span + (float)D * uu * f2 <= exp_err ||
+                               (float)(10 * D + 32) * uu * rq2 <= exp_err);
       if (expanded && lane == 0) atomicAdd(exp_ctr, (unsigned long long)qn * tot);
       new_run = false;
     }

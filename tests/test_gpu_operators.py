@@ -172,11 +172,11 @@ def test_prune_and_base_operators(setup, orc, dev):
         want[qi] += orc.naive_kde(Qp, Rp, h)
         # float32 rounding: each term exp(-x) with x = d^2/2h^2 carries the
         # ex2 error (< 2^-21 relative) and either (D+4)u x (direct form) or
-        # at most 5e-6 + 2(D+4)u x (expanded form, used only when its bound
+        # at most 5e-6 + (4D+8)u x (expanded form, used only when its bound
         # allows); the run of at most 24 terms is summed in float32
         x = ((Qp[:, None, :] - Rp[None, :, :]) ** 2).sum(2) / (2 * h * h)
         K = np.exp(-x)
-        tol[qi] += (K * (2.0 ** -21 + 2 * (D + 4) * U * x + 5e-6)).sum(1) + 24 * U * K.sum(1)
+        tol[qi] += (K * (2.0 ** -21 + (4 * D + 8) * U * x + 5e-6)).sum(1) + 24 * U * K.sum(1)
         # terms below the float32 normal range flush to zero
         tol[qi] += np.where(K < 2.0 ** -125, K, 0.0).sum(1)
     bad = np.abs(G - want) > tol + 1e-300

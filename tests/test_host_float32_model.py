@@ -1,6 +1,8 @@
-"""The rounding model behind the float32 kernel values of the direct form
-(the brute force, the D <= 5 exact sums in direct form and the D >= 6 SIMT
-exact sums all compute a term the same way): D float32 differences q_k - r_k,
+"""The rounding models behind the float32 exponents of the exact sums, checked
+by emulating the kernels' float32 operations on the host.  The expanded form
+of the D <= 5 sums is described at its tests below.  The direct form (the
+brute force, the D <= 5 exact sums in direct form and the D >= 6 SIMT exact
+sums all compute a term the same way): D float32 differences q_k - r_k,
 their squares summed by a chain of fused multiply-adds, one float32 product
 with c = fl(-log2(e) / (2h^2)), then 2^x.  Counting first-order relative
 errors of the exponent x = |q - r|^2 / (2h^2) (u = 2^-24): 2u from squaring
@@ -161,3 +163,99 @@ def test_emulation_rounds_every_step():
     once = np.abs(x.astype(f32).astype(f64) - x)
     emul = np.abs(kernel_exponent(q, r, h).astype(f64) - x)
     assert emul.mean() > 2 * once.mean()
+
+
+# ---- the expanded form (D <= 5 exact sums) ----
+#
+# About the query box centre m, with q~ = q - m and r~ = r - m rounded in
+# float32: A_q = fl(c |q~|^2) and B_r = fl(c |r~|^2) from fused multiply-add
+# chains, W_q = fl(-2c q~), and S = B_r + W_q . r~ by a chain of D fused
+# multiply-adds that starts from B_r; the exponent is A_q + S (2^S is summed
+# and the sum scaled by 2^A_q, so A_q + S is never rounded).  Its error,
+# in natural units, is at most u ((D+4) (|q~| + |r~|)^2 + D |r~|^2) / 2h^2.
+
+
+def expanded_exponent(q, r, m, h):
+    """A_q + S (log2 units, float64 sum of the two float32 values) and the
+    rounded offsets q~, r~, in the kernel's operation order."""
+    inv = 1.0 / (2.0 * h * h)
+    c = f32(-LOG2E * inv)
+    n, D = q.shape
+    qt = (q - m).astype(f32)
+    rt = (r - m).astype(f32)
+    a2 = np.zeros(n, f32)
+    b2 = np.zeros(n, f32)
+    for k in range(D):
+        a2 = fma32(qt[:, k], qt[:, k], a2)
+        b2 = fma32(rt[:, k], rt[:, k], b2)
+    A = (c * a2).astype(f32)
+    B = (c * b2).astype(f32)
+    W = ((f32(-2.0) * c) * qt).astype(f32)  # -2c is exact; one rounding
+    S = B
+    for k in range(D):
+        S = fma32(W[:, k], rt[:, k], S)
+    return A.astype(f64) + S.astype(f64), qt, rt
+
+
+def expanded_ratios(q, r, m, h):
+    """The exponent's error (natural units) over the corrected bound and over
+    (D+4) u (|q~| + |r~|)^2 / 2h^2 alone."""
+    D = q.shape[1]
+    xh, qt, rt = expanded_exponent(q, r, m, h)
+    xe = -LOG2E * ((q.astype(f64) - r.astype(f64)) ** 2).sum(1) / (2 * h * h)
+    err = np.abs(xh - xe) / LOG2E
+    nq = np.sqrt((qt.astype(f64) ** 2).sum(1))
+    nr = np.sqrt((rt.astype(f64) ** 2).sum(1))
+    old = (D + 4) * U * (nq + nr) ** 2 / (2 * h * h)
+    new = old + D * U * nr ** 2 / (2 * h * h)
+    return err / new, err / old
+
+
+@pytest.mark.parametrize("D", [1, 2, 3, 4, 5])
+def test_expanded_exponent_within_bound(D):
+    rng = np.random.default_rng(200 + D)
+    n = 50000
+    worst = 0.0
+    for side, h in ((1.0, 0.3), (0.1, 0.05), (0.01, 0.02)):
+        # a query box of the given side about its centre, references anywhere
+        m = rng.random((1, D)).astype(f32)
+        q = (m + side * (rng.random((n, D)) - 0.5)).astype(f32)
+        r = rng.random((n, D)).astype(f32)
+        rn, _ = expanded_ratios(q, r, m, h)
+        worst = max(worst, float(rn.max()))
+    assert worst <= 1.0 + 1e-3, worst
+
+
+def test_chain_from_b_r_breaks_the_bound_without_its_term():
+    # D = 5, m = 0: |B_r| just above a power of two and every W_k r~_k just
+    # under half an ulp of it, so each step of the chain rounds its addend
+    # away in the same direction; the error exceeds (D+4) u (|q~| + |r~|)^2 /
+    # 2h^2 and stays within the bound with the D |r~|^2 term
+    hexq = ["-0x1.88e2ep-25", "0x1.036804p-23", "-0x1.a91a98p-25", "0x1.224e4cp-23", "0x1.3c8ae2p-23"]
+    hexr = ["0x1.6d458p-1", "-0x1.149cd8p-2", "0x1.5196a2p-1", "-0x1.ee575ap-3", "-0x1.c55e2p-3"]
+    q = np.array([[float.fromhex(v) for v in hexq]], dtype=f32)
+    r = np.array([[float.fromhex(v) for v in hexr]], dtype=f32)
+    h = 0.4502110246667935
+    rn, ro = expanded_ratios(q, r, np.zeros((1, 5), f32), h)
+    assert ro[0] > 1.0, ro[0]          # 9.26 / 9
+    assert rn[0] <= 1.0, rn[0]
+
+
+@pytest.mark.parametrize("D", [1, 3, 5])
+def test_radius_criterion_per_term_error(D):
+    # a run admitted by (10 D + 32) u rho_Q^2 / 2h^2 <= E has per-term error
+    # at most E + (4 D + 8) u x, x = |q - r|^2 / 2h^2
+    rng = np.random.default_rng(300 + D)
+    n = 50000
+    rho, h = 0.05, 0.1
+    m = np.full((1, D), 0.5, f32)
+    dirs = rng.standard_normal((n, D))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    q = (m + dirs * rho * rng.random((n, 1)) ** (1.0 / D)).astype(f32)
+    r = (m + (rng.random((n, D)) - 0.5) * 2.0).astype(f32)
+    xh, qt, _ = expanded_exponent(q, r, m, h)
+    rho_q2 = float((qt.astype(f64) ** 2).sum(1).max())
+    E = (10 * D + 32) * U * rho_q2 / (2 * h * h)
+    x = ((q.astype(f64) - r.astype(f64)) ** 2).sum(1) / (2 * h * h)
+    err = np.abs(xh + LOG2E * x) / LOG2E
+    assert np.all(err <= (E + (4 * D + 8) * U * x) * (1.0 + 1e-3))
